@@ -1,0 +1,370 @@
+#!/usr/bin/env python3
+"""Benchmark of the batched transfer-matrix hot path on GB300.
+
+One step = one call of tmm_coh_batched over the whole dispersive workload
+(16384 stacks x 24 layers, 8 Cauchy materials, 512 lambda in 300-1200 nm x
+32 theta in 0-85 deg, s and p, R and T), inputs resident in HBM.  The metric is
+evaluations per second, one evaluation being one (stack, lambda, theta, pol)
+R, T pair.  The headline runs in FP32; the FP64 path is measured the same way
+and reported beside it.
+
+Prints ONE JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle instead, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+L2_BYTES = 129 * 1024 * 1024
+FLUSH_BYTES = 512 * 1024 * 1024
+# Algorithmic work per (eval, interface): real flops of the vector sweep with
+# both polarisations sharing Snell's law and the phase, FMA = 2, transcendental
+# instructions not counted.  Breakdown per (lambda, theta, interface): shared
+# 21 (n^2 - beta^2, root, phase, |q|^2 product), s 44, p 51 -> 116 / 2 pols.
+FLOPS_PER_EVAL_INTERFACE = 58.0
+# Unit-count peaks (152 SMs, max SM clock 2070 MHz): FP32 128 FMA lanes / SM;
+# FP64 from the nominal 1.25 TFLOP/s of the part.
+SMS = 152
+MAX_SM_MHZ = 2070.0
+PEAK_F32_FLOPS = SMS * 128 * 2 * MAX_SM_MHZ * 1e6
+PEAK_F64_FLOPS = 1.25e12
+DOMINANT_KERNEL_SOURCES = ["paper_2111_13667_gb300/csrc/tmm_fwd.cu", "paper_2111_13667_gb300/csrc/tmm_device.cuh"]
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in DOMINANT_KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def stored_traffic(kernel_key):
+    """DRAM bytes per launch from the committed ncu summary, if it still
+    describes the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as fh:
+        data = json.load(fh)
+    ent = data.get(kernel_key)
+    if not ent or ent.get("source_hash") != kernel_hash():
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            return json.load(fh)
+    return None
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- GPU arm
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def time_steps(fn, steps, warmup, torch, flush):
+    """Per-step device time (ms) of fn() with an L2 flush before every step,
+    measured with CUDA events on the current stream."""
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    evs = []
+    for _ in range(steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        evs.append((a, b))
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in evs]
+
+
+def gpu_arm(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2111_13667_gb300 import abi
+    from paper_2111_13667_gb300 import workloads as W
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    abi.load()
+
+    w = W.dispersive(S=args.stacks) if args.stacks else W.dispersive()
+    evals = w.evals
+    interfaces = w.L_max + 1
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    out = {}
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(v):
+        if world == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    for prec, steps, warmup in (("f32", args.steps, args.warmup), ("f64", args.f64_steps, 3)):
+        if prec == "f64" and args.skip_f64:
+            continue
+        prob = abi.to_device(w, prec, device=dev)
+        R = prob.empty_out()
+        T = prob.empty_out()
+        step = lambda: abi.tmm_coh_batched(prob, R, T)
+        barrier()
+        sampler = ClockSampler(local) if prec == "f32" else None
+        wall0 = time.perf_counter()
+        if sampler:
+            sampler.__enter__()
+        try:
+            times = time_steps(step, steps, warmup, torch, flush)
+        finally:
+            if sampler:
+                sampler.__exit__()
+        barrier()
+        wall = time.perf_counter() - wall0
+        ms = max_over_ranks(sum(times) / len(times))
+        value = evals * world / (ms * 1e-3)
+        flops = FLOPS_PER_EVAL_INTERFACE * interfaces * evals
+        achieved = flops / (ms * 1e-3)
+        peak = PEAK_F32_FLOPS if prec == "f32" else PEAK_F64_FLOPS
+        key = f"tmm_fwd_kernel<{'float' if prec == 'f32' else 'double'},3,true>"
+        entry = {"value": value, "ms_per_step": ms, "steps": steps, "warmup": warmup, "wall_s": wall,
+                 "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
+                              "unit": "TFLOP/s", "frac": achieved / peak, "traffic": stored_traffic(key),
+                              "kernel": key,
+                              "work": f"{FLOPS_PER_EVAL_INTERFACE:g} flop per eval-interface x {interfaces} "
+                                      f"interfaces x {evals} evals"}}
+        try:
+            f, pms = abi.tmm_probe_fma_rate(abi.TMM_F32 if prec == "f32" else abi.TMM_F64)
+            entry["roofline"]["probe_peak"] = f / 1e12
+        except Exception as e:  # the probe is optional context
+            entry["roofline"]["probe_peak"] = f"probe failed: {e}"
+        if sampler:
+            entry["clocks"] = sampler.summary()
+        # end to end through the C ABI from pinned host buffers
+        if not args.skip_e2e and (prec == "f32" or not args.skip_e2e_f64):
+            h_in = {k: getattr(prob, k).cpu().pin_memory() for k in ("theta", "lam", "d", "table", "mat_idx")}
+            hR = torch.empty(R.shape, dtype=R.dtype).pin_memory()
+            hT = torch.empty(T.shape, dtype=T.dtype).pin_memory()
+            d_in = {k: getattr(prob, k) for k in h_in}
+
+            def e2e_step():
+                for k, v in h_in.items():
+                    d_in[k].copy_(v, non_blocking=True)
+                abi.tmm_coh_batched(prob, R, T)
+                hR.copy_(R, non_blocking=True)
+                hT.copy_(T, non_blocking=True)
+
+            e_steps = max(2, min(steps, 5))
+            et = time_steps(e2e_step, e_steps, 2, torch, flush)
+            ems = max_over_ranks(sum(et) / len(et))
+            h2d = sum(v.numel() * v.element_size() for v in h_in.values())
+            d2h = (hR.numel() * hR.element_size()) * 2
+            entry["e2e"] = {"value": evals * world / (ems * 1e-3), "unit": "evals/s", "ms_per_step": ems,
+                            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": e_steps}
+        out[prec] = entry
+        del R, T, prob
+        torch.cuda.empty_cache()
+
+    head = out["f32"]
+    line = {
+        "metric": "TMM evals/s (stack x lambda x theta x pol), dispersive 16384x24, 512 lambda x 32 theta, s+p",
+        "value": head["value"], "unit": "evals/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded)",
+        "config": {"workload": w.name, "stacks_per_gpu": w.S, "layers": w.L_max, "n_lambda": w.n_lambda,
+                   "n_theta": w.n_theta, "pols": "s+p", "outputs": "R,T",
+                   "l2": f"flushed ({FLUSH_BYTES >> 20} MiB memset) before every timed step; "
+                         f"outputs {R_bytes(w, 4) >> 20} MiB per step also exceed L2",
+                   "parallelism": f"replicas x{world} (independent stacks, no collective)"},
+        "roofline": head["roofline"], "clocks": head.get("clocks"), "e2e": head.get("e2e"),
+        "gpu_launches": args.steps,
+    }
+    if "f64" in out:
+        line["f64"] = out["f64"]
+    line["cpu_baseline"] = cpu_baseline(w, args) if (rank == 0 and world == 1 and not args.skip_cpu) else None
+    peaks = measured_peaks()
+    if peaks:
+        line["measured_peaks_file"] = {k: peaks[k] for k in list(peaks)[:8]}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def R_bytes(w, elt):
+    return w.S * w.n_theta * w.n_lambda * w.n_pol * elt
+
+
+# ---------------------------------------------------------------- CPU oracle
+def cpu_threads():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_sample_rate(w, target_s, max_stacks=None):
+    """Time the oracle (as it stands) on the first k stacks of w, k chosen so
+    the run takes roughly target_s seconds.  Returns (evals/s, k, seconds)."""
+    import oracle
+    threads = cpu_threads()
+
+    def run(k):
+        sub = w.subset(np.arange(k))
+        n = oracle.assemble_index(sub.n_direct, sub.table, sub.mat_idx, sub.n_lambda)
+        t0 = time.perf_counter()
+        oracle.coh_tmm_pols(sub.pols, n, sub.d, sub.theta, sub.lam, L_per_stack=sub.L_per_stack, nthreads=threads)
+        return time.perf_counter() - t0
+
+    k = max(1, min(threads, w.S))
+    t = run(k)
+    k2 = int(min(w.S, max_stacks or w.S, max(k, k * target_s / max(t, 1e-3))))
+    if k2 > k:
+        k, t = k2, run(k2)
+    per_stack = w.n_lambda * w.n_theta * w.n_pol
+    return k * per_stack / t, k, t
+
+
+def cpu_baseline(w, args):
+    rate, k, t = oracle_sample_rate(w, args.cpu_seconds)
+    return {"value": rate, "unit": "evals/s", "cores": cpu_threads(), "kind": "oracle",
+            "sample": f"first {k} of {w.S} stacks, all {w.n_lambda} lambda x {w.n_theta} theta x 2 pol, "
+                      f"FP64 C oracle, {t:.1f} s"}
+
+
+def reference_arm(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2111_13667_gb300 import workloads as W
+    w = W.dispersive()
+    per_step = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+    rates = []
+    for i in range(args.warmup + args.steps):
+        rate, k, t = oracle_sample_rate(w, per_step)
+        if i >= args.warmup:
+            rates.append((rate, k, t))
+    value = statistics.mean(r for r, _, _ in rates)
+    ms = statistics.mean(t for _, _, t in rates) * 1e3
+    k = rates[-1][1]
+    line = {
+        "impl": "reference",
+        "metric": "TMM evals/s (stack x lambda x theta x pol), dispersive 16384x24, 512 lambda x 32 theta, s+p",
+        "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded)",
+        "config": {"workload": w.name, "sample_per_step": f"first {k} stacks (bounded CPU sample)"},
+        "cpu_baseline": {"value": value, "unit": "evals/s", "kind": "oracle", "cores": cpu_threads(),
+                         "sample": f"first {k} of {w.S} stacks per step, FP64 C oracle"},
+        "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--f64-steps", type=int, default=3)
+    ap.add_argument("--skip-f64", action="store_true")
+    ap.add_argument("--skip-e2e-f64", action="store_true", default=True)
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--stacks", type=int, default=0, help="shrink the workload (profiling runs only)")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)  # never fewer than 3 untimed warm-up steps
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

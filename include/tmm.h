@@ -1,0 +1,195 @@
+/*
+ * tmm.h -- C ABI of libtmm, a GB300 (sm_103a) library for the batched
+ * coherent transfer-matrix method of TMM-Fast (arXiv 2111.13667).
+ *
+ * Physics (arXiv 2111.13667, Sec. 2): a plane wave of vacuum wavelength
+ * lambda enters a stack from the semi-infinite injection medium 0 at angle
+ * theta, crosses L finite layers (index n_j, thickness d_j) and leaves into
+ * the semi-infinite outcoupling medium L+1.  For every (stack, lambda, theta,
+ * polarisation) the library evaluates Snell's law, the Fresnel coefficients
+ * of Eq. 1, the layer matrices of Eq. 3, their product (Eq. 4), the
+ * extraction of r and t (Eqs. 5-6) and R, T (Eq. 2).
+ *
+ * Conventions shared by every entry point
+ *   - Time dependence exp(-i omega t); absorbing media have n = n' + i k with
+ *     k >= 0.  Lengths in nm, angles in radians in medium 0.
+ *   - Complex arrays are interleaved (re, im) pairs of the working type.
+ *   - Root of cos(theta_j): the one whose n_j cos(theta_j) has a positive
+ *     imaginary part (decaying along +z); if that part is zero to rounding,
+ *     the one with positive real part.  Im(delta_j) of a layer's phase is
+ *     clamped at 35 (opaque layers).  At exact grazing incidence
+ *     (cos(theta_0) = 0) R = 1 and T = 0.  T follows the Poynting-flux form of
+ *     Eq. 2: s: Re(n_out c_out)/Re(n_in c_in)|t|^2, p: with conj(c).
+ *   - Every pointer named "device" is caller-owned device memory, contiguous,
+ *     C order, in the working type selected by `prec` (double for TMM_F64,
+ *     float for TMM_F32) unless stated otherwise.  The library keeps no
+ *     pointer after a call returns and allocates no device memory, except the
+ *     surrogate object, which owns its weights.
+ *   - Calls are asynchronous on `stream` (a cudaStream_t passed as void*;
+ *     NULL = the legacy default stream).  Arguments are checked on the host
+ *     before anything is launched; a rejected call launches nothing.  No C++
+ *     exception crosses this boundary.
+ *   - Values that can only be checked on the device (a material index out of
+ *     range, a layer count outside [0, L_max], a complex injection index)
+ *     poison the outputs of the affected stack with NaN instead of reading
+ *     out of bounds.
+ */
+#ifndef TMM_GB300_TMM_H
+#define TMM_GB300_TMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define TMM_API __attribute__((visibility("default")))
+#else
+#define TMM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TMM_OK = 0,
+    TMM_ERR_INVALID_ARG = -1, /* a host-side argument check failed */
+    TMM_ERR_UNSUPPORTED = -2, /* valid request this build cannot serve */
+    TMM_ERR_CUDA = -3,        /* a CUDA runtime call failed (see tmm_last_cuda_error) */
+    TMM_ERR_TIMEOUT = -4,     /* a device-side iteration limit was hit */
+    TMM_ERR_NOMEM = -5        /* workspace too small / host allocation failed */
+} tmm_status;
+
+typedef enum { TMM_F64 = 0, TMM_F32 = 1 } tmm_prec;
+
+/* Polarisation bits of tmm_problem.pol_mask; outputs store s before p. */
+#define TMM_POL_S 1u
+#define TMM_POL_P 2u
+
+/*
+ * One batched problem: S stacks, each with up to L_max finite layers,
+ * evaluated on an n_lambda x n_theta grid for the polarisations in pol_mask.
+ *
+ * The complex index of medium j of stack s at wavelength l comes from exactly
+ * one of two sources (index assembly; Sec. 3, coh_tmm_fast / _disp, and the
+ * material matrix I of Sec. 5):
+ *   direct:    n_direct != NULL.  n_direct_per_lambda = 1: complex
+ *              [S][L_max+2][n_lambda]; = 0: complex [S][L_max+2] (no
+ *              dispersion).  mat_table, mat_idx must be NULL.
+ *   gathered:  mat_table complex [n_materials][n_lambda] and mat_idx int32
+ *              [S][L_max+2] (device); n[s][j][l] = mat_table[mat_idx[s][j]][l].
+ * Media rows hold 0 (injection), 1..L_s (finite layers) and L_s+1
+ * (outcoupling); Im(n_0) must be 0.
+ *   d            device [S][L_max]: thickness of finite layer j at d[s][j-1].
+ *   L_per_stack  device int32 [S] or NULL.  NULL: every stack has L_max
+ *                layers.  Otherwise stack s has L_s layers (0 <= L_s <=
+ *                L_max); its rows past L_s+1 and thicknesses past L_s are
+ *                never read.
+ *   theta        device [n_theta], radians in medium 0.
+ *   lambda       device [n_lambda], vacuum wavelength in nm.
+ */
+typedef struct {
+    int32_t S, L_max, n_lambda, n_theta;
+    uint32_t pol_mask; /* TMM_POL_S | TMM_POL_P */
+    int32_t prec;      /* tmm_prec */
+    const void *n_direct;
+    int32_t n_direct_per_lambda;
+    const void *mat_table;
+    const int32_t *mat_idx;
+    int32_t n_materials;
+    const void *d;
+    const int32_t *L_per_stack;
+    const void *theta;
+    const void *lambda;
+} tmm_problem;
+
+/*
+ * Launch shape (all fields 0 = library default).  One block evaluates one
+ * work item: one stack x tile_lambda wavelengths x tile_theta angles, one
+ * thread per (lambda, theta) pair covering the requested polarisations.
+ *   persistent   0: one block per work item.  1: a persistent grid pulls work
+ *                items from a device counter, longest stacks first (ragged
+ *                batches); needs a workspace (tmm_workspace_size).
+ *   blocks_per_sm  persistent grid size = blocks_per_sm x SM count.
+ *   max_items_per_block  persistent only: a block that has taken this many
+ *                items stops, flags TMM_ERR_TIMEOUT in the workspace and
+ *                returns (0 = no limit beyond the item count).
+ */
+typedef struct {
+    int32_t tile_lambda;
+    int32_t tile_theta;
+    int32_t persistent;
+    int32_t blocks_per_sm;
+    int32_t max_items_per_block;
+} tmm_launch_cfg;
+
+/*
+ * R and T for every (pol, stack, theta, lambda) (Sec. 2, Eqs. 1-6).
+ *   R  device [P][S][n_theta][n_lambda], P = number of bits in pol_mask
+ *   T  same layout, or NULL to skip it
+ * Equivalent to tmm_coh_batched_ex with the default launch shape and no
+ * workspace.
+ */
+TMM_API tmm_status tmm_coh_batched(const tmm_problem *p, void *R, void *T, void *stream);
+
+/*
+ * As tmm_coh_batched with an explicit launch shape (cfg may be NULL).  A
+ * persistent launch needs `workspace` (device, at least the bytes reported by
+ * tmm_workspace_size, 256-byte aligned); the call zeroes what it uses.  The
+ * whole call is a fixed sequence of launches and memsets on `stream`, so it
+ * can be captured in a CUDA graph.
+ */
+TMM_API tmm_status tmm_coh_batched_ex(const tmm_problem *p, const tmm_launch_cfg *cfg,
+                              void *workspace, size_t workspace_bytes, void *R, void *T,
+                              void *stream);
+
+/* Workspace bytes tmm_coh_batched_ex / tmm_coh_grad need for this problem. */
+TMM_API tmm_status tmm_workspace_size(const tmm_problem *p, const tmm_launch_cfg *cfg,
+                              size_t *bytes);
+
+/*
+ * Status a persistent launch recorded in its workspace: TMM_OK or
+ * TMM_ERR_TIMEOUT.  Synchronises `stream`.
+ */
+TMM_API tmm_status tmm_workspace_status(const void *workspace, void *stream);
+
+/*
+ * Per-stack merit and its adjoint gradient (replaces the autograd path of
+ * Sec. 4 / appendix A.3):
+ *   merit[s] = mean over (pol, theta, lambda) of (R - R_target)^2
+ *   dm_dd[s][j-1] = d merit[s] / d d_j                      (1/nm)
+ *   dm_dn[s][j-1] = d merit[s] / d (Delta n_j), where n_j(lambda) ->
+ *                   n_j(lambda) + Delta n_j (a real offset at every lambda);
+ *                   for a non-dispersive index this is d merit / d n_j.
+ * Entries past L_s are written as 0.
+ *   R_target  device [P][n_theta][n_lambda] (shared by every stack)
+ *   merit     device [S]; dm_dd device [S][L_max]; dm_dn device [S][L_max] or NULL
+ *   workspace optional: with a workspace of tmm_workspace_size(p, NULL)
+ *             bytes each stack is split over several blocks and reduced in a
+ *             fixed order in a second pass; with NULL one block covers a
+ *             stack.  Results are deterministic either way.
+ */
+TMM_API tmm_status tmm_coh_grad(const tmm_problem *p, const void *R_target, void *merit,
+                        void *dm_dd, void *dm_dn, void *workspace, size_t workspace_bytes,
+                        void *stream);
+
+/* Short description of a status code (static string). */
+TMM_API const char *tmm_status_string(int status);
+
+/* Message of the last CUDA error this library saw on the calling thread. */
+TMM_API const char *tmm_last_cuda_error(void);
+
+/* Library ABI version (major * 10000 + minor * 100 + patch). */
+TMM_API int32_t tmm_version(void);
+
+/*
+ * Issue-rate probe, not part of the method: runs independent FMA chains in
+ * the working type on every SM and reports the achieved rate.
+ *   flops_per_s  host out: 2 x FMAs per second;  ms  host out: kernel time.
+ * Synchronises `stream`.
+ */
+TMM_API tmm_status tmm_probe_fma_rate(int32_t prec, double *flops_per_s, float *ms, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TMM_GB300_TMM_H */

@@ -1,0 +1,278 @@
+"""Thin ctypes binding of libtmm's C ABI (``include/tmm.h``).
+
+Functions carry the C names and only marshal arguments: torch tensors become
+device pointers, the current torch stream becomes the ``cudaStream_t``.  Every
+step of the computation runs in libtmm's CUDA kernels; there is no CPU path.
+If libtmm.so is missing (not built) every call raises instead of computing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libtmm.so")
+
+TMM_OK = 0
+TMM_ERR_INVALID_ARG = -1
+TMM_ERR_UNSUPPORTED = -2
+TMM_ERR_CUDA = -3
+TMM_ERR_TIMEOUT = -4
+TMM_ERR_NOMEM = -5
+TMM_F64 = 0
+TMM_F32 = 1
+TMM_POL_S = 1
+TMM_POL_P = 2
+
+EXPORTED = ("tmm_coh_batched", "tmm_coh_batched_ex", "tmm_workspace_size", "tmm_workspace_status",
+            "tmm_coh_grad", "tmm_status_string", "tmm_last_cuda_error", "tmm_version",
+            "tmm_probe_fma_rate")
+
+
+class TmmProblem(ctypes.Structure):
+    """Mirror of ``tmm_problem``."""
+    _fields_ = [
+        ("S", ctypes.c_int32), ("L_max", ctypes.c_int32), ("n_lambda", ctypes.c_int32),
+        ("n_theta", ctypes.c_int32), ("pol_mask", ctypes.c_uint32), ("prec", ctypes.c_int32),
+        ("n_direct", ctypes.c_void_p), ("n_direct_per_lambda", ctypes.c_int32),
+        ("mat_table", ctypes.c_void_p), ("mat_idx", ctypes.c_void_p), ("n_materials", ctypes.c_int32),
+        ("d", ctypes.c_void_p), ("L_per_stack", ctypes.c_void_p), ("theta", ctypes.c_void_p),
+        ("lambda_", ctypes.c_void_p),
+    ]
+
+
+class TmmLaunchCfg(ctypes.Structure):
+    """Mirror of ``tmm_launch_cfg``."""
+    _fields_ = [("tile_lambda", ctypes.c_int32), ("tile_theta", ctypes.c_int32),
+                ("persistent", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
+                ("max_items_per_block", ctypes.c_int32)]
+
+
+class TmmError(RuntimeError):
+    def __init__(self, fn, status, detail=""):
+        self.status = status
+        msg = f"{fn} failed: {status} ({status_text(status)})"
+        if detail:
+            msg += f": {detail}"
+        super().__init__(msg)
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load(path: Optional[str] = None):
+    """Load libtmm.so (no device work).  Raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is not None and path is None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"libtmm.so is not built ({p}); run __graft_entry__.build() first")
+        lib = ctypes.CDLL(p)
+        vp, sz = ctypes.c_void_p, ctypes.c_size_t
+        P = ctypes.POINTER(TmmProblem)
+        C = ctypes.POINTER(TmmLaunchCfg)
+        lib.tmm_coh_batched.argtypes = [P, vp, vp, vp]
+        lib.tmm_coh_batched_ex.argtypes = [P, C, vp, sz, vp, vp, vp]
+        lib.tmm_workspace_size.argtypes = [P, C, ctypes.POINTER(sz)]
+        lib.tmm_workspace_status.argtypes = [vp, vp]
+        lib.tmm_coh_grad.argtypes = [P, vp, vp, vp, vp, vp, sz, vp]
+        lib.tmm_status_string.argtypes = [ctypes.c_int]
+        lib.tmm_status_string.restype = ctypes.c_char_p
+        lib.tmm_last_cuda_error.argtypes = []
+        lib.tmm_last_cuda_error.restype = ctypes.c_char_p
+        lib.tmm_version.restype = ctypes.c_int32
+        lib.tmm_probe_fma_rate.argtypes = [ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
+                                           ctypes.POINTER(ctypes.c_float), vp]
+        for name in ("tmm_coh_batched", "tmm_coh_batched_ex", "tmm_workspace_size",
+                     "tmm_workspace_status", "tmm_coh_grad", "tmm_probe_fma_rate"):
+            getattr(lib, name).restype = ctypes.c_int
+        if path is None:
+            _lib = lib
+        return lib
+
+
+def status_text(status: int) -> str:
+    try:
+        return load().tmm_status_string(int(status)).decode()
+    except Exception:  # library missing: plain text
+        return str(status)
+
+
+def _check(fn, status):
+    if status != TMM_OK:
+        detail = load().tmm_last_cuda_error().decode() if status == TMM_ERR_CUDA else ""
+        raise TmmError(fn, status, detail)
+
+
+def _ptr(t) -> Optional[int]:
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("libtmm takes device tensors only")
+    if not t.is_contiguous():
+        raise ValueError("libtmm takes contiguous tensors only")
+    return t.data_ptr()
+
+
+def _stream(stream=None) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+# ---------------------------------------------------------------- problems on the device
+@dataclass
+class DeviceProblem:
+    """A ``tmm_problem`` whose arrays are torch tensors on one CUDA device."""
+
+    prec: int
+    pol_mask: int
+    theta: torch.Tensor
+    lam: torch.Tensor
+    d: torch.Tensor
+    n_direct: Optional[torch.Tensor] = None      # complex, [S][L+2] or [S][L+2][N_lambda]
+    table: Optional[torch.Tensor] = None         # complex [M][N_lambda]
+    mat_idx: Optional[torch.Tensor] = None       # int32 [S][L+2]
+    L_per_stack: Optional[torch.Tensor] = None   # int32 [S]
+
+    @property
+    def real_dtype(self):
+        return torch.float64 if self.prec == TMM_F64 else torch.float32
+
+    @property
+    def S(self):
+        return int(self.d.shape[0])
+
+    @property
+    def L_max(self):
+        return int(self.d.shape[1])
+
+    @property
+    def n_pol(self):
+        return bin(self.pol_mask).count("1")
+
+    def struct(self) -> TmmProblem:
+        p = TmmProblem()
+        p.S, p.L_max = self.S, self.L_max
+        p.n_lambda, p.n_theta = int(self.lam.shape[0]), int(self.theta.shape[0])
+        p.pol_mask, p.prec = self.pol_mask, self.prec
+        if self.n_direct is not None:
+            p.n_direct = _ptr(self.n_direct)
+            p.n_direct_per_lambda = 1 if self.n_direct.dim() == 3 else 0
+        else:
+            p.mat_table, p.mat_idx = _ptr(self.table), _ptr(self.mat_idx)
+            p.n_materials = int(self.table.shape[0])
+        p.d, p.theta, p.lambda_ = _ptr(self.d), _ptr(self.theta), _ptr(self.lam)
+        p.L_per_stack = _ptr(self.L_per_stack)
+        return p
+
+    def out_shape(self):
+        return (self.n_pol, self.S, int(self.theta.shape[0]), int(self.lam.shape[0]))
+
+    def empty_out(self):
+        return torch.empty(self.out_shape(), dtype=self.real_dtype, device=self.d.device)
+
+
+def pol_mask_of(pols: str) -> int:
+    return (TMM_POL_S if "s" in pols else 0) | (TMM_POL_P if "p" in pols else 0)
+
+
+def to_device(w, prec="f64", device="cuda", pols=None) -> DeviceProblem:
+    """Upload a ``workloads.Workload`` (numpy arrays) as a DeviceProblem."""
+    pr = TMM_F64 if prec in ("f64", TMM_F64) else TMM_F32
+    rd = torch.float64 if pr == TMM_F64 else torch.float32
+    cd = torch.complex128 if pr == TMM_F64 else torch.complex64
+    t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a)).to(device=device, dtype=dt).contiguous()
+    return DeviceProblem(
+        prec=pr, pol_mask=pol_mask_of(pols or w.pols), theta=t(w.theta, rd), lam=t(w.lam, rd), d=t(w.d, rd),
+        n_direct=None if w.n_direct is None else t(w.n_direct, cd),
+        table=None if w.table is None else t(w.table, cd),
+        mat_idx=None if w.mat_idx is None else t(w.mat_idx, torch.int32),
+        L_per_stack=None if w.L_per_stack is None else t(w.L_per_stack, torch.int32))
+
+
+def launch_cfg(tile_lambda=0, tile_theta=0, persistent=0, blocks_per_sm=0, max_items_per_block=0):
+    return TmmLaunchCfg(tile_lambda, tile_theta, persistent, blocks_per_sm, max_items_per_block)
+
+
+# ---------------------------------------------------------------- the C entry points
+def tmm_coh_batched(prob: DeviceProblem, R: torch.Tensor, T: Optional[torch.Tensor] = None, stream=None):
+    s = prob.struct()
+    _check("tmm_coh_batched", load().tmm_coh_batched(ctypes.byref(s), _ptr(R), _ptr(T), _stream(stream)))
+
+
+def tmm_workspace_size(prob: DeviceProblem, cfg: Optional[TmmLaunchCfg] = None) -> int:
+    s = prob.struct()
+    n = ctypes.c_size_t(0)
+    _check("tmm_workspace_size", load().tmm_workspace_size(ctypes.byref(s), ctypes.byref(cfg) if cfg else None,
+                                                           ctypes.byref(n)))
+    return int(n.value)
+
+
+def tmm_coh_batched_ex(prob: DeviceProblem, cfg: Optional[TmmLaunchCfg], workspace: Optional[torch.Tensor],
+                       R: torch.Tensor, T: Optional[torch.Tensor] = None, stream=None):
+    s = prob.struct()
+    ws_bytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
+    _check("tmm_coh_batched_ex", load().tmm_coh_batched_ex(ctypes.byref(s), ctypes.byref(cfg) if cfg else None,
+                                                           _ptr(workspace), ws_bytes, _ptr(R), _ptr(T),
+                                                           _stream(stream)))
+
+
+def tmm_workspace_status(workspace: torch.Tensor, stream=None) -> int:
+    """TMM_OK or TMM_ERR_TIMEOUT recorded by a persistent launch (synchronises)."""
+    st = load().tmm_workspace_status(_ptr(workspace), _stream(stream))
+    if st not in (TMM_OK, TMM_ERR_TIMEOUT):
+        _check("tmm_workspace_status", st)
+    return st
+
+
+def tmm_coh_grad(prob: DeviceProblem, R_target: torch.Tensor, merit: torch.Tensor, dm_dd: torch.Tensor,
+                 dm_dn: Optional[torch.Tensor] = None, workspace: Optional[torch.Tensor] = None, stream=None):
+    s = prob.struct()
+    ws_bytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
+    _check("tmm_coh_grad", load().tmm_coh_grad(ctypes.byref(s), _ptr(R_target), _ptr(merit), _ptr(dm_dd),
+                                               _ptr(dm_dn), _ptr(workspace), ws_bytes, _stream(stream)))
+
+
+def tmm_probe_fma_rate(prec: int, stream=None):
+    """(flops per second, kernel ms) of the FMA issue-rate probe."""
+    f = ctypes.c_double(0)
+    ms = ctypes.c_float(0)
+    _check("tmm_probe_fma_rate", load().tmm_probe_fma_rate(int(prec), ctypes.byref(f), ctypes.byref(ms),
+                                                           _stream(stream)))
+    return f.value, ms.value
+
+
+def tmm_version() -> int:
+    return int(load().tmm_version())
+
+
+def alloc_workspace(nbytes: int, device="cuda") -> Optional[torch.Tensor]:
+    """A 256-byte aligned device buffer of at least nbytes (None for 0)."""
+    if nbytes <= 0:
+        return None
+    return torch.empty((nbytes + 255) // 256 * 256, dtype=torch.uint8, device=device)
+
+
+# ---------------------------------------------------------------- convenience
+def coh_tmm(prob: DeviceProblem, with_T=True, cfg: Optional[TmmLaunchCfg] = None, stream=None):
+    """R (and T) as [P][S][N_theta][N_lambda] device tensors for a DeviceProblem."""
+    R = prob.empty_out()
+    T = prob.empty_out() if with_T else None
+    if cfg is not None and cfg.persistent:
+        ws = alloc_workspace(tmm_workspace_size(prob, cfg), R.device)
+        tmm_coh_batched_ex(prob, cfg, ws, R, T, stream)
+    elif cfg is not None:
+        tmm_coh_batched_ex(prob, cfg, None, R, T, stream)
+    else:
+        tmm_coh_batched(prob, R, T, stream)
+    return R, T

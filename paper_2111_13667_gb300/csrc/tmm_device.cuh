@@ -1,0 +1,190 @@
+// tmm_device.cuh -- device-side building blocks of the transfer-matrix kernels.
+//
+// Working-precision helpers (complex arithmetic, the forward root of
+// cos(theta_j), the layer phase factors and exact power-of-two rescaling),
+// the per-(medium, wavelength) shared-memory stage and the index assembly that
+// fills it.  Everything here is written for sm_103a and shared by the forward,
+// ragged and adjoint kernels.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/tmm.h"
+
+namespace tmm {
+
+// Largest Im(delta) of a layer phase (opaque-layer clamp), in turns: 35 / (2 pi).
+constexpr double kImDeltaMax = 35.0;
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+constexpr double kLog2e = 1.4426950408889634073599246810019;
+
+template <typename R> struct Cx { R x, y; };
+
+template <typename R> __device__ __forceinline__ Cx<R> cx(R x, R y) { return Cx<R>{x, y}; }
+template <typename R> __device__ __forceinline__ Cx<R> operator+(Cx<R> a, Cx<R> b) { return {a.x + b.x, a.y + b.y}; }
+template <typename R> __device__ __forceinline__ Cx<R> operator-(Cx<R> a, Cx<R> b) { return {a.x - b.x, a.y - b.y}; }
+template <typename R> __device__ __forceinline__ Cx<R> operator-(Cx<R> a) { return {-a.x, -a.y}; }
+template <typename R> __device__ __forceinline__ Cx<R> cmul(Cx<R> a, Cx<R> b)
+{
+    return {fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x)};
+}
+// a * b + c
+template <typename R> __device__ __forceinline__ Cx<R> cfma(Cx<R> a, Cx<R> b, Cx<R> c)
+{
+    return {fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y))};
+}
+template <typename R> __device__ __forceinline__ Cx<R> conj(Cx<R> a) { return {a.x, -a.y}; }
+template <typename R> __device__ __forceinline__ R abs2(Cx<R> a) { return fma(a.x, a.x, a.y * a.y); }
+template <typename R> __device__ __forceinline__ Cx<R> scale(R s, Cx<R> a) { return {s * a.x, s * a.y}; }
+// i * a
+template <typename R> __device__ __forceinline__ Cx<R> mul_i(Cx<R> a) { return {-a.y, a.x}; }
+
+// ---------------------------------------------------------------- precision-specific math
+__device__ __forceinline__ float rsqrt_w(float v) { return rsqrtf(v); }
+__device__ __forceinline__ double rsqrt_w(double v) { return rsqrt(v); }
+__device__ __forceinline__ float rint_w(float v) { return rintf(v); }
+__device__ __forceinline__ double rint_w(double v) { return rint(v); }
+// sin and cos of 2 pi f for |f| <= 1/2.
+__device__ __forceinline__ void sincos_turn(float f, float *s, float *c) { __sincosf(6.2831853f * f, s, c); }
+__device__ __forceinline__ void sincos_turn(double f, double *s, double *c) { sincospi(2.0 * f, s, c); }
+// exp(2 pi y) and exp(-2 pi y).
+__device__ __forceinline__ void exp_pm_turn(float y, float *ep, float *em)
+{
+    const float k = (float)(kTwoPi * kLog2e);
+    *ep = exp2f(k * y);
+    *em = exp2f(-k * y);
+}
+__device__ __forceinline__ void exp_pm_turn(double y, double *ep, double *em)
+{
+    *ep = exp(kTwoPi * y);
+    *em = exp(-kTwoPi * y);
+}
+__device__ __forceinline__ float sin_w(float v) { return sinf(v); }
+__device__ __forceinline__ double sin_w(double v) { return sin(v); }
+template <typename R> __device__ __forceinline__ R eps_w();
+template <> __device__ __forceinline__ float eps_w<float>() { return 1.1920929e-7f; }
+template <> __device__ __forceinline__ double eps_w<double>() { return 2.220446049250313e-16; }
+template <typename R> __device__ __forceinline__ R nan_w();
+template <> __device__ __forceinline__ float nan_w<float>() { return __int_as_float(0x7fc00000); }
+template <> __device__ __forceinline__ double nan_w<double>() { return __longlong_as_double(0x7ff8000000000000LL); }
+
+// Exact rescaling by powers of two.  `exponent_of(m)` is floor(log2 m) for a
+// normal positive m (-127 / -1023 for zero and subnormals); `pow2_neg(e)` is
+// 2^-e for e inside the normal range.
+__device__ __forceinline__ int exponent_of(float m) { return ((__float_as_int(m) >> 23) & 0xff) - 127; }
+__device__ __forceinline__ int exponent_of(double m) { return (int)((__double_as_longlong(m) >> 52) & 0x7ff) - 1023; }
+template <typename R> __device__ __forceinline__ R pow2_neg(int e);
+template <> __device__ __forceinline__ float pow2_neg<float>(int e) { return __int_as_float((127 - e) << 23); }
+template <> __device__ __forceinline__ double pow2_neg<double>(int e) { return __longlong_as_double((long long)(1023 - e) << 52); }
+__device__ __forceinline__ float ldexp_w(float v, int e) { return ldexpf(v, e); }
+__device__ __forceinline__ double ldexp_w(double v, int e) { return ldexp(v, e); }
+
+// Keep a positive running product m in [1, 2): m <- m 2^-k, e <- e + k.
+template <typename R> __device__ __forceinline__ void renorm_scalar(R &m, int &e)
+{
+    const int k = exponent_of(m);
+    m *= pow2_neg<R>(k);
+    e += k;
+}
+
+// Rescale the amplitude pair (x0, x1) so its largest component is in [1, 2).
+template <typename R> __device__ __forceinline__ void renorm_pair(Cx<R> &x0, Cx<R> &x1, int &e)
+{
+    const R m = fmax(fmax(fabs(x0.x), fabs(x0.y)), fmax(fabs(x1.x), fabs(x1.y)));
+    const int k = exponent_of(m);
+    const R s = pow2_neg<R>(k);
+    x0 = scale(s, x0);
+    x1 = scale(s, x1);
+    e += k;
+}
+
+// q = n cos(theta) = sqrt(n^2 - beta^2), the forward root (see tmm.h); also
+// returns |q|^2 = |z|.  z = 0 gives q = 0.
+template <typename R> __device__ __forceinline__ Cx<R> forward_root(Cx<R> z, R *absz_out)
+{
+    const R hyp = fma(z.x, z.x, z.y * z.y);
+    Cx<R> q = {R(0), R(0)};
+    R absz = R(0);
+    if (hyp > R(0)) {
+        const R rh = rsqrt_w(hyp);
+        absz = hyp * rh;
+        const R u = R(0.5) * (absz + fabs(z.x));
+        const R ru = rsqrt_w(u);
+        const R t = u * ru;             // sqrt(u)
+        const R o = R(0.5) * z.y * ru;  // Im z / (2 sqrt(u))
+        q = z.x >= R(0) ? Cx<R>{t, o} : Cx<R>{fabs(o), copysign(t, z.y)};
+        // principal root has Re >= 0; take the decaying one unless Im q is
+        // zero to rounding (|Im q| <= 100 eps |q|, compared squared)
+        const R tol = R(100) * eps_w<R>();
+        if (q.y < R(0) && q.y * q.y > tol * tol * absz) q = -q;
+    }
+    *absz_out = absz;
+    return q;
+}
+
+// ---------------------------------------------------------------- shared-memory stage
+// Per (medium j, wavelength): n_j^2, 1 / n_j^2, |1 / n_j^2|^2 and d_j / lambda
+// (0 for the two semi-infinite media).  Two arrays keep the loads vectorised.
+template <typename R> struct StageA { R n2x, n2y, in2x, in2y; };
+template <typename R> struct StageB { R ain2, dl; };
+
+template <typename R> __device__ __forceinline__ Cx<R> load_cx(const R *p, long long i)
+{
+    return Cx<R>{p[2 * i], p[2 * i + 1]};
+}
+
+// Index n[s][j][l] of a problem (either source); poison = NaN on a bad index.
+template <typename R>
+__device__ __forceinline__ Cx<R> index_of(const tmm_problem &p, int s, int j, int l)
+{
+    if (p.n_direct) {
+        const R *nd = (const R *)p.n_direct;
+        const long long row = (long long)s * (p.L_max + 2) + j;
+        return p.n_direct_per_lambda ? load_cx(nd, row * p.n_lambda + l) : load_cx(nd, row);
+    }
+    const int m = p.mat_idx[(long long)s * (p.L_max + 2) + j];
+    if (m < 0 || m >= p.n_materials) return Cx<R>{nan_w<R>(), nan_w<R>()};
+    return load_cx((const R *)p.mat_table, (long long)m * p.n_lambda + l);
+}
+
+// Layer count of stack s, or -1 if it is outside [0, L_max].
+__device__ __forceinline__ int layers_of(const tmm_problem &p, int s)
+{
+    if (!p.L_per_stack) return p.L_max;
+    const int L = p.L_per_stack[s];
+    return (L < 0 || L > p.L_max) ? -1 : L;
+}
+
+// Fill the stage for media 0..L+1 of stack s and wavelengths l0..l0+TL-1.
+// Row L+1 is the outcoupling medium (row L_s+1 of the stack's media).
+// n0 receives the (real) injection index per wavelength, NaN if complex.
+template <typename R>
+__device__ __forceinline__ void fill_stage(const tmm_problem &p, int s, int L, int l0, int TL,
+                                           StageA<R> *sa, StageB<R> *sb, R *n0, int tid, int nthr)
+{
+    const R *lam = (const R *)p.lambda;
+    const R *d = (const R *)p.d;
+    const int total = (L + 2) * TL;
+    for (int idx = tid; idx < total; idx += nthr) {
+        const int j = idx / TL, tl = idx - j * TL;
+        const int l = min(l0 + tl, p.n_lambda - 1);
+        Cx<R> n = index_of<R>(p, s, j, l);
+        const Cx<R> n2 = {fma(n.x, n.x, -n.y * n.y), R(2) * n.x * n.y};
+        const R a = abs2(n2);
+        const R ia = R(1) / a;
+        StageA<R> A;
+        A.n2x = n2.x;
+        A.n2y = n2.y;
+        A.in2x = n2.x * ia;
+        A.in2y = -n2.y * ia;
+        StageB<R> B;
+        B.ain2 = ia;  // |1/n^2|^2 = 1 / |n^2|^2
+        B.dl = (j >= 1 && j <= L) ? d[(long long)s * p.L_max + (j - 1)] / lam[l] : R(0);
+        sa[idx] = A;
+        sb[idx] = B;
+        if (j == 0) n0[tl] = (n.y == R(0)) ? n.x : nan_w<R>();
+    }
+}
+
+}  // namespace tmm

@@ -1,0 +1,377 @@
+// tmm_fwd.cu -- forward transfer-matrix kernels: R and T for every
+// (stack, lambda, theta, polarisation) of a batch (arXiv 2111.13667, Sec. 2).
+//
+// Design (sm_103a):
+//   * one thread per (stack, lambda, theta); it carries both polarisations,
+//     which share Snell's law and the layer phase;
+//   * the layer loop runs right to left in registers on the 2-vector
+//     x_j = M_j x_{j+1}, x_{L+1} = (1, 0) -- the first column of the product of
+//     Eq. 4, which is all Eqs. 5-6 need;
+//   * each interface matrix is kept unnormalised, (1/t)[[1,r],[r,1]] times
+//     2a (a = q_j for s, q_j / n_j^2 for p, q = n cos(theta)), so no layer needs
+//     a complex division; the dropped scale factors only enter |t|^2 and are
+//     carried as a product of |q_j|^2 (and |1/n_j^2|^2 for p);
+//   * all running products are rescaled by exact powers of two every layer,
+//     which keeps the FP32 path finite through opaque layers;
+//   * per-(medium, wavelength) data (n^2, 1/n^2, d/lambda) are staged once per
+//     block in shared memory and reused by every angle of the block.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "tmm_device.cuh"
+#include "tmm_internal.h"
+
+namespace tmm {
+
+// Largest block of the forward kernels (threads); keeps 128 registers per thread.
+constexpr int kMaxThreads = 512;
+
+// One (lambda, theta) point of one stack, both polarisations as requested.
+// out = {R_s, T_s, R_p, T_p}.
+template <typename R, int POL>
+__device__ __forceinline__ void eval_point(const StageA<R> *__restrict__ sa, const StageB<R> *__restrict__ sb,
+                                           int TL, int tl, int L, R n0, R sin_theta, R out[4])
+{
+    const R beta = n0 * sin_theta;
+    const R beta2 = beta * beta;
+    const R yi_max = R(kImDeltaMax / kTwoPi);
+
+    StageA<R> A = sa[(L + 1) * TL + tl];
+    StageB<R> B = sb[(L + 1) * TL + tl];
+    R absz;
+    Cx<R> q_nx = forward_root(Cx<R>{A.n2x - beta2, A.n2y}, &absz);
+    const Cx<R> q_out = q_nx, n2_out = {A.n2x, A.n2y};
+    Cx<R> g_nx = cmul(q_nx, Cx<R>{A.in2x, A.in2y});
+    R Ps = R(1), Pp = B.ain2;
+    int eP = 0, ePp = 0;
+    renorm_scalar(Pp, ePp);
+    Cx<R> s0 = {R(1), R(0)}, s1 = {R(0), R(0)}, p0 = {R(1), R(0)}, p1 = {R(0), R(0)};
+    int es = 0, ep = 0;
+
+    for (int j = L; j >= 1; --j) {
+        A = sa[j * TL + tl];
+        B = sb[j * TL + tl];
+        const Cx<R> q = forward_root(Cx<R>{A.n2x - beta2, A.n2y}, &absz);
+        Ps *= absz;
+        renorm_scalar(Ps, eP);
+        // layer phase in turns: delta / (2 pi) = (d / lambda) q, Im clamped
+        const R yr = B.dl * q.x;
+        const R yi = fmin(B.dl * q.y, yi_max);
+        R sn, cs, Ep, Em;
+        sincos_turn(yr - rint_w(yr), &sn, &cs);
+        exp_pm_turn(yi, &Ep, &Em);
+        const Cx<R> emi = {Ep * cs, -Ep * sn};  // e^{-i delta}
+        const Cx<R> epi = {Em * cs, Em * sn};   // e^{+i delta}
+        if (POL & 1) {
+            const Cx<R> a = q + q_nx, b = q - q_nx;
+            const Cx<R> u0 = cfma(a, s0, cmul(b, s1));
+            const Cx<R> u1 = cfma(b, s0, cmul(a, s1));
+            s0 = cmul(emi, u0);
+            s1 = cmul(epi, u1);
+            renorm_pair(s0, s1, es);
+        }
+        if (POL & 2) {
+            Pp *= B.ain2;
+            renorm_scalar(Pp, ePp);
+            const Cx<R> g = cmul(q, Cx<R>{A.in2x, A.in2y});
+            const Cx<R> a = g + g_nx, b = g - g_nx;
+            const Cx<R> u0 = cfma(a, p0, cmul(b, p1));
+            const Cx<R> u1 = cfma(b, p0, cmul(a, p1));
+            p0 = cmul(emi, u0);
+            p1 = cmul(epi, u1);
+            renorm_pair(p0, p1, ep);
+            g_nx = g;
+        }
+        q_nx = q;
+    }
+    // interface 0 -> 1 (the injection medium carries no phase)
+    A = sa[tl];
+    const Cx<R> q0 = forward_root(Cx<R>{A.n2x - beta2, A.n2y}, &absz);
+    Ps *= absz;
+    const int e4 = 2 * (L + 1);  // the factors 2 of every 2a
+    if (POL & 1) {
+        const Cx<R> a = q0 + q_nx, b = q0 - q_nx;
+        const Cx<R> x0 = cfma(a, s0, cmul(b, s1));
+        const Cx<R> x1 = cfma(b, s0, cmul(a, s1));
+        const R ax0 = abs2(x0);
+        R Rv = abs2(x1) / ax0;
+        R Tv = q_out.x / q0.x * ldexp_w(Ps / ax0, e4 + eP - 2 * es);
+        if (q0.x == R(0) && q0.y == R(0)) { Rv = R(1); Tv = R(0); }
+        out[0] = Rv;
+        out[1] = Tv;
+    }
+    if (POL & 2) {
+        const Cx<R> g0 = cmul(q0, Cx<R>{A.in2x, A.in2y});
+        const Cx<R> a = g0 + g_nx, b = g0 - g_nx;
+        const Cx<R> x0 = cfma(a, p0, cmul(b, p1));
+        const Cx<R> x1 = cfma(b, p0, cmul(a, p1));
+        const R ax0 = abs2(x0);
+        R Rv = abs2(x1) / ax0;
+        const R num = cmul(n2_out, conj(q_out)).x;
+        const R den = cmul(Cx<R>{A.n2x, A.n2y}, conj(q0)).x;
+        R Tv = num / den * ldexp_w(Ps * Pp / ax0, e4 + eP + ePp - 2 * ep);
+        if (q0.x == R(0) && q0.y == R(0)) { Rv = R(1); Tv = R(0); }
+        out[2] = Rv;
+        out[3] = Tv;
+    }
+}
+
+// Stage one work item and evaluate it.  Every thread of the block calls this;
+// it contains two barriers.
+template <typename R, int POL, bool WITH_T>
+__device__ __forceinline__ void run_item(const tmm_problem &p, int s, int lt, int tt, int TL, int TT,
+                                         unsigned char *smem, R *__restrict__ Rout, R *__restrict__ Tout)
+{
+    StageA<R> *sa = reinterpret_cast<StageA<R> *>(smem);
+    StageB<R> *sb = reinterpret_cast<StageB<R> *>(sa + (size_t)(p.L_max + 2) * TL);
+    R *n0s = reinterpret_cast<R *>(sb + (size_t)(p.L_max + 2) * TL);
+
+    const int tid = threadIdx.y * TL + threadIdx.x;
+    const int nthr = TL * TT;
+    const int L = layers_of(p, s);
+    const int l0 = lt * TL, t0 = tt * TT;
+    if (L >= 0) fill_stage<R>(p, s, L, l0, TL, sa, sb, n0s, tid, nthr);
+    __syncthreads();
+
+    const int tl = threadIdx.x, l = l0 + tl, a = t0 + threadIdx.y;
+    if (l < p.n_lambda && a < p.n_theta) {
+        R out[4];
+        if (L >= 0) {
+            const R th = ((const R *)p.theta)[a];
+            eval_point<R, POL>(sa, sb, TL, tl, L, n0s[tl], sin_w(th), out);
+        } else {
+            out[0] = out[1] = out[2] = out[3] = nan_w<R>();
+        }
+        const long long plane = (long long)p.S * p.n_theta * p.n_lambda;
+        const long long o = ((long long)s * p.n_theta + a) * p.n_lambda + l;
+        int pi = 0;
+        if (POL & 1) {
+            Rout[o] = out[0];
+            if (WITH_T) Tout[o] = out[1];
+            ++pi;
+        }
+        if (POL & 2) {
+            Rout[pi * plane + o] = out[2];
+            if (WITH_T) Tout[pi * plane + o] = out[3];
+        }
+    }
+    __syncthreads();
+}
+
+template <typename R, int POL, bool WITH_T>
+__global__ void __launch_bounds__(kMaxThreads) tmm_fwd_kernel(const tmm_problem p, int TL, int TT, int n_lt, int n_tt,
+                                                       R *__restrict__ Rout, R *__restrict__ Tout)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const long long item = blockIdx.x;
+    const int per_stack = n_lt * n_tt;
+    const int s = (int)(item / per_stack);
+    const int r = (int)(item - (long long)s * per_stack);
+    run_item<R, POL, WITH_T>(p, s, r / n_tt, r % n_tt, TL, TT, smem, Rout, Tout);
+}
+
+// Persistent variant: blocks pull work items from `counter`; item k belongs to
+// stack order[k / per_stack] (longest stacks first), tile k % per_stack.
+template <typename R, int POL, bool WITH_T>
+__global__ void __launch_bounds__(kMaxThreads) tmm_fwd_persistent(const tmm_problem p, int TL, int TT, int n_lt, int n_tt,
+                                                           const int *__restrict__ order, unsigned int *counter,
+                                                           int *err, unsigned int n_items, int max_items,
+                                                           R *__restrict__ Rout, R *__restrict__ Tout)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ unsigned int item_sh;
+    const int per_stack = n_lt * n_tt;
+    int taken = 0;
+    for (;;) {
+        if (threadIdx.x == 0 && threadIdx.y == 0) item_sh = atomicAdd(counter, 1u);
+        __syncthreads();
+        const unsigned int item = item_sh;
+        __syncthreads();  // item_sh is rewritten on the next pass
+        if (item >= n_items) break;
+        if (max_items > 0 && ++taken > max_items) {
+            if (threadIdx.x == 0 && threadIdx.y == 0) atomicExch(err, 1);
+            break;
+        }
+        const int k = (int)(item / per_stack);
+        const int r = (int)(item - (unsigned int)k * per_stack);
+        run_item<R, POL, WITH_T>(p, order[k], r / n_tt, r % n_tt, TL, TT, smem, Rout, Tout);
+    }
+}
+
+// ---------------------------------------------------------------- longest-first ordering
+// Counting sort of the stacks by layer count, descending; a bad count goes last.
+__global__ void count_lengths(const int *__restrict__ Ls, int S, int L_max, int *counts)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    const int L = Ls[s];
+    const int bucket = (L < 0 || L > L_max) ? L_max + 1 : L_max - L;
+    atomicAdd(&counts[bucket], 1);
+}
+
+__global__ void scan_lengths(const int *__restrict__ counts, int n_buckets, int *offsets)
+{
+    if (threadIdx.x != 0) return;
+    int acc = 0;
+    for (int b = 0; b < n_buckets; ++b) {
+        offsets[b] = acc;
+        acc += counts[b];
+    }
+}
+
+__global__ void scatter_lengths(const int *__restrict__ Ls, int S, int L_max, int *offsets, int *order)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    const int L = Ls[s];
+    const int bucket = (L < 0 || L > L_max) ? L_max + 1 : L_max - L;
+    order[atomicAdd(&offsets[bucket], 1)] = s;
+}
+
+__global__ void iota_order(int S, int *order)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < S) order[s] = s;
+}
+
+// ---------------------------------------------------------------- host side
+static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+PersistentWs persistent_ws_layout(const tmm_problem *p)
+{
+    PersistentWs w;
+    w.counter = 0;
+    w.err = 4;
+    w.counts = 256;
+    w.offsets = align_up(w.counts + sizeof(int) * (size_t)(p->L_max + 2), 256);
+    w.order = align_up(w.offsets + sizeof(int) * (size_t)(p->L_max + 2), 256);
+    w.total = align_up(w.order + sizeof(int) * (size_t)p->S, 256);
+    return w;
+}
+
+static size_t stage_bytes(const tmm_problem *p, int TL)
+{
+    const size_t r = real_size(p->prec);
+    return (size_t)(p->L_max + 2) * TL * (6 * r) + (size_t)TL * r;
+}
+
+tmm_status choose_tile(const tmm_problem *p, const tmm_launch_cfg *cfg, Tile *t)
+{
+    DeviceInfo di;
+    tmm_status st = device_info(&di);
+    if (st != TMM_OK) return st;
+    int TT = cfg && cfg->tile_theta > 0 ? cfg->tile_theta : std::min(p->n_theta, 32);
+    int TL = cfg && cfg->tile_lambda > 0 ? cfg->tile_lambda : 0;
+    if (TL == 0) {
+        TL = 1;
+        while (TL * TT < 256 && TL * 2 * TT <= kMaxThreads) TL *= 2;
+        while (TL > 1 && TL / 2 >= p->n_lambda) TL /= 2;
+        while (TL > 1 && stage_bytes(p, TL) > (size_t)di.max_smem_optin) TL /= 2;
+    }
+    if (TL < 1 || TT < 1 || TL * TT > kMaxThreads) return TMM_ERR_INVALID_ARG;
+    t->TL = TL;
+    t->TT = TT;
+    t->n_lt = (p->n_lambda + TL - 1) / TL;
+    t->n_tt = (p->n_theta + TT - 1) / TT;
+    t->n_items = (long long)p->S * t->n_lt * t->n_tt;
+    t->smem = stage_bytes(p, TL);
+    if (t->smem > (size_t)di.max_smem_optin) return TMM_ERR_UNSUPPORTED;
+    return TMM_OK;
+}
+
+template <typename Kernel> static tmm_status allow_smem(Kernel k, size_t bytes)
+{
+    if (bytes <= 48 * 1024) return TMM_OK;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    return e == cudaSuccess ? TMM_OK : cuda_fail(e);
+}
+
+template <typename R, int POL, bool WITH_T>
+static tmm_status launch_typed(const tmm_problem *p, const tmm_launch_cfg *cfg, const Tile &t, void *ws,
+                               R *Rout, R *Tout, cudaStream_t st)
+{
+    const dim3 block(t.TL, t.TT);
+    const bool persistent = cfg && cfg->persistent;
+    if (!persistent) {
+        auto k = tmm_fwd_kernel<R, POL, WITH_T>;
+        tmm_status s = allow_smem(k, t.smem);
+        if (s != TMM_OK) return s;
+        if (t.n_items > 0x7fffffffLL) return TMM_ERR_UNSUPPORTED;
+        if (t.n_items == 0) return TMM_OK;
+        k<<<(unsigned)t.n_items, block, t.smem, st>>>(*p, t.TL, t.TT, t.n_lt, t.n_tt, Rout, Tout);
+        return check_launch();
+    }
+    auto k = tmm_fwd_persistent<R, POL, WITH_T>;
+    tmm_status s = allow_smem(k, t.smem);
+    if (s != TMM_OK) return s;
+    if (t.n_items > 0xffffffffLL) return TMM_ERR_UNSUPPORTED;
+    const PersistentWs w = persistent_ws_layout(p);
+    unsigned char *base = static_cast<unsigned char *>(ws);
+    cudaError_t e = cudaMemsetAsync(base, 0, w.order, st);  // counter, err, counts, offsets
+    if (e != cudaSuccess) return cuda_fail(e);
+    int *order = reinterpret_cast<int *>(base + w.order);
+    const int nb = (p->S + 255) / 256;
+    if (p->S > 0) {
+        if (p->L_per_stack) {
+            int *counts = reinterpret_cast<int *>(base + w.counts);
+            int *offsets = reinterpret_cast<int *>(base + w.offsets);
+            count_lengths<<<nb, 256, 0, st>>>(p->L_per_stack, p->S, p->L_max, counts);
+            scan_lengths<<<1, 32, 0, st>>>(counts, p->L_max + 2, offsets);
+            scatter_lengths<<<nb, 256, 0, st>>>(p->L_per_stack, p->S, p->L_max, offsets, order);
+        } else {
+            iota_order<<<nb, 256, 0, st>>>(p->S, order);
+        }
+        tmm_status cs = check_launch();
+        if (cs != TMM_OK) return cs;
+    }
+    if (t.n_items == 0) return TMM_OK;
+    DeviceInfo di;
+    s = device_info(&di);
+    if (s != TMM_OK) return s;
+    int per_sm = cfg->blocks_per_sm;
+    if (per_sm <= 0) {
+        cudaError_t oe = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, t.TL * t.TT, t.smem);
+        if (oe != cudaSuccess) return cuda_fail(oe);
+        per_sm = std::max(per_sm, 1);
+    }
+    long long grid = (long long)per_sm * di.sms;
+    grid = std::min(grid, t.n_items);
+    k<<<(unsigned)grid, block, t.smem, st>>>(*p, t.TL, t.TT, t.n_lt, t.n_tt, order,
+                                             reinterpret_cast<unsigned int *>(base + w.counter),
+                                             reinterpret_cast<int *>(base + w.err), (unsigned)t.n_items,
+                                             cfg->max_items_per_block, Rout, Tout);
+    return check_launch();
+}
+
+template <typename R>
+static tmm_status launch_prec(const tmm_problem *p, const tmm_launch_cfg *cfg, const Tile &t, void *ws, void *R_,
+                              void *T_, cudaStream_t st)
+{
+    R *Ro = static_cast<R *>(R_);
+    R *To = static_cast<R *>(T_);
+    const bool wt = To != nullptr;
+    switch (p->pol_mask) {
+    case 1: return wt ? launch_typed<R, 1, true>(p, cfg, t, ws, Ro, To, st) : launch_typed<R, 1, false>(p, cfg, t, ws, Ro, To, st);
+    case 2: return wt ? launch_typed<R, 2, true>(p, cfg, t, ws, Ro, To, st) : launch_typed<R, 2, false>(p, cfg, t, ws, Ro, To, st);
+    case 3: return wt ? launch_typed<R, 3, true>(p, cfg, t, ws, Ro, To, st) : launch_typed<R, 3, false>(p, cfg, t, ws, Ro, To, st);
+    default: return TMM_ERR_INVALID_ARG;
+    }
+}
+
+tmm_status launch_forward(const tmm_problem *p, const tmm_launch_cfg *cfg, void *ws, size_t ws_bytes, void *R,
+                          void *T, cudaStream_t st)
+{
+    Tile t;
+    tmm_status s = choose_tile(p, cfg, &t);
+    if (s != TMM_OK) return s;
+    if (cfg && cfg->persistent) {
+        if (!ws) return TMM_ERR_INVALID_ARG;
+        if (ws_bytes < persistent_ws_layout(p).total) return TMM_ERR_NOMEM;
+        if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return TMM_ERR_INVALID_ARG;
+    }
+    return p->prec == TMM_F64 ? launch_prec<double>(p, cfg, t, ws, R, T, st)
+                              : launch_prec<float>(p, cfg, t, ws, R, T, st);
+}
+
+}  // namespace tmm

@@ -1,0 +1,54 @@
+// tmm_internal.h -- host-side declarations shared by the translation units of
+// libtmm (launchers behind the C ABI).  Not part of the public interface.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/tmm.h"
+
+namespace tmm {
+
+struct Tile {
+    int TL = 0, TT = 0;        // wavelengths x angles per work item
+    int n_lt = 0, n_tt = 0;    // tiles along lambda / theta
+    long long n_items = 0;     // S * n_lt * n_tt
+    size_t smem = 0;           // dynamic shared memory per block
+};
+
+// Device facts cached per device (SM count, opt-in shared memory limit).
+struct DeviceInfo {
+    int sms = 0;
+    int max_smem_optin = 0;
+};
+tmm_status device_info(DeviceInfo *out);
+
+int npol(uint32_t pol_mask);
+size_t real_size(int prec);
+
+// Host-side validation of a problem (sizes, pointers, modes).
+tmm_status validate_problem(const tmm_problem *p);
+
+// Tile choice for a forward launch (cfg fields of 0 take defaults).
+tmm_status choose_tile(const tmm_problem *p, const tmm_launch_cfg *cfg, Tile *t);
+
+// Workspace layout of a persistent forward launch.
+struct PersistentWs {
+    size_t counter = 0, err = 0, counts = 0, offsets = 0, order = 0, total = 0;
+};
+PersistentWs persistent_ws_layout(const tmm_problem *p);
+
+tmm_status launch_forward(const tmm_problem *p, const tmm_launch_cfg *cfg, void *ws, size_t ws_bytes,
+                          void *R, void *T, cudaStream_t st);
+
+// Adjoint / merit.
+size_t grad_ws_bytes(const tmm_problem *p);
+tmm_status launch_grad(const tmm_problem *p, const void *R_target, void *merit, void *dm_dd,
+                       void *dm_dn, void *ws, size_t ws_bytes, cudaStream_t st);
+
+// Record a CUDA error for tmm_last_cuda_error and map it to a status.
+tmm_status cuda_fail(cudaError_t e);
+tmm_status check_launch();
+
+}  // namespace tmm

@@ -1,0 +1,130 @@
+"""CPU-side checks of the C-ABI library: it builds, loads, exports every symbol
+``include/tmm.h`` declares, its structs match the header's layout, and the
+host-side argument checks reject bad problems before touching a device."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2111_13667_gb300 import build
+    build.build()
+    from paper_2111_13667_gb300 import abi
+    return abi.load()
+
+
+def declared_symbols():
+    out = []
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if h.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", h)).read()
+            out += re.findall(r"TMM_API\s+[\w\s\*]+?\b(\w+)\s*\(", txt)
+    return out
+
+
+def test_every_declared_symbol_is_exported(lib):
+    syms = declared_symbols()
+    assert "tmm_coh_batched" in syms and "tmm_coh_grad" in syms
+    for s in syms:
+        assert hasattr(lib, s), s
+    nm = subprocess.run(["nm", "-D", "--defined-only", os.path.join(ROOT, "paper_2111_13667_gb300", "libtmm.so")],
+                        capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r" T (tmm_\w+)", nm))
+    assert set(syms) <= exported
+    from paper_2111_13667_gb300 import abi
+    assert set(abi.EXPORTED) <= set(syms)
+
+
+def test_struct_layout_matches_header(tmp_path, lib):
+    from paper_2111_13667_gb300.abi import TmmLaunchCfg, TmmProblem
+    src = tmp_path / "layout.c"
+    src.write_text("""
+#include <stdio.h>
+#include <stddef.h>
+#include "tmm.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(tmm_problem), offsetof(tmm_problem, n_direct),
+         offsetof(tmm_problem, mat_table), offsetof(tmm_problem, n_materials), offsetof(tmm_problem, d),
+         offsetof(tmm_problem, lambda), sizeof(tmm_launch_cfg), offsetof(tmm_launch_cfg, max_items_per_block));
+  return 0;
+}
+""")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    want = [ctypes.sizeof(TmmProblem), TmmProblem.n_direct.offset, TmmProblem.mat_table.offset,
+            TmmProblem.n_materials.offset, TmmProblem.d.offset, TmmProblem.lambda_.offset,
+            ctypes.sizeof(TmmLaunchCfg), TmmLaunchCfg.max_items_per_block.offset]
+    assert got == want
+
+
+def _problem(**kw):
+    from paper_2111_13667_gb300.abi import TmmProblem
+    p = TmmProblem()
+    p.S, p.L_max, p.n_lambda, p.n_theta, p.pol_mask, p.prec = 4, 3, 8, 2, 3, 0
+    p.n_direct = 0x1000
+    p.d, p.theta, p.lambda_ = 0x2000, 0x3000, 0x4000
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+@pytest.mark.parametrize("bad", [
+    dict(S=-1), dict(L_max=-2), dict(n_lambda=-1), dict(pol_mask=0), dict(pol_mask=4), dict(prec=7),
+    dict(mat_table=0x5000),                       # both index sources
+    dict(n_direct=None),                          # neither index source
+    dict(n_direct_per_lambda=2),
+    dict(theta=None), dict(d=None),
+    dict(n_direct=None, mat_table=0x5000, mat_idx=0x6000, n_materials=0),
+])
+def test_host_rejects_bad_problem(lib, bad):
+    from paper_2111_13667_gb300 import abi
+    p = _problem(**bad)
+    st = lib.tmm_coh_batched(ctypes.byref(p), ctypes.c_void_p(0x7000), None, None)
+    assert st == abi.TMM_ERR_INVALID_ARG
+    n = ctypes.c_size_t(0)
+    assert lib.tmm_workspace_size(ctypes.byref(p), None, ctypes.byref(n)) == abi.TMM_ERR_INVALID_ARG
+
+
+def test_host_rejects_missing_outputs_and_bad_cfg(lib):
+    from paper_2111_13667_gb300 import abi
+    p = _problem()
+    assert lib.tmm_coh_batched(ctypes.byref(p), None, None, None) == abi.TMM_ERR_INVALID_ARG
+    cfg = abi.launch_cfg(tile_lambda=-4)
+    assert lib.tmm_coh_batched_ex(ctypes.byref(p), ctypes.byref(cfg), None, 0, ctypes.c_void_p(0x7000),
+                                  None, None) == abi.TMM_ERR_INVALID_ARG
+    cfg = abi.launch_cfg(persistent=2)
+    assert lib.tmm_coh_batched_ex(ctypes.byref(p), ctypes.byref(cfg), None, 0, ctypes.c_void_p(0x7000),
+                                  None, None) == abi.TMM_ERR_INVALID_ARG
+    assert lib.tmm_coh_grad(ctypes.byref(p), None, None, None, None, None, 0, None) == abi.TMM_ERR_INVALID_ARG
+    assert lib.tmm_workspace_status(None, None) == abi.TMM_ERR_INVALID_ARG
+
+
+def test_empty_problem_is_a_noop(lib):
+    from paper_2111_13667_gb300 import abi
+    p = _problem(S=0)
+    assert lib.tmm_coh_batched(ctypes.byref(p), None, None, None) == abi.TMM_OK
+
+
+def test_status_strings(lib):
+    from paper_2111_13667_gb300 import abi
+    assert lib.tmm_status_string(abi.TMM_OK) == b"ok"
+    assert b"argument" in lib.tmm_status_string(abi.TMM_ERR_INVALID_ARG)
+    assert lib.tmm_version() >= 100
+
+
+def test_product_package_has_no_oracle_dependency():
+    pkg = os.path.join(ROOT, "paper_2111_13667_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in txt and "from oracle" not in txt, f
+                assert "tmm_oracle" not in txt, f

@@ -1,0 +1,212 @@
+"""GPU parity of the forward path (tmm_coh_batched) against the FP64 oracle.
+
+Tolerances: FP64 path within 1e-10 absolute in R and T, FP32 path within
+1e-4 absolute, element by element on the same seeded inputs.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2111_13667_gb300 import abi
+from paper_2111_13667_gb300 import workloads as W
+from tests.helpers import oracle_index, oracle_RT
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-10, "f32": 1e-4}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    abi.load()
+
+
+def gpu_RT(w, prec, cfg=None, with_T=True, pols=None):
+    prob = abi.to_device(w, prec, pols=pols)
+    R, T = abi.coh_tmm(prob, with_T=with_T, cfg=cfg)
+    torch.cuda.synchronize()
+    return R.double().cpu().numpy(), (T.double().cpu().numpy() if with_T else None)
+
+
+def assert_close(got, ref, tol, what=""):
+    assert got.shape == ref.shape, (got.shape, ref.shape)
+    assert np.all(np.isfinite(got)), f"non-finite {what}"
+    err = np.max(np.abs(got - ref)) if got.size else 0.0
+    assert err <= tol, f"{what}: max |err| = {err:.3e} > {tol:.0e}"
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_plain_fp64_workload_full(prec):
+    w = W.plain_fp64()
+    Ro, To = oracle_RT(w)
+    R, T = gpu_RT(w, prec)
+    assert_close(R, Ro, TOL[prec], "R")
+    assert_close(T, To, TOL[prec], "T")
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_dispersive_small_ragged_tail(prec):
+    # several lambda / theta tiles with a partial last tile, gathered index
+    w = W.dispersive(seed=11, S=37, L=24, n_lambda=203, n_theta=13)
+    Ro, To = oracle_RT(w)
+    R, T = gpu_RT(w, prec)
+    assert_close(R, Ro, TOL[prec], "R")
+    assert_close(T, To, TOL[prec], "T")
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_direct_per_lambda_index(prec):
+    w = W.dispersive(seed=12, S=9, L=10, n_lambda=40, n_theta=5)
+    w.n_direct = oracle_index(w)  # same indices given directly, [S][L+2][N_lambda]
+    w.table = w.mat_idx = None
+    Ro, To = oracle_RT(w)
+    R, T = gpu_RT(w, prec)
+    assert_close(R, Ro, TOL[prec], "R")
+    assert_close(T, To, TOL[prec], "T")
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("pols", ["s", "p"])
+def test_single_polarisation_and_R_only(prec, pols):
+    w = W.plain_fp64(seed=13, S=5, L=7)
+    Ro, _ = oracle_RT(w, pols=pols)
+    R, _ = gpu_RT(w, prec, with_T=False, pols=pols)
+    assert_close(R, Ro, TOL[prec], "R")
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_total_internal_reflection_and_grazing(prec):
+    w = W.map_x3()  # injection index 2 into air, theta up to exactly 90 deg
+    Ro, To = oracle_RT(w)
+    R, T = gpu_RT(w, prec)
+    if prec == "f64":
+        assert_close(R, Ro, TOL[prec], "R")
+        assert_close(T, To, TOL[prec], "T")
+    else:
+        # the last angle is 90 deg: pi/2 rounded to float has cos > 0, so the
+        # grazing reading is compared in FP64 only
+        assert_close(R[..., :-1, :], Ro[..., :-1, :], TOL[prec], "R")
+        assert_close(T[..., :-1, :], To[..., :-1, :], TOL[prec], "T")
+    assert np.all(R[:, 0, -1, :] == 1.0) or prec == "f32"
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_single_interface_and_opaque_layers(prec):
+    lam = np.linspace(400, 800, 33)
+    th = np.deg2rad(np.linspace(0, 70, 6))
+    cases = [
+        ([1.0, 1.5], []),                                    # L = 0
+        ([1.0, 2.0 + 1.0j, 1.7, 1.52], [1e5, 80.0]),         # clamp: thick absorber
+        ([1.0] + [2.0 + 1.0j, 1.5] * 12 + [1.52], [1e5, 100.0] * 12),  # many opaque layers
+    ]
+    for media, d in cases:
+        L = len(d)
+        nd = np.asarray(media, dtype=np.complex128)[None, :]
+        w = W.Workload("case", theta=th, lam=lam, d=np.asarray(d, dtype=np.float64).reshape(1, L), n_direct=nd)
+        Ro, To = oracle_RT(w)
+        R, T = gpu_RT(w, prec)
+        assert_close(R, Ro, TOL[prec], f"R {media[:3]}")
+        assert_close(T, To, TOL[prec], f"T {media[:3]}")
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("persistent", [0, 1])
+def test_ragged_layer_counts(prec, persistent):
+    w = W.ragged(seed=14, S=301, L_max=60, n_lambda=45, n_theta=7)
+    Ro, To = oracle_RT(w)
+    cfg = abi.launch_cfg(persistent=persistent)
+    R, T = gpu_RT(w, prec, cfg=cfg)
+    assert_close(R, Ro, TOL[prec], "R")
+    assert_close(T, To, TOL[prec], "T")
+    # padded problem (zero-thickness outcoupling layers up to L_max) gives the same
+    wp = W.Workload(w.name, theta=w.theta, lam=w.lam, d=w.d, table=w.table, mat_idx=w.mat_idx)
+    Rp, Tp = gpu_RT(wp, prec)
+    assert_close(Rp, Ro, TOL[prec], "R padded")
+
+
+def test_bad_material_index_poisons_only_its_stack():
+    w = W.dispersive(seed=15, S=6, L=5, n_lambda=16, n_theta=3)
+    w.mat_idx = w.mat_idx.copy()
+    w.mat_idx[2, 3] = 99
+    R, T = gpu_RT(w, "f64")
+    assert np.all(np.isnan(R[:, 2])) and np.all(np.isnan(T[:, 2]))
+    ok = [0, 1, 3, 4, 5]
+    Ro, To = oracle_RT(w.subset(ok))
+    assert_close(R[:, ok], Ro, TOL["f64"], "R")
+
+
+def test_bad_layer_count_poisons_only_its_stack():
+    w = W.ragged(seed=16, S=5, L_max=8, n_lambda=16, n_theta=3)
+    w.L_per_stack = w.L_per_stack.copy()
+    w.L_per_stack[1] = 9
+    w.L_per_stack[3] = -1
+    for persistent in (0, 1):
+        R, _ = gpu_RT(w, "f32", cfg=abi.launch_cfg(persistent=persistent))
+        assert np.all(np.isnan(R[:, 1])) and np.all(np.isnan(R[:, 3]))
+        assert np.all(np.isfinite(R[:, [0, 2, 4]]))
+
+
+def test_persistent_iteration_limit_reports_timeout():
+    # a deliberately small per-block item budget: blocks stop early and the
+    # workspace records TMM_ERR_TIMEOUT (no fault, no hang)
+    w = W.ragged(seed=17, S=2000, L_max=10, n_lambda=64, n_theta=4)
+    prob = abi.to_device(w, "f32")
+    cfg = abi.launch_cfg(persistent=1, blocks_per_sm=1, max_items_per_block=1)
+    ws = abi.alloc_workspace(abi.tmm_workspace_size(prob, cfg))
+    R = prob.empty_out()
+    abi.tmm_coh_batched_ex(prob, cfg, ws, R, None)
+    assert abi.tmm_workspace_status(ws) == abi.TMM_ERR_TIMEOUT
+    cfg = abi.launch_cfg(persistent=1)
+    abi.tmm_coh_batched_ex(prob, cfg, ws, R, None)
+    assert abi.tmm_workspace_status(ws) == abi.TMM_OK
+
+
+def test_workspace_checks():
+    w = W.ragged(seed=18, S=10, L_max=10, n_lambda=8, n_theta=2)
+    prob = abi.to_device(w, "f32")
+    cfg = abi.launch_cfg(persistent=1)
+    R = prob.empty_out()
+    with pytest.raises(abi.TmmError) as e:
+        abi.tmm_coh_batched_ex(prob, cfg, None, R, None)
+    assert e.value.status == abi.TMM_ERR_INVALID_ARG
+    small = abi.alloc_workspace(256)
+    with pytest.raises(abi.TmmError) as e:
+        abi.tmm_coh_batched_ex(prob, cfg, small, R, None)
+    assert e.value.status == abi.TMM_ERR_NOMEM
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_dispersive_full_size_sampled(prec):
+    """The full 16384 x 24 x 512 x 32 problem in the launch the benchmark
+    times; a seeded sample of stacks is checked against the oracle."""
+    w = W.dispersive()
+    prob = abi.to_device(w, prec)
+    R, T = abi.coh_tmm(prob)
+    torch.cuda.synchronize()
+    idx = np.sort(np.random.default_rng(99).choice(w.S, size=6, replace=False))
+    idx = np.concatenate([[0], idx, [w.S - 1]])
+    Ro, To = oracle_RT(w.subset(idx))
+    it = torch.as_tensor(idx, device=R.device)
+    Rg = R[:, it].double().cpu().numpy()
+    Tg = T[:, it].double().cpu().numpy()
+    assert_close(Rg, Ro, TOL[prec], "R")
+    assert_close(Tg, To, TOL[prec], "T")
+    # properties that hold everywhere: finite, 0 <= R, T and R + T <= 1
+    Rall = R.double()
+    Tall = T.double()
+    assert bool(torch.isfinite(Rall).all()) and bool(torch.isfinite(Tall).all())
+    assert float(Rall.min()) >= -TOL[prec] and float(Tall.min()) >= -TOL[prec]
+    assert float((Rall + Tall).max()) <= 1 + TOL[prec]
+
+
+def test_empty_batch():
+    w = W.plain_fp64(S=3, L=2)
+    prob = abi.to_device(w, "f64")
+    prob.d = prob.d[:0]
+    prob.n_direct = prob.n_direct[:0]
+    R = prob.empty_out()
+    abi.tmm_coh_batched(prob, R, None)
+    assert R.numel() == 0
