@@ -60,8 +60,23 @@ __device__ __forceinline__ void exp_pm_turn(double y, double *ep, double *em)
     *ep = exp(kTwoPi * y);
     *em = exp(-kTwoPi * y);
 }
+// exp(-4 pi y): the e^{+i delta} factor relative to e^{-i delta} for Im delta = 2 pi y.
+__device__ __forceinline__ float exp_m2_turn(float y) { return exp2f((float)(-2.0 * kTwoPi * kLog2e) * y); }
+__device__ __forceinline__ double exp_m2_turn(double y) { return exp(-2.0 * kTwoPi * y); }
+__device__ __forceinline__ float exp2_w(float v) { return exp2f(v); }
+__device__ __forceinline__ double exp2_w(double v) { return exp2(v); }
+__device__ __forceinline__ float floor_w(float v) { return floorf(v); }
+__device__ __forceinline__ double floor_w(double v) { return floor(v); }
 __device__ __forceinline__ float sin_w(float v) { return sinf(v); }
 __device__ __forceinline__ double sin_w(double v) { return sin(v); }
+__device__ __forceinline__ void sincos_w(float v, float *s, float *c) { sincosf(v, s, c); }
+__device__ __forceinline__ void sincos_w(double v, double *s, double *c) { sincos(v, s, c); }
+// Layers between two rescalings of the running products: the per-layer growth
+// is below 2^63 (|n| <= 32 and the Im(delta) <= 35 clamp), so FP32 can take
+// two layers and FP64 eight before the exponent range is at risk.
+template <typename R> struct RenormEvery;
+template <> struct RenormEvery<float> { static constexpr int value = 2; };
+template <> struct RenormEvery<double> { static constexpr int value = 8; };
 template <typename R> __device__ __forceinline__ R eps_w();
 template <> __device__ __forceinline__ float eps_w<float>() { return 1.1920929e-7f; }
 template <> __device__ __forceinline__ double eps_w<double>() { return 2.220446049250313e-16; }

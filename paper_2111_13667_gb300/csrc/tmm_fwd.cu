@@ -28,76 +28,91 @@ namespace tmm {
 constexpr int kMaxThreads = 512;
 
 // One (lambda, theta) point of one stack, both polarisations as requested.
-// out = {R_s, T_s, R_p, T_p}.
+// out = {R_s, T_s, R_p, T_p}.  Pp_m * 2^Pp_e = prod_{j=1..L+1} |1/n_j^2|^2 for
+// this wavelength (theta-independent, computed while staging).
+//
+// Each layer's phase matrix is applied divided by its real factor
+// e^{Im delta}: diag(e^{-i Re delta}, e^{-2 Im delta} e^{i Re delta}).  R does
+// not see the factor; for T the product of all factors enters |t|^2 as
+// 2^{-2 K Y}, Y = sum of Im(delta) / (2 pi), K = 2 pi log2(e).
 template <typename R, int POL>
 __device__ __forceinline__ void eval_point(const StageA<R> *__restrict__ sa, const StageB<R> *__restrict__ sb,
-                                           int TL, int tl, int L, R n0, R sin_theta, R out[4])
+                                           int TL, int tl, int L, R n0, R sin_theta, R cos_theta, R Pp_m,
+                                           int Pp_e, R out[4])
 {
+    constexpr int RN = RenormEvery<R>::value;
     const R beta = n0 * sin_theta;
     const R beta2 = beta * beta;
     const R yi_max = R(kImDeltaMax / kTwoPi);
 
     StageA<R> A = sa[(L + 1) * TL + tl];
-    StageB<R> B = sb[(L + 1) * TL + tl];
     R absz;
     Cx<R> q_nx = forward_root(Cx<R>{A.n2x - beta2, A.n2y}, &absz);
     const Cx<R> q_out = q_nx, n2_out = {A.n2x, A.n2y};
     Cx<R> g_nx = cmul(q_nx, Cx<R>{A.in2x, A.in2y});
-    R Ps = R(1), Pp = B.ain2;
-    int eP = 0, ePp = 0;
-    renorm_scalar(Pp, ePp);
+    R Ps = R(1), Y = R(0);
+    int eP = 0;
     Cx<R> s0 = {R(1), R(0)}, s1 = {R(0), R(0)}, p0 = {R(1), R(0)}, p1 = {R(0), R(0)};
     int es = 0, ep = 0;
 
     for (int j = L; j >= 1; --j) {
         A = sa[j * TL + tl];
-        B = sb[j * TL + tl];
+        const StageB<R> B = sb[j * TL + tl];
         const Cx<R> q = forward_root(Cx<R>{A.n2x - beta2, A.n2y}, &absz);
         Ps *= absz;
-        renorm_scalar(Ps, eP);
         // layer phase in turns: delta / (2 pi) = (d / lambda) q, Im clamped
         const R yr = B.dl * q.x;
         const R yi = fmin(B.dl * q.y, yi_max);
-        R sn, cs, Ep, Em;
+        Y += yi;
+        R sn, cs;
         sincos_turn(yr - rint_w(yr), &sn, &cs);
-        exp_pm_turn(yi, &Ep, &Em);
-        const Cx<R> emi = {Ep * cs, -Ep * sn};  // e^{-i delta}
-        const Cx<R> epi = {Em * cs, Em * sn};   // e^{+i delta}
+        const R E2 = exp_m2_turn(yi);
+        const Cx<R> emi = {cs, -sn};            // e^{-i delta} / e^{Im delta}
+        const Cx<R> epi = {E2 * cs, E2 * sn};   // e^{+i delta} / e^{Im delta}
         if (POL & 1) {
             const Cx<R> a = q + q_nx, b = q - q_nx;
             const Cx<R> u0 = cfma(a, s0, cmul(b, s1));
             const Cx<R> u1 = cfma(b, s0, cmul(a, s1));
             s0 = cmul(emi, u0);
             s1 = cmul(epi, u1);
-            renorm_pair(s0, s1, es);
         }
         if (POL & 2) {
-            Pp *= B.ain2;
-            renorm_scalar(Pp, ePp);
             const Cx<R> g = cmul(q, Cx<R>{A.in2x, A.in2y});
             const Cx<R> a = g + g_nx, b = g - g_nx;
             const Cx<R> u0 = cfma(a, p0, cmul(b, p1));
             const Cx<R> u1 = cfma(b, p0, cmul(a, p1));
             p0 = cmul(emi, u0);
             p1 = cmul(epi, u1);
-            renorm_pair(p0, p1, ep);
             g_nx = g;
         }
         q_nx = q;
+        if ((L - j) % RN == RN - 1) {
+            renorm_scalar(Ps, eP);
+            if (POL & 1) renorm_pair(s0, s1, es);
+            if (POL & 2) renorm_pair(p0, p1, ep);
+        }
     }
-    // interface 0 -> 1 (the injection medium carries no phase)
+    // interface 0 -> 1; the injection medium is real, so q_0 = n_0 cos(theta)
+    // (computed directly: n_0^2 - beta^2 cancels near grazing incidence)
     A = sa[tl];
-    const Cx<R> q0 = forward_root(Cx<R>{A.n2x - beta2, A.n2y}, &absz);
-    Ps *= absz;
+    const bool grazing = beta >= n0;  // false for a NaN (complex, rejected) n_0
+    const Cx<R> q0 = {n0 * cos_theta, R(0)};
+    Ps *= q0.x * q0.x;
     const int e4 = 2 * (L + 1);  // the factors 2 of every 2a
+    // 2^{-2 K Y} = 2^{yf} 2^{yn}, yn integer
+    R u = R(-2.0 * kTwoPi * kLog2e) * Y;
+    u = fmax(u, R(-1.0e6));
+    const R un = floor_w(u);
+    const R yscale = exp2_w(u - un);
+    const int yn = (int)un;
     if (POL & 1) {
         const Cx<R> a = q0 + q_nx, b = q0 - q_nx;
         const Cx<R> x0 = cfma(a, s0, cmul(b, s1));
         const Cx<R> x1 = cfma(b, s0, cmul(a, s1));
         const R ax0 = abs2(x0);
         R Rv = abs2(x1) / ax0;
-        R Tv = q_out.x / q0.x * ldexp_w(Ps / ax0, e4 + eP - 2 * es);
-        if (q0.x == R(0) && q0.y == R(0)) { Rv = R(1); Tv = R(0); }
+        R Tv = q_out.x / q0.x * ldexp_w(Ps * yscale / ax0, e4 + eP + yn - 2 * es);
+        if (grazing) { Rv = R(1); Tv = R(0); }
         out[0] = Rv;
         out[1] = Tv;
     }
@@ -109,9 +124,9 @@ __device__ __forceinline__ void eval_point(const StageA<R> *__restrict__ sa, con
         const R ax0 = abs2(x0);
         R Rv = abs2(x1) / ax0;
         const R num = cmul(n2_out, conj(q_out)).x;
-        const R den = cmul(Cx<R>{A.n2x, A.n2y}, conj(q0)).x;
-        R Tv = num / den * ldexp_w(Ps * Pp / ax0, e4 + eP + ePp - 2 * ep);
-        if (q0.x == R(0) && q0.y == R(0)) { Rv = R(1); Tv = R(0); }
+        const R den = A.n2x * q0.x;
+        R Tv = num / den * ldexp_w(Ps * Pp_m * yscale / ax0, e4 + eP + Pp_e + yn - 2 * ep);
+        if (grazing) { Rv = R(1); Tv = R(0); }
         out[2] = Rv;
         out[3] = Tv;
     }
@@ -126,6 +141,8 @@ __device__ __forceinline__ void run_item(const tmm_problem &p, int s, int lt, in
     StageA<R> *sa = reinterpret_cast<StageA<R> *>(smem);
     StageB<R> *sb = reinterpret_cast<StageB<R> *>(sa + (size_t)(p.L_max + 2) * TL);
     R *n0s = reinterpret_cast<R *>(sb + (size_t)(p.L_max + 2) * TL);
+    R *ppm = n0s + TL;
+    int *ppe = reinterpret_cast<int *>(ppm + TL);
 
     const int tid = threadIdx.y * TL + threadIdx.x;
     const int nthr = TL * TT;
@@ -133,13 +150,27 @@ __device__ __forceinline__ void run_item(const tmm_problem &p, int s, int lt, in
     const int l0 = lt * TL, t0 = tt * TT;
     if (L >= 0) fill_stage<R>(p, s, L, l0, TL, sa, sb, n0s, tid, nthr);
     __syncthreads();
+    if ((POL & 2) && L >= 0 && tid < TL) {
+        // prod_{j=1..L+1} |1/n_j^2|^2 for this wavelength
+        R m = R(1);
+        int e = 0;
+        for (int j = 1; j <= L + 1; ++j) {
+            m *= sb[j * TL + tid].ain2;
+            renorm_scalar(m, e);
+        }
+        ppm[tid] = m;
+        ppe[tid] = e;
+    }
+    __syncthreads();
 
     const int tl = threadIdx.x, l = l0 + tl, a = t0 + threadIdx.y;
     if (l < p.n_lambda && a < p.n_theta) {
         R out[4];
         if (L >= 0) {
-            const R th = ((const R *)p.theta)[a];
-            eval_point<R, POL>(sa, sb, TL, tl, L, n0s[tl], sin_w(th), out);
+            R sth, cth;
+            sincos_w(((const R *)p.theta)[a], &sth, &cth);
+            eval_point<R, POL>(sa, sb, TL, tl, L, n0s[tl], sth, cth, (POL & 2) ? ppm[tl] : R(1),
+                               (POL & 2) ? ppe[tl] : 0, out);
         } else {
             out[0] = out[1] = out[2] = out[3] = nan_w<R>();
         }
@@ -253,7 +284,7 @@ PersistentWs persistent_ws_layout(const tmm_problem *p)
 static size_t stage_bytes(const tmm_problem *p, int TL)
 {
     const size_t r = real_size(p->prec);
-    return (size_t)(p->L_max + 2) * TL * (6 * r) + (size_t)TL * r;
+    return (size_t)(p->L_max + 2) * TL * (6 * r) + (size_t)TL * (2 * r + sizeof(int));
 }
 
 tmm_status choose_tile(const tmm_problem *p, const tmm_launch_cfg *cfg, Tile *t)
