@@ -248,6 +248,10 @@ def gpu_arm(args):
         del R, T, prob
         torch.cuda.empty_cache()
 
+    if not args.skip_extras:
+        out["ragged"] = bench_ragged(args, torch, abi, W, flush, world, max_over_ranks)
+        out["adjoint"] = bench_adjoint(args, torch, abi, W, flush, world, max_over_ranks)
+
     head = out["f32"]
     line = {
         "metric": "TMM evals/s (stack x lambda x theta x pol), dispersive 16384x24, 512 lambda x 32 theta, s+p",
@@ -262,8 +266,9 @@ def gpu_arm(args):
         "roofline": head["roofline"], "clocks": head.get("clocks"), "e2e": head.get("e2e"),
         "gpu_launches": args.steps,
     }
-    if "f64" in out:
-        line["f64"] = out["f64"]
+    for k in ("f64", "ragged", "adjoint"):
+        if k in out:
+            line[k] = out[k]
     line["cpu_baseline"] = cpu_baseline(w, args) if (rank == 0 and world == 1 and not args.skip_cpu) else None
     peaks = measured_peaks()
     if peaks:
@@ -272,6 +277,63 @@ def gpu_arm(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def bench_ragged(args, torch, abi, W, flush, world, max_over_ranks):
+    """Ragged batch (131072 stacks, L_s ~ U{1..120}, 256 lambda x 16 theta, FP32):
+    autotuned persistent launch replayed from a CUDA graph vs one padded launch
+    at L_max = 120 (zero-thickness outcoupling layers, exact by invariance)."""
+    from paper_2111_13667_gb300 import autotune
+    from paper_2111_13667_gb300.ragged import RaggedRunner
+    w = W.ragged()
+    prob = abi.to_device(w, "f32")
+    report = []
+    t0 = time.perf_counter()
+    cfg = autotune.tune(prob, report=report, reps=2)
+    tune_s = time.perf_counter() - t0
+    run = RaggedRunner(prob, cfg=cfg).capture()
+    steps = max(3, args.steps // 2)
+    tg = time_steps(lambda: run.graph.replay(), steps, 3, torch, flush)
+    status = run.status()
+    ms_g = max_over_ranks(sum(tg) / len(tg))
+    del run
+    padded = abi.DeviceProblem(prob.prec, prob.pol_mask, prob.theta, prob.lam, prob.d, table=prob.table,
+                               mat_idx=prob.mat_idx)
+    R = padded.empty_out()
+    T = padded.empty_out()
+    tp = time_steps(lambda: abi.tmm_coh_batched(padded, R, T), steps, 3, torch, flush)
+    ms_p = max_over_ranks(sum(tp) / len(tp))
+    del R, T
+    torch.cuda.empty_cache()
+    evals = w.evals * world
+    return {"workload": w.name, "unit": "evals/s", "dtype": "f32",
+            "graph_persistent": {"value": evals / (ms_g * 1e-3), "ms_per_step": ms_g,
+                                 "tile_lambda": cfg.tile_lambda, "tile_theta": cfg.tile_theta,
+                                 "persistent": cfg.persistent, "status": status},
+            "padded_L120": {"value": evals / (ms_p * 1e-3), "ms_per_step": ms_p},
+            "speedup_vs_padded": ms_p / ms_g, "autotune_s": tune_s, "candidates": len(report),
+            "layer_steps_ratio": w.layer_steps() / (w.evals * (w.L_max + 1)), "steps": steps}
+
+
+def bench_adjoint(args, torch, abi, W, flush, world, max_over_ranks):
+    """Merit + gradients (4096 stacks x 40 layers, 512 lambda x 16 theta, s+p)."""
+    from paper_2111_13667_gb300 import autograd as ag
+    w = W.adjoint()
+    res = {"workload": w.name, "unit": "evals/s (merit and both gradients)"}
+    for prec, steps in (("f32", max(3, args.steps // 2)), ("f64", 2)):
+        if prec == "f64" and args.skip_f64:
+            continue
+        prob = abi.to_device(w, prec)
+        dt = prob.real_dtype
+        Rt = torch.as_tensor(w.R_target).to(device=prob.d.device, dtype=dt).contiguous()
+        m = torch.empty(w.S, dtype=dt, device=prob.d.device)
+        dd = torch.empty(w.S, w.L_max, dtype=dt, device=prob.d.device)
+        dn = torch.empty_like(dd)
+        ws = ag.grad_workspace(prob)
+        t = time_steps(lambda: abi.tmm_coh_grad(prob, Rt, m, dd, dn, ws), steps, 3, torch, flush)
+        ms = max_over_ranks(sum(t) / len(t))
+        res[prec] = {"value": w.evals * world / (ms * 1e-3), "ms_per_step": ms, "steps": steps}
+    return res
 
 
 def R_bytes(w, elt):
@@ -356,6 +418,7 @@ def main():
     ap.add_argument("--skip-e2e-f64", action="store_true", default=True)
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-extras", action="store_true", help="headline only (no ragged / adjoint lines)")
     ap.add_argument("--stacks", type=int, default=0, help="shrink the workload (profiling runs only)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     args = ap.parse_args()

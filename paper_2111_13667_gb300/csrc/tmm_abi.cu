@@ -61,10 +61,12 @@ tmm_status validate_problem(const tmm_problem *p)
     if (p->S < 0 || p->L_max < 0 || p->n_lambda < 0 || p->n_theta < 0) return TMM_ERR_INVALID_ARG;
     if (p->pol_mask == 0 || (p->pol_mask & ~3u)) return TMM_ERR_INVALID_ARG;
     if (p->prec != TMM_F64 && p->prec != TMM_F32) return TMM_ERR_INVALID_ARG;
+    if (p->n_direct_per_lambda != 0 && p->n_direct_per_lambda != 1) return TMM_ERR_INVALID_ARG;
+    // an empty batch reads no array, so its pointers are not checked
+    if ((long long)p->S * p->n_lambda * p->n_theta == 0) return TMM_OK;
     const bool direct = p->n_direct != nullptr;
     const bool gathered = p->mat_table != nullptr || p->mat_idx != nullptr;
     if (direct == gathered) return TMM_ERR_INVALID_ARG;
-    if (direct && p->n_direct_per_lambda != 0 && p->n_direct_per_lambda != 1) return TMM_ERR_INVALID_ARG;
     if (gathered && (!p->mat_table || !p->mat_idx || p->n_materials < 1)) return TMM_ERR_INVALID_ARG;
     const bool any = (long long)p->S * p->n_lambda * p->n_theta > 0;
     if (any) {

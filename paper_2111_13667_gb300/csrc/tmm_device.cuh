@@ -121,7 +121,7 @@ template <typename R> __device__ __forceinline__ Cx<R> forward_root(Cx<R> z, R *
     const R hyp = fma(z.x, z.x, z.y * z.y);
     Cx<R> q = {R(0), R(0)};
     R absz = R(0);
-    if (hyp > R(0)) {
+    if (!(hyp <= R(0))) {  // also taken for NaN, so a poisoned index stays NaN
         const R rh = rsqrt_w(hyp);
         absz = hyp * rh;
         const R u = R(0.5) * (absz + fabs(z.x));
@@ -139,9 +139,13 @@ template <typename R> __device__ __forceinline__ Cx<R> forward_root(Cx<R> z, R *
 }
 
 // ---------------------------------------------------------------- shared-memory stage
-// Per (medium j, wavelength): n_j^2, 1 / n_j^2, |1 / n_j^2|^2 and d_j / lambda
-// (0 for the two semi-infinite media).  Two arrays keep the loads vectorised.
-template <typename R> struct StageA { R n2x, n2y, in2x, in2y; };
+// Per (medium j, wavelength): n_j^2 - n_0^2 (real part; the imaginary part is
+// that of n_j^2), 1 / n_j^2, |1 / n_j^2|^2 and d_j / lambda (0 for the two
+// semi-infinite media).  A point then forms n_j^2 - beta^2 as
+// (n_j^2 - n_0^2) + (n_0 cos theta)^2, which has no cancellation for media
+// index-matched to the injection medium near grazing incidence.  Two arrays
+// keep the loads vectorised.
+template <typename R> struct StageA { R d2x, n2y, in2x, in2y; };
 template <typename R> struct StageB { R ain2, dl; };
 
 template <typename R> __device__ __forceinline__ Cx<R> load_cx(const R *p, long long i)
@@ -185,11 +189,12 @@ __device__ __forceinline__ void fill_stage(const tmm_problem &p, int s, int L, i
         const int j = idx / TL, tl = idx - j * TL;
         const int l = min(l0 + tl, p.n_lambda - 1);
         Cx<R> n = index_of<R>(p, s, j, l);
+        const R n0 = j == 0 ? n.x : index_of<R>(p, s, 0, l).x;
         const Cx<R> n2 = {fma(n.x, n.x, -n.y * n.y), R(2) * n.x * n.y};
         const R a = abs2(n2);
         const R ia = R(1) / a;
         StageA<R> A;
-        A.n2x = n2.x;
+        A.d2x = (n.x - n0) * (n.x + n0) - n.y * n.y;
         A.n2y = n2.y;
         A.in2x = n2.x * ia;
         A.in2y = -n2.y * ia;

@@ -18,6 +18,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
+#include <vector>
 
 #include "tmm_device.cuh"
 #include "tmm_internal.h"
@@ -42,13 +44,14 @@ __device__ __forceinline__ void eval_point(const StageA<R> *__restrict__ sa, con
 {
     constexpr int RN = RenormEvery<R>::value;
     const R beta = n0 * sin_theta;
-    const R beta2 = beta * beta;
+    const R c0 = n0 * cos_theta;
+    const R q0sq = c0 * c0;  // n_j^2 - beta^2 = (n_j^2 - n_0^2) + q0sq
     const R yi_max = R(kImDeltaMax / kTwoPi);
 
     StageA<R> A = sa[(L + 1) * TL + tl];
     R absz;
-    Cx<R> q_nx = forward_root(Cx<R>{A.n2x - beta2, A.n2y}, &absz);
-    const Cx<R> q_out = q_nx, n2_out = {A.n2x, A.n2y};
+    Cx<R> q_nx = forward_root(Cx<R>{A.d2x + q0sq, A.n2y}, &absz);
+    const Cx<R> q_out = q_nx, n2_out = {A.d2x + n0 * n0, A.n2y};
     Cx<R> g_nx = cmul(q_nx, Cx<R>{A.in2x, A.in2y});
     R Ps = R(1), Y = R(0);
     int eP = 0;
@@ -58,7 +61,7 @@ __device__ __forceinline__ void eval_point(const StageA<R> *__restrict__ sa, con
     for (int j = L; j >= 1; --j) {
         A = sa[j * TL + tl];
         const StageB<R> B = sb[j * TL + tl];
-        const Cx<R> q = forward_root(Cx<R>{A.n2x - beta2, A.n2y}, &absz);
+        const Cx<R> q = forward_root(Cx<R>{A.d2x + q0sq, A.n2y}, &absz);
         Ps *= absz;
         // layer phase in turns: delta / (2 pi) = (d / lambda) q, Im clamped
         const R yr = B.dl * q.x;
@@ -96,7 +99,7 @@ __device__ __forceinline__ void eval_point(const StageA<R> *__restrict__ sa, con
     // (computed directly: n_0^2 - beta^2 cancels near grazing incidence)
     A = sa[tl];
     const bool grazing = beta >= n0;  // false for a NaN (complex, rejected) n_0
-    const Cx<R> q0 = {n0 * cos_theta, R(0)};
+    const Cx<R> q0 = {c0, R(0)};
     Ps *= q0.x * q0.x;
     const int e4 = 2 * (L + 1);  // the factors 2 of every 2a
     // 2^{-2 K Y} = 2^{yf} 2^{yn}, yn integer
@@ -124,7 +127,7 @@ __device__ __forceinline__ void eval_point(const StageA<R> *__restrict__ sa, con
         const R ax0 = abs2(x0);
         R Rv = abs2(x1) / ax0;
         const R num = cmul(n2_out, conj(q_out)).x;
-        const R den = A.n2x * q0.x;
+        const R den = n0 * n0 * q0.x;
         R Tv = num / den * ldexp_w(Ps * Pp_m * yscale / ax0, e4 + eP + Pp_e + yn - 2 * ep);
         if (grazing) { Rv = R(1); Tv = R(0); }
         out[2] = Rv;
@@ -311,11 +314,46 @@ tmm_status choose_tile(const tmm_problem *p, const tmm_launch_cfg *cfg, Tile *t)
     return TMM_OK;
 }
 
-template <typename Kernel> static tmm_status allow_smem(Kernel k, size_t bytes)
+// Per-(kernel, device) host-side facts, cached so that repeated launches (and
+// launches recorded into a CUDA graph) make no attribute or occupancy calls.
+struct KernelFacts {
+    const void *fn;
+    int dev, threads;
+    size_t smem;
+    int smem_set, per_sm;
+};
+static std::mutex g_facts_mu;
+static std::vector<KernelFacts> g_facts;
+
+static KernelFacts *facts_for(const void *fn, int dev, int threads, size_t smem)
 {
-    if (bytes <= 48 * 1024) return TMM_OK;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    return e == cudaSuccess ? TMM_OK : cuda_fail(e);
+    for (auto &f : g_facts)
+        if (f.fn == fn && f.dev == dev && f.threads == threads && f.smem == smem) return &f;
+    g_facts.push_back(KernelFacts{fn, dev, threads, smem, 0, 0});
+    return &g_facts.back();
+}
+
+template <typename Kernel>
+static tmm_status prepare_kernel(Kernel k, int threads, size_t smem, bool need_occupancy, int *per_sm)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e);
+    std::lock_guard<std::mutex> lk(g_facts_mu);
+    KernelFacts *f = facts_for(reinterpret_cast<const void *>(k), dev, threads, smem);
+    if (smem > 48 * 1024 && !f->smem_set) {
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return cuda_fail(e);
+        f->smem_set = 1;
+    }
+    if (need_occupancy && f->per_sm == 0) {
+        int n = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, threads, smem);
+        if (e != cudaSuccess) return cuda_fail(e);
+        f->per_sm = std::max(n, 1);
+    }
+    if (per_sm) *per_sm = f->per_sm;
+    return TMM_OK;
 }
 
 template <typename R, int POL, bool WITH_T>
@@ -326,7 +364,7 @@ static tmm_status launch_typed(const tmm_problem *p, const tmm_launch_cfg *cfg, 
     const bool persistent = cfg && cfg->persistent;
     if (!persistent) {
         auto k = tmm_fwd_kernel<R, POL, WITH_T>;
-        tmm_status s = allow_smem(k, t.smem);
+        tmm_status s = prepare_kernel(k, t.TL * t.TT, t.smem, false, nullptr);
         if (s != TMM_OK) return s;
         if (t.n_items > 0x7fffffffLL) return TMM_ERR_UNSUPPORTED;
         if (t.n_items == 0) return TMM_OK;
@@ -334,7 +372,8 @@ static tmm_status launch_typed(const tmm_problem *p, const tmm_launch_cfg *cfg, 
         return check_launch();
     }
     auto k = tmm_fwd_persistent<R, POL, WITH_T>;
-    tmm_status s = allow_smem(k, t.smem);
+    int occ = 0;
+    tmm_status s = prepare_kernel(k, t.TL * t.TT, t.smem, true, &occ);
     if (s != TMM_OK) return s;
     if (t.n_items > 0xffffffffLL) return TMM_ERR_UNSUPPORTED;
     const PersistentWs w = persistent_ws_layout(p);
@@ -360,12 +399,7 @@ static tmm_status launch_typed(const tmm_problem *p, const tmm_launch_cfg *cfg, 
     DeviceInfo di;
     s = device_info(&di);
     if (s != TMM_OK) return s;
-    int per_sm = cfg->blocks_per_sm;
-    if (per_sm <= 0) {
-        cudaError_t oe = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, t.TL * t.TT, t.smem);
-        if (oe != cudaSuccess) return cuda_fail(oe);
-        per_sm = std::max(per_sm, 1);
-    }
+    const int per_sm = cfg->blocks_per_sm > 0 ? cfg->blocks_per_sm : occ;
     long long grid = (long long)per_sm * di.sms;
     grid = std::min(grid, t.n_items);
     k<<<(unsigned)grid, block, t.smem, st>>>(*p, t.TL, t.TT, t.n_lt, t.n_tt, order,

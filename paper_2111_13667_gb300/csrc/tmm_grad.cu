@@ -61,10 +61,10 @@ template <typename R> struct Medium {
 };
 
 template <typename R>
-__device__ __forceinline__ Medium<R> medium_at(const StageA<R> &A, Cx<R> n, R beta2, bool derivs)
+__device__ __forceinline__ Medium<R> medium_at(const StageA<R> &A, Cx<R> n, R q0sq, bool derivs)
 {
     Medium<R> m;
-    m.q = forward_root(Cx<R>{A.n2x - beta2, A.n2y}, &m.absz);
+    m.q = forward_root(Cx<R>{A.d2x + q0sq, A.n2y}, &m.absz);
     const Cx<R> in2 = {A.in2x, A.in2y};
     m.ap = cmul(m.q, in2);
     if (derivs) {
@@ -135,18 +135,18 @@ __global__ void __launch_bounds__(kGradThreads) tmm_grad_kernel(const tmm_proble
         R sth, cth;
         sincos_w(th[ac], &sth, &cth);
         const R beta = n0s[tl] * sth;
-        const R beta2 = beta * beta;
+        const R q0sq = (n0s[tl] * cth) * (n0s[tl] * cth);
         const R two_pi_inv_lam = R(kTwoPi) / lam[lc];
 
         // ---- 1. right-to-left sweep, storing x_j (j = L+1 .. 1)
-        Medium<R> nx = medium_at(sa[(L + 1) * TL + tl], sn[(L + 1) * TL + tl], beta2, false);
+        Medium<R> nx = medium_at(sa[(L + 1) * TL + tl], sn[(L + 1) * TL + tl], q0sq, false);
         Cx<R> s0 = {R(1), R(0)}, s1 = {R(0), R(0)}, p0 = s0, p1 = s1;
         int es = 0, ep = 0;
         X[L + 1] = XState<R>{s0, s1, p0, p1, 0, 0};
         for (int j = L; j >= 1; --j) {
             const StageA<R> A = sa[j * TL + tl];
             const StageB<R> B = sb[j * TL + tl];
-            const Medium<R> m = medium_at(A, sn[j * TL + tl], beta2, false);
+            const Medium<R> m = medium_at(A, sn[j * TL + tl], q0sq, false);
             const R yr = B.dl * m.q.x, yi = fmin(B.dl * m.q.y, yi_max);
             R sn_, cs, Ep, Em;
             sincos_turn(yr - rint_w(yr), &sn_, &cs);
@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(kGradThreads) tmm_grad_kernel(const tmm_proble
 
         // ---- 3. left-to-right cotangent sweep
         // cur = medium j, nx = medium j+1 (with n-derivatives when it is a layer)
-        nx = medium_at(sa[1 * TL + tl], sn[1 * TL + tl], beta2, L >= 1);
+        nx = medium_at(sa[1 * TL + tl], sn[1 * TL + tl], q0sq, L >= 1);
         R dn_carry = R(0);  // right-side F term for layer j+1, from step j
         for (int j = 0; j <= L; ++j) {
             const XState<R> Xn = X[j + 1];
@@ -289,7 +289,7 @@ __global__ void __launch_bounds__(kGradThreads) tmm_grad_kernel(const tmm_proble
             if (j + 1 <= L) {
                 cur = nx;
                 const int jn = j + 2;
-                nx = medium_at(sa[jn * TL + tl], sn[jn * TL + tl], beta2, jn <= L);
+                nx = medium_at(sa[jn * TL + tl], sn[jn * TL + tl], q0sq, jn <= L);
             }
         }
         (void)P;
@@ -379,8 +379,18 @@ static tmm_status launch_grad_typed(const tmm_problem *p, const GradPlan &g, con
 {
     auto k = tmm_grad_kernel<R, KMAX>;
     if (g.smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
+        // set once per (instantiation, device): the launch sequence stays free of
+        // attribute calls when it is recorded into a CUDA graph
+        static int set_bytes[64] = {};
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
         if (e != cudaSuccess) return cuda_fail(e);
+        if (dev < 0 || dev >= 64) return TMM_ERR_UNSUPPORTED;
+        if (set_bytes[dev] < (int)g.smem) {
+            e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
+            if (e != cudaSuccess) return cuda_fail(e);
+            set_bytes[dev] = (int)g.smem;
+        }
     }
     const long long blocks = (long long)p->S * g.G;
     if (blocks > 0x7fffffffLL) return TMM_ERR_UNSUPPORTED;
