@@ -189,12 +189,12 @@ __device__ __forceinline__ void fill_stage(const tmm_problem &p, int s, int L, i
         const int j = idx / TL, tl = idx - j * TL;
         const int l = min(l0 + tl, p.n_lambda - 1);
         Cx<R> n = index_of<R>(p, s, j, l);
-        const R n0 = j == 0 ? n.x : index_of<R>(p, s, 0, l).x;
+        const R n0v = j == 0 ? n.x : index_of<R>(p, s, 0, l).x;
         const Cx<R> n2 = {fma(n.x, n.x, -n.y * n.y), R(2) * n.x * n.y};
         const R a = abs2(n2);
         const R ia = R(1) / a;
         StageA<R> A;
-        A.d2x = (n.x - n0) * (n.x + n0) - n.y * n.y;
+        A.d2x = (n.x - n0v) * (n.x + n0v) - n.y * n.y;
         A.n2y = n2.y;
         A.in2x = n2.x * ia;
         A.in2y = -n2.y * ia;
