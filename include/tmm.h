@@ -189,6 +189,21 @@ TMM_API int32_t tmm_version(void);
  */
 TMM_API tmm_status tmm_probe_fma_rate(int32_t prec, double *flops_per_s, float *ms, void *stream);
 
+/*
+ * Building block of the learned surrogate, exported for testing: one bf16
+ * tensor-core GEMM (tcgen05, TMA-fed) with a fused epilogue.
+ *   D[M][N] = sum_k A[M][k] B[N][k];  A, B device bf16, row-major, K a
+ *   multiple of 8 and both base addresses 16-byte aligned.
+ *   epilogue 0: out f32 [M][N] = D + bias        (bias device [N] or NULL)
+ *            1: aux bf16 [M][N] = D + bias; out bf16 = GELU(aux)   (erf form)
+ *            2: out bf16 = D * GELU'(aux)        (aux device bf16 [M][N], read)
+ *            3: out f32 = clamp(D + bias, 0, 1)
+ * Synchronises `stream` and reports TMM_ERR_TIMEOUT if a pipeline wait of the
+ * kernel expired (the kernel then returns without finishing its tile).
+ */
+TMM_API tmm_status tmm_gemm_bf16(const void *A, const void *B, const float *bias, int32_t M, int32_t N,
+                                 int32_t K, int32_t epilogue, void *out, void *aux, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

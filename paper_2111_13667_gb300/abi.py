@@ -32,7 +32,7 @@ TMM_POL_P = 2
 
 EXPORTED = ("tmm_coh_batched", "tmm_coh_batched_ex", "tmm_workspace_size", "tmm_workspace_status",
             "tmm_coh_grad", "tmm_status_string", "tmm_last_cuda_error", "tmm_version",
-            "tmm_probe_fma_rate")
+            "tmm_probe_fma_rate", "tmm_gemm_bf16")
 
 
 class TmmProblem(ctypes.Structure):
@@ -92,8 +92,10 @@ def load(path: Optional[str] = None):
         lib.tmm_version.restype = ctypes.c_int32
         lib.tmm_probe_fma_rate.argtypes = [ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(ctypes.c_float), vp]
+        lib.tmm_gemm_bf16.argtypes = [vp, vp, vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                      vp, vp, vp]
         for name in ("tmm_coh_batched", "tmm_coh_batched_ex", "tmm_workspace_size",
-                     "tmm_workspace_status", "tmm_coh_grad", "tmm_probe_fma_rate"):
+                     "tmm_workspace_status", "tmm_coh_grad", "tmm_probe_fma_rate", "tmm_gemm_bf16"):
             getattr(lib, name).restype = ctypes.c_int
         if path is None:
             _lib = lib
@@ -250,6 +252,15 @@ def tmm_probe_fma_rate(prec: int, stream=None):
     _check("tmm_probe_fma_rate", load().tmm_probe_fma_rate(int(prec), ctypes.byref(f), ctypes.byref(ms),
                                                            _stream(stream)))
     return f.value, ms.value
+
+
+def tmm_gemm_bf16(A: torch.Tensor, B: torch.Tensor, bias: Optional[torch.Tensor], epilogue: int,
+                  out: torch.Tensor, aux: Optional[torch.Tensor] = None, stream=None):
+    """out = epilogue(A @ B^T) on the tcgen05 GEMM (A [M][K], B [N][K] bf16)."""
+    M, K = A.shape
+    N = B.shape[0]
+    _check("tmm_gemm_bf16", load().tmm_gemm_bf16(_ptr(A), _ptr(B), _ptr(bias), M, N, K, epilogue, _ptr(out),
+                                                 _ptr(aux), _stream(stream)))
 
 
 def tmm_version() -> int:

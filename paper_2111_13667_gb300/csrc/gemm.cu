@@ -1,0 +1,148 @@
+// gemm.cu -- host side of the tcgen05 bf16 GEMM: TMA tensor maps, tile and
+// pipeline-depth choice, launch, and the exported test entry point.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "tcgen05_gemm.cuh"
+#include "tmm_internal.h"
+
+namespace tmm {
+namespace gemm {
+
+// Device-side error flag of the GEMM pipeline waits (one per device).
+static __device__ int g_gemm_err;
+
+// cuTensorMapEncodeTiled, resolved through the runtime so that the library
+// itself does not link the driver (it must load on machines without one).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_tiled()
+{
+    static std::once_flag once;
+    static EncodeTiledFn fn = nullptr;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    });
+    return fn;
+}
+
+static tmm_status make_tmap(CUtensorMap *map, const void *base, int rows, int K, int ld, int box_rows)
+{
+    if (reinterpret_cast<uintptr_t>(base) % 16 != 0 || (ld * 2) % 16 != 0) return TMM_ERR_INVALID_ARG;
+    EncodeTiledFn cuTensorMapEncodeTiled = encode_tiled();
+    if (!cuTensorMapEncodeTiled) return TMM_ERR_UNSUPPORTED;
+    const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    CUresult r = cuTensorMapEncodeTiled(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims,
+                                        strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? TMM_OK : TMM_ERR_INVALID_ARG;
+}
+
+template <int BN, int STAGES>
+static tmm_status launch_bn(const CUtensorMap &ta, const CUtensorMap &tb, int M, int N, int K, const EpiArgs &ep,
+                            cudaStream_t st)
+{
+    auto k = gemm_bf16_kernel<BN, STAGES>;
+    constexpr size_t smem = GemmSmem<BN, STAGES>::total;
+    static int set_dev[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (dev < 0 || dev >= 64) return TMM_ERR_UNSUPPORTED;
+    if (!set_dev[dev]) {
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return cuda_fail(e);
+        set_dev[dev] = 1;
+    }
+    const dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
+    k<<<grid, 128, smem, st>>>(ta, tb, M, N, K, ep);
+    return check_launch();
+}
+
+int *error_flag()
+{
+    int *p = nullptr;
+    cudaGetSymbolAddress(reinterpret_cast<void **>(&p), g_gemm_err);
+    return p;
+}
+
+// D[M][N] = A[M][K] . B[N][K]^T with the requested epilogue.  A, B row-major
+// bf16 with leading dimensions lda, ldb (elements, multiples of 8).
+tmm_status gemm(const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *B, int ldb, int M, int N, int K, EpiArgs ep,
+                cudaStream_t st)
+{
+    if (M <= 0 || N <= 0 || K <= 0) return TMM_OK;
+    if (lda < K || ldb < K || (lda % 8) || (ldb % 8) || ep.ldo < N) return TMM_ERR_INVALID_ARG;
+    if (!ep.err) {
+        ep.err = error_flag();
+        if (!ep.err) return TMM_ERR_CUDA;
+    }
+    const int BN = N >= 256 ? 256 : (N >= 128 ? 128 : 64);
+    CUtensorMap ta, tb;
+    tmm_status s = make_tmap(&ta, A, M, K, lda, BM);
+    if (s != TMM_OK) return s;
+    s = make_tmap(&tb, B, N, K, ldb, BN);
+    if (s != TMM_OK) return s;
+    if (BN == 256) return launch_bn<256, 4>(ta, tb, M, N, K, ep, st);
+    if (BN == 128) return launch_bn<128, 6>(ta, tb, M, N, K, ep, st);
+    return launch_bn<64, 8>(ta, tb, M, N, K, ep, st);
+}
+
+// Clear the wait-error flag (a set flag makes every later wait give up).
+tmm_status clear_error(cudaStream_t st)
+{
+    int *p = error_flag();
+    if (!p) return TMM_ERR_CUDA;
+    cudaError_t e = cudaMemsetAsync(p, 0, sizeof(int), st);
+    return e == cudaSuccess ? TMM_OK : cuda_fail(e);
+}
+
+tmm_status gemm_status(cudaStream_t st)
+{
+    int h = 0;
+    cudaError_t e = cudaMemcpyFromSymbolAsync(&h, g_gemm_err, sizeof(int), 0, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    return h ? TMM_ERR_TIMEOUT : TMM_OK;
+}
+
+}  // namespace gemm
+}  // namespace tmm
+
+using namespace tmm;
+
+extern "C" TMM_API tmm_status tmm_gemm_bf16(const void *A, const void *B, const float *bias, int32_t M, int32_t N,
+                                            int32_t K, int32_t epilogue, void *out, void *aux, void *stream)
+{
+    if (!A || !B || !out || M < 0 || N < 0 || K < 0 || epilogue < 0 || epilogue > 3) return TMM_ERR_INVALID_ARG;
+    if ((epilogue == gemm::EPI_DGELU) && !aux) return TMM_ERR_INVALID_ARG;
+    gemm::EpiArgs ep{};
+    ep.epi = epilogue;
+    ep.bias = bias;
+    ep.ldo = N;
+    if (epilogue == gemm::EPI_F32 || epilogue == gemm::EPI_F32_CLAMP) ep.out_f32 = static_cast<float *>(out);
+    else ep.out_bf = static_cast<__nv_bfloat16 *>(out);
+    ep.aux = static_cast<__nv_bfloat16 *>(aux);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    tmm_status s = gemm::clear_error(st);
+    if (s != TMM_OK) return s;
+    s = gemm::gemm(static_cast<const __nv_bfloat16 *>(A), K, static_cast<const __nv_bfloat16 *>(B), K, M,
+                              N, K, ep, st);
+    if (s != TMM_OK) return s;
+    return gemm::gemm_status(st);
+}
