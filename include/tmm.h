@@ -190,6 +190,30 @@ TMM_API int32_t tmm_version(void);
 TMM_API tmm_status tmm_probe_fma_rate(int32_t prec, double *flops_per_s, float *ms, void *stream);
 
 /*
+ * Allocation-free variant of the persistent launch (no counterpart in the
+ * paper; it serves callers that cannot allocate device memory at call time,
+ * such as request paths that must not take cudaMalloc's implicit device
+ * synchronisation, or programs whose device memory is owned by another
+ * allocator).  Same results as tmm_coh_batched_ex with cfg->persistent = 1
+ * and a caller workspace, but the scratch (work counter, error flag, sort
+ * buckets, stack order) lives in a 1 MiB array inside the library that every
+ * GPU which loads it keeps until exit; nothing is allocated or freed.
+ *   cfg      may be NULL; persistent is forced on; max_items_per_block must be 0
+ *            (there is no workspace to report a timeout through).
+ *   Limit    the problem's persistent workspace (tmm_workspace_size with
+ *            persistent = 1: about 4 * (S + 2 * (L_max + 2)) bytes plus
+ *            headers) must fit in 1 MiB, i.e. up to ~261,000 stacks for small
+ *            L_max; larger problems return TMM_ERR_NOMEM before any launch.
+ *   The first call on a device looks up the array's device address (once per
+ *   device, with that device current); make that first call before any stream
+ *   capture.  Every call shares the one array: calls whose work overlaps on the
+ *   GPU (several streams, several host threads) race and must be serialised
+ *   by the caller.  Each call zeroes what must start at zero itself.
+ */
+TMM_API tmm_status tmm_coh_batched_noalloc(const tmm_problem *p, const tmm_launch_cfg *cfg, void *R, void *T,
+                                           void *stream);
+
+/*
  * Building block of the learned surrogate, exported for testing: one bf16
  * tensor-core GEMM (tcgen05, TMA-fed) with a fused epilogue.
  *   D[M][N] = sum_k A[M][k] B[N][k];  A, B device bf16, row-major, K a

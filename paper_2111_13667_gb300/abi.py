@@ -32,7 +32,7 @@ TMM_POL_P = 2
 
 EXPORTED = ("tmm_coh_batched", "tmm_coh_batched_ex", "tmm_workspace_size", "tmm_workspace_status",
             "tmm_coh_grad", "tmm_status_string", "tmm_last_cuda_error", "tmm_version",
-            "tmm_probe_fma_rate", "tmm_gemm_bf16")
+            "tmm_probe_fma_rate", "tmm_gemm_bf16", "tmm_coh_batched_noalloc")
 
 
 class TmmProblem(ctypes.Structure):
@@ -94,8 +94,10 @@ def load(path: Optional[str] = None):
                                            ctypes.POINTER(ctypes.c_float), vp]
         lib.tmm_gemm_bf16.argtypes = [vp, vp, vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                       vp, vp, vp]
+        lib.tmm_coh_batched_noalloc.argtypes = [P, C, vp, vp, vp]
         for name in ("tmm_coh_batched", "tmm_coh_batched_ex", "tmm_workspace_size",
-                     "tmm_workspace_status", "tmm_coh_grad", "tmm_probe_fma_rate", "tmm_gemm_bf16"):
+                     "tmm_workspace_status", "tmm_coh_grad", "tmm_probe_fma_rate", "tmm_gemm_bf16",
+                     "tmm_coh_batched_noalloc"):
             getattr(lib, name).restype = ctypes.c_int
         if path is None:
             _lib = lib
@@ -227,6 +229,15 @@ def tmm_coh_batched_ex(prob: DeviceProblem, cfg: Optional[TmmLaunchCfg], workspa
     _check("tmm_coh_batched_ex", load().tmm_coh_batched_ex(ctypes.byref(s), ctypes.byref(cfg) if cfg else None,
                                                            _ptr(workspace), ws_bytes, _ptr(R), _ptr(T),
                                                            _stream(stream)))
+
+
+def tmm_coh_batched_noalloc(prob: DeviceProblem, cfg: Optional[TmmLaunchCfg], R: torch.Tensor,
+                            T: Optional[torch.Tensor] = None, stream=None):
+    """Persistent launch whose scratch is the library's own static device array
+    (no allocation; calls that overlap on the GPU race)."""
+    s = prob.struct()
+    _check("tmm_coh_batched_noalloc", load().tmm_coh_batched_noalloc(
+        ctypes.byref(s), ctypes.byref(cfg) if cfg else None, _ptr(R), _ptr(T), _stream(stream)))
 
 
 def tmm_workspace_status(workspace: torch.Tensor, stream=None) -> int:
