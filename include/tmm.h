@@ -190,6 +190,64 @@ TMM_API int32_t tmm_version(void);
 TMM_API tmm_status tmm_probe_fma_rate(int32_t prec, double *flops_per_s, float *ms, void *stream);
 
 /*
+ * Learned surrogate (motivated by the paper's dataset generation for machine
+ * learning, abstract and Sec. "Core functionality speedup and dataset
+ * generation"; the network itself is not in the paper): an MLP from the L
+ * thicknesses of a fixed stack to its R spectra, s then p, theta-major,
+ * lambda fastest (2 n_theta n_lambda outputs).  Hidden layers of width
+ * `hidden` with GELU (erf form), a linear head; bf16 weights and activations,
+ * fp32 accumulation on the tcgen05 tensor cores; Adam on fp32 masters.  The
+ * exact transfer-matrix kernel (FP32) generates training spectra and judges
+ * inference outputs.  The object owns its device memory (weights, optimizer
+ * state, batch buffers grown on demand; growth synchronises the device).
+ */
+typedef struct tmm_surrogate tmm_surrogate;
+typedef struct {
+    int32_t n_layers;        /* L finite layers, 1..64 */
+    const double *n_media;   /* host complex [L+2] (re, im): media 0..L+1; Im n_0 = 0 */
+    int32_t n_lambda;
+    const double *lambda;    /* host [n_lambda], nm */
+    int32_t n_theta;
+    const double *theta;     /* host [n_theta], radians */
+    double d_min, d_max;     /* thickness range; inputs are mapped to [-1, 1] */
+    int32_t hidden;          /* width, multiple of 64 */
+    int32_t depth;           /* hidden layers, 1..16 */
+    uint64_t seed;           /* weight initialisation */
+} tmm_surrogate_desc;
+
+TMM_API tmm_status tmm_surrogate_create(const tmm_surrogate_desc *desc, tmm_surrogate **out);
+TMM_API void tmm_surrogate_destroy(tmm_surrogate *s);
+TMM_API int32_t tmm_surrogate_outputs(const tmm_surrogate *s);
+TMM_API int64_t tmm_surrogate_parameters(const tmm_surrogate *s);
+/* Exact spectra (training targets): d device [B][L] f32 -> R device [B][outputs] f32. */
+TMM_API tmm_status tmm_surrogate_generate(tmm_surrogate *s, const float *d, int32_t B, float *R, void *stream);
+/* One Adam step on the MSE between the network and R_target (device [B][outputs]);
+ * B a multiple of 8, >= 128; loss: device f32 (mean squared error) or NULL. */
+TMM_API tmm_status tmm_surrogate_train_step(tmm_surrogate *s, const float *d, const float *R_target, int32_t B,
+                                            float lr, float *loss, void *stream);
+/* R device [B][outputs] = clamp(network(d), 0, 1).  Every round(1/judge_fraction)-th
+ * row (judge_fraction in [0, 1]; 0 = none, 1 = all) is recomputed with the exact
+ * kernel; a judged row whose max |R - R_exact| exceeds tol is replaced by the exact
+ * spectrum.  n_fallback (device int32) and max_err (device f32, largest judged
+ * error) may be NULL. */
+TMM_API tmm_status tmm_surrogate_infer(tmm_surrogate *s, const float *d, int32_t B, float *R, float judge_fraction,
+                                       float tol, int32_t *n_fallback, float *max_err, void *stream);
+/* Read-only view of layer i (0 .. depth; depth = the head): device pointers to
+ * the fp32 master weights W [N][K] (input columns >= Kvalid are zero padding),
+ * bias [N], and the gradients dW, db of the last train_step (taken before its
+ * Adam update). */
+typedef struct {
+    int32_t N, K, Kvalid;
+    const float *W, *b, *dW, *db;
+} tmm_surrogate_layer_view;
+TMM_API tmm_status tmm_surrogate_layer(const tmm_surrogate *s, int32_t i, tmm_surrogate_layer_view *out);
+/* TMM_OK, or TMM_ERR_TIMEOUT if a tensor-core pipeline wait expired (synchronises). */
+TMM_API tmm_status tmm_surrogate_status(tmm_surrogate *s, void *stream);
+/* Checkpoint: weights, Adam moments and step count (host file). */
+TMM_API tmm_status tmm_surrogate_save(tmm_surrogate *s, const char *path);
+TMM_API tmm_status tmm_surrogate_load(tmm_surrogate *s, const char *path);
+
+/*
  * Allocation-free variant of the persistent launch (no counterpart in the
  * paper; it serves callers that cannot allocate device memory at call time,
  * such as request paths that must not take cudaMalloc's implicit device

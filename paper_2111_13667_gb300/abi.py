@@ -32,7 +32,10 @@ TMM_POL_P = 2
 
 EXPORTED = ("tmm_coh_batched", "tmm_coh_batched_ex", "tmm_workspace_size", "tmm_workspace_status",
             "tmm_coh_grad", "tmm_status_string", "tmm_last_cuda_error", "tmm_version",
-            "tmm_probe_fma_rate", "tmm_gemm_bf16", "tmm_coh_batched_noalloc")
+            "tmm_probe_fma_rate", "tmm_gemm_bf16", "tmm_coh_batched_noalloc",
+            "tmm_surrogate_create", "tmm_surrogate_destroy", "tmm_surrogate_outputs", "tmm_surrogate_parameters",
+            "tmm_surrogate_generate", "tmm_surrogate_train_step", "tmm_surrogate_infer", "tmm_surrogate_layer",
+            "tmm_surrogate_status", "tmm_surrogate_save", "tmm_surrogate_load")
 
 
 class TmmProblem(ctypes.Structure):
@@ -52,6 +55,21 @@ class TmmLaunchCfg(ctypes.Structure):
     _fields_ = [("tile_lambda", ctypes.c_int32), ("tile_theta", ctypes.c_int32),
                 ("persistent", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
                 ("max_items_per_block", ctypes.c_int32)]
+
+
+class TmmSurrogateDesc(ctypes.Structure):
+    """Mirror of ``tmm_surrogate_desc``."""
+    _fields_ = [("n_layers", ctypes.c_int32), ("n_media", ctypes.POINTER(ctypes.c_double)),
+                ("n_lambda", ctypes.c_int32), ("lambda_", ctypes.POINTER(ctypes.c_double)),
+                ("n_theta", ctypes.c_int32), ("theta", ctypes.POINTER(ctypes.c_double)),
+                ("d_min", ctypes.c_double), ("d_max", ctypes.c_double), ("hidden", ctypes.c_int32),
+                ("depth", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+
+
+class TmmSurrogateLayerView(ctypes.Structure):
+    """Mirror of ``tmm_surrogate_layer_view``."""
+    _fields_ = [("N", ctypes.c_int32), ("K", ctypes.c_int32), ("Kvalid", ctypes.c_int32),
+                ("W", ctypes.c_void_p), ("b", ctypes.c_void_p), ("dW", ctypes.c_void_p), ("db", ctypes.c_void_p)]
 
 
 class TmmError(RuntimeError):
@@ -95,6 +113,25 @@ def load(path: Optional[str] = None):
         lib.tmm_gemm_bf16.argtypes = [vp, vp, vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                       vp, vp, vp]
         lib.tmm_coh_batched_noalloc.argtypes = [P, C, vp, vp, vp]
+        i32, f32 = ctypes.c_int32, ctypes.c_float
+        lib.tmm_surrogate_create.argtypes = [ctypes.POINTER(TmmSurrogateDesc), ctypes.POINTER(vp)]
+        lib.tmm_surrogate_destroy.argtypes = [vp]
+        lib.tmm_surrogate_destroy.restype = None
+        lib.tmm_surrogate_outputs.argtypes = [vp]
+        lib.tmm_surrogate_outputs.restype = i32
+        lib.tmm_surrogate_parameters.argtypes = [vp]
+        lib.tmm_surrogate_parameters.restype = ctypes.c_int64
+        lib.tmm_surrogate_generate.argtypes = [vp, vp, i32, vp, vp]
+        lib.tmm_surrogate_train_step.argtypes = [vp, vp, vp, i32, f32, vp, vp]
+        lib.tmm_surrogate_infer.argtypes = [vp, vp, i32, vp, f32, f32, vp, vp, vp]
+        lib.tmm_surrogate_layer.argtypes = [vp, i32, ctypes.POINTER(TmmSurrogateLayerView)]
+        lib.tmm_surrogate_status.argtypes = [vp, vp]
+        lib.tmm_surrogate_save.argtypes = [vp, ctypes.c_char_p]
+        lib.tmm_surrogate_load.argtypes = [vp, ctypes.c_char_p]
+        for name in ("tmm_surrogate_create", "tmm_surrogate_generate", "tmm_surrogate_train_step",
+                     "tmm_surrogate_infer", "tmm_surrogate_layer", "tmm_surrogate_status", "tmm_surrogate_save",
+                     "tmm_surrogate_load"):
+            getattr(lib, name).restype = ctypes.c_int
         for name in ("tmm_coh_batched", "tmm_coh_batched_ex", "tmm_workspace_size",
                      "tmm_workspace_status", "tmm_coh_grad", "tmm_probe_fma_rate", "tmm_gemm_bf16",
                      "tmm_coh_batched_noalloc"):

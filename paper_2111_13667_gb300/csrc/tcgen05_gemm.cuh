@@ -43,7 +43,8 @@ struct EpiArgs {
     float *out_f32;         // [M][ldo]
     __nv_bfloat16 *out_bf;  // [M][ldo]
     __nv_bfloat16 *aux;     // [M][ldo] pre-activation (written by GELU, read by DGELU)
-    int ldo;
+    __nv_bfloat16 *out_bfT; // [N][ldoT] transposed copy of out_bf, or null
+    int ldo, ldoT;
     int *err;               // error flag (device)
 };
 
@@ -293,12 +294,18 @@ __global__ void __launch_bounds__(128, 1)
                     ep.out_f32[o + i] = z;
                 } else if (ep.epi == EPI_F32_CLAMP) {
                     ep.out_f32[o + i] = fminf(fmaxf(z, 0.0f), 1.0f);
-                } else if (ep.epi == EPI_GELU) {
-                    const __nv_bfloat16 zb = __float2bfloat16(z);
-                    if (ep.aux) ep.aux[o + i] = zb;
-                    ep.out_bf[o + i] = __float2bfloat16(gelu(__bfloat162float(zb)));
-                } else {  // EPI_DGELU
-                    ep.out_bf[o + i] = __float2bfloat16(v[i] * gelu_grad(__bfloat162float(ep.aux[o + i])));
+                } else {
+                    __nv_bfloat16 y;
+                    if (ep.epi == EPI_GELU) {
+                        const __nv_bfloat16 zb = __float2bfloat16(z);
+                        if (ep.aux) ep.aux[o + i] = zb;
+                        y = __float2bfloat16(gelu(__bfloat162float(zb)));
+                    } else {  // EPI_DGELU
+                        y = __float2bfloat16(v[i] * gelu_grad(__bfloat162float(ep.aux[o + i])));
+                    }
+                    ep.out_bf[o + i] = y;
+                    // lanes hold consecutive rows: the transposed store is coalesced
+                    if (ep.out_bfT) ep.out_bfT[(long long)col * ep.ldoT + row] = y;
                 }
             }
         }
