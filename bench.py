@@ -251,6 +251,8 @@ def gpu_arm(args):
     if not args.skip_extras:
         out["ragged"] = bench_ragged(args, torch, abi, W, flush, world, max_over_ranks)
         out["adjoint"] = bench_adjoint(args, torch, abi, W, flush, world, max_over_ranks)
+        if not args.skip_surrogate:
+            out["surrogate"] = bench_surrogate(args, torch, abi, W, flush, world, max_over_ranks)
 
     head = out["f32"]
     line = {
@@ -266,7 +268,7 @@ def gpu_arm(args):
         "roofline": head["roofline"], "clocks": head.get("clocks"), "e2e": head.get("e2e"),
         "gpu_launches": args.steps,
     }
-    for k in ("f64", "ragged", "adjoint"):
+    for k in ("f64", "ragged", "adjoint", "surrogate"):
         if k in out:
             line[k] = out[k]
     line["cpu_baseline"] = cpu_baseline(w, args) if (rank == 0 and world == 1 and not args.skip_cpu) else None
@@ -334,6 +336,68 @@ def bench_adjoint(args, torch, abi, W, flush, world, max_over_ranks):
         ms = max_over_ranks(sum(t) / len(t))
         res[prec] = {"value": w.evals * world / (ms * 1e-3), "ms_per_step": ms, "steps": steps}
     return res
+
+
+def bench_surrogate(args, torch, abi, W, flush, world, max_over_ranks):
+    """Learned surrogate (20 x 1.46/2.35 stack, 256 lambda x 8 theta x s+p = 4096
+    outputs, 6 x 1024 GELU MLP): trained here on GPU-generated spectra, then
+    inference on 65536 stacks vs the exact kernel on the same stacks."""
+    from paper_2111_13667_gb300.surrogate import Surrogate, make_dataset, random_thicknesses, train
+    sur = Surrogate()
+    t0 = time.perf_counter()
+    d, R = make_dataset(sur, args.sur_train, seed=4)
+    gen_s = time.perf_counter() - t0
+    rep = train(sur, d, R, steps=args.sur_steps, batch=8192, lr_max=1e-3, warmup=100)
+    del d, R
+    torch.cuda.empty_cache()
+    B = 65536
+    dt = random_thicknesses(B, seed=44)
+    exact = sur.generate(dt)
+    raw = sur.infer(dt)
+    torch.cuda.synchronize()
+    err = (raw - exact).abs().amax(dim=1)
+    mean_abs = float((raw - exact).abs().mean())
+    within = float((err <= 1e-3).float().mean())
+    outR = torch.empty_like(exact)
+    stats = torch.zeros(2, dtype=torch.int32, device=dt.device)
+    steps = max(3, args.steps // 2)
+    t_exact = time_steps(lambda: sur.generate(dt, outR), steps, 3, torch, flush)
+    t_net = time_steps(lambda: sur.infer(dt, out=outR), steps, 3, torch, flush)
+    t_judge = time_steps(lambda: sur.infer(dt, 1.0, 1e-3, out=outR, stats=stats), steps, 3, torch, flush)
+    n_fb = int(stats[0].item())
+    judged_err = float((outR - exact).abs().max())
+    ms_e = max_over_ranks(sum(t_exact) / len(t_exact))
+    ms_n = max_over_ranks(sum(t_net) / len(t_net))
+    ms_j = max_over_ranks(sum(t_judge) / len(t_judge))
+    flops = 2.0 * B * sum(n * k for n, k in sur_shapes(sur))
+    peaks = measured_peaks() or {}
+    peak = peaks.get("bf16_tflops")
+    peak_src = "MEASURED_PEAKS.json bf16_tflops (burst)" if peak else "fallback 1900 TFLOP/s (profiling recipe)"
+    peak = float(peak) if peak else 1900.0
+    achieved = flops / (ms_n * 1e-3) / 1e12
+    status = sur.status()
+    sur.close()
+    return {"unit": "spectra/s", "outputs_per_spectrum": int(exact.shape[1]), "batch": B,
+            "parameters": sur.parameters, "dataset_spectra": args.sur_train, "dataset_gen_s": gen_s,
+            "train": {"steps": rep.steps, "batch": rep.batch, "seconds": rep.seconds, "loss_first": rep.loss_first,
+                      "loss_last": rep.loss_last},
+            "exact_tmm": {"value": B * world / (ms_e * 1e-3), "ms_per_step": ms_e},
+            "network_only": {"value": B * world / (ms_n * 1e-3), "ms_per_step": ms_n,
+                             "max_abs_err": float(err.max()), "mean_abs_err": mean_abs,
+                             "rows_within_1e-3": within},
+            "judged_all_fallback": {"value": B * world / (ms_j * 1e-3), "ms_per_step": ms_j,
+                                    "fallback_rows": n_fb, "max_abs_err_delivered": judged_err, "tol": 1e-3},
+            "speedup_network_only": ms_e / ms_n, "speedup_at_max_err_1e-3": ms_e / ms_j,
+            "roofline": {"bound": "tensor", "kernel": "gemm_bf16_kernel (7 GEMMs of one inference)",
+                         "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                         "peak_source": peak_src, "work": f"{flops / 1e12:.3f} TFLOP per 65536-spectrum batch"},
+            "status": status, "steps": steps}
+
+
+def sur_shapes(sur):
+    """(N, K) of every GEMM of one inference (K = 64-padded input for the first)."""
+    shapes = [(sur.hidden, 64)] + [(sur.hidden, sur.hidden)] * (sur.depth - 1) + [(sur.outputs, sur.hidden)]
+    return shapes
 
 
 def R_bytes(w, elt):
@@ -419,6 +483,9 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-extras", action="store_true", help="headline only (no ragged / adjoint lines)")
+    ap.add_argument("--skip-surrogate", action="store_true")
+    ap.add_argument("--sur-train", type=int, default=2_000_000, help="training spectra (GPU-generated)")
+    ap.add_argument("--sur-steps", type=int, default=2000, help="training steps of 8192 spectra")
     ap.add_argument("--stacks", type=int, default=0, help="shrink the workload (profiling runs only)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     args = ap.parse_args()

@@ -10,7 +10,7 @@ namespace tmm {
 constexpr int kChains = 8;
 
 // Store target that keeps the chains from being optimised away.
-static __device__ double g_probe_sink;
+__device__ double tmm_probe_sink;
 
 template <typename R>
 __global__ void __launch_bounds__(256) fma_chains(int iters, R a, R b)
@@ -25,7 +25,7 @@ __global__ void __launch_bounds__(256) fma_chains(int iters, R a, R b)
     R acc = R(0);
 #pragma unroll
     for (int c = 0; c < kChains; ++c) acc += v[c];
-    if (acc == R(12345.678)) g_probe_sink = (double)acc;
+    if (acc == R(12345.678)) tmm_probe_sink = (double)acc;
 }
 
 template <typename R>

@@ -178,6 +178,13 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16])
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 32 consecutive fp32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float v[32])
+{
+    tmem_ld16(taddr, v);
+    tmem_ld16(taddr + 16, v + 16);
+}
+
 // GELU, erf form (CUDA's erff), and its derivative.
 __device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
 __device__ __forceinline__ float gelu_grad(float z)
@@ -278,36 +285,50 @@ __global__ void __launch_bounds__(128, 1)
     const bool have = __all_sync(0xffffffffu, mbar_wait(done, 0, ep.err)) && s_fail == 0;
     if (!have && lane == 0) atomicExch(ep.err, 1);
     tc_fence_after();
-    const int row = m0 + warp * 32 + lane;
+    // Each warp stages its 32 rows x 32 columns in the (now idle) operand ring
+    // and writes them back row by row, so every store instruction covers
+    // consecutive addresses of one row.
+    const int row0 = m0 + warp * 32;
+    const int row = row0 + lane;
+    float *stage = reinterpret_cast<float *>(smem) + warp * (32 * 33);
     if (have) {
-        for (int c = 0; c < BN; c += 16) {
-            float v[16];
-            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
-            if (row >= M) continue;
-            const long long o = (long long)row * ep.ldo + n0 + c;
+        for (int c = 0; c < BN; c += 32) {
+            float v[32];
+            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
 #pragma unroll
-            for (int i = 0; i < 16; ++i) {
+            for (int i = 0; i < 32; ++i) {
                 const int col = n0 + c + i;
-                if (col >= N) break;
-                float z = v[i] + (ep.bias ? ep.bias[col] : 0.0f);
+                const bool in = row < M && col < N;
+                float z = v[i] + ((ep.bias && col < N) ? ep.bias[col] : 0.0f);
+                float y;
                 if (ep.epi == EPI_F32) {
-                    ep.out_f32[o + i] = z;
+                    y = z;
                 } else if (ep.epi == EPI_F32_CLAMP) {
-                    ep.out_f32[o + i] = fminf(fmaxf(z, 0.0f), 1.0f);
-                } else {
-                    __nv_bfloat16 y;
-                    if (ep.epi == EPI_GELU) {
-                        const __nv_bfloat16 zb = __float2bfloat16(z);
-                        if (ep.aux) ep.aux[o + i] = zb;
-                        y = __float2bfloat16(gelu(__bfloat162float(zb)));
-                    } else {  // EPI_DGELU
-                        y = __float2bfloat16(v[i] * gelu_grad(__bfloat162float(ep.aux[o + i])));
-                    }
-                    ep.out_bf[o + i] = y;
-                    // lanes hold consecutive rows: the transposed store is coalesced
-                    if (ep.out_bfT) ep.out_bfT[(long long)col * ep.ldoT + row] = y;
+                    y = fminf(fmaxf(z, 0.0f), 1.0f);
+                } else if (ep.epi == EPI_GELU) {
+                    const __nv_bfloat16 zb = __float2bfloat16(z);
+                    if (ep.aux && in) ep.aux[(long long)row * ep.ldo + col] = zb;
+                    y = gelu(__bfloat162float(zb));
+                } else {  // EPI_DGELU
+                    y = in ? v[i] * gelu_grad(__bfloat162float(ep.aux[(long long)row * ep.ldo + col])) : 0.0f;
+                }
+                if (ep.out_bfT && in)  // lanes hold consecutive rows: coalesced
+                    ep.out_bfT[(long long)col * ep.ldoT + row] = __float2bfloat16(y);
+                stage[lane * 33 + i] = y;
+            }
+            __syncwarp();
+            const int col = n0 + c + lane;
+            if (col < N) {
+                for (int r = 0; r < 32; ++r) {
+                    const int rr = row0 + r;
+                    if (rr >= M) break;
+                    const float y = stage[r * 33 + lane];
+                    const long long o = (long long)rr * ep.ldo + col;
+                    if (ep.epi == EPI_F32 || ep.epi == EPI_F32_CLAMP) ep.out_f32[o] = y;
+                    else ep.out_bf[o] = __float2bfloat16(y);
                 }
             }
+            __syncwarp();
         }
     }
     tc_fence_before();

@@ -107,7 +107,7 @@ class _DeviceArray:
     """A float32 device buffer owned by the library, exposed for a copy."""
 
     def __init__(self, ptr: int, shape):
-        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": "<f4", "data": (int(ptr), True),
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": "<f4", "data": (int(ptr), False),
                                          "version": 3, "strides": None}
 
 
