@@ -4,6 +4,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "tcgen05_gemm.cuh"
@@ -68,8 +69,12 @@ static tmm_status launch_bn(const CUtensorMap &ta, const CUtensorMap &tb, int M,
         if (e != cudaSuccess) return cuda_fail(e);
         set_dev[dev] = 1;
     }
-    const dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
-    k<<<grid, 128, smem, st>>>(ta, tb, M, N, K, ep);
+    DeviceInfo di;
+    tmm_status s = device_info(&di);
+    if (s != TMM_OK) return s;
+    const long long tiles = (long long)((M + BM - 1) / BM) * ((N + BN - 1) / BN);
+    const int grid = (int)std::min<long long>(tiles, di.sms);
+    k<<<grid, kGemmThreads, smem, st>>>(ta, tb, M, N, K, ep);
     return check_launch();
 }
 
@@ -97,9 +102,9 @@ tmm_status gemm(const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *B, int ldb
     if (s != TMM_OK) return s;
     s = make_tmap(&tb, B, N, K, ldb, BN);
     if (s != TMM_OK) return s;
-    if (BN == 256) return launch_bn<256, 4>(ta, tb, M, N, K, ep, st);
-    if (BN == 128) return launch_bn<128, 6>(ta, tb, M, N, K, ep, st);
-    return launch_bn<64, 8>(ta, tb, M, N, K, ep, st);
+    if (BN == 256) return launch_bn<256, 3>(ta, tb, M, N, K, ep, st);
+    if (BN == 128) return launch_bn<128, 5>(ta, tb, M, N, K, ep, st);
+    return launch_bn<64, 6>(ta, tb, M, N, K, ep, st);
 }
 
 // Clear the wait-error flag (a set flag makes every later wait give up).

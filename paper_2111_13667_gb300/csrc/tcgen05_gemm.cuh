@@ -194,146 +194,208 @@ __device__ __forceinline__ float gelu_grad(float z)
     return cdf + z * pdf;
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+constexpr int kEpiWarps = 8;                       // epilogue warps (two per TMEM lane quarter)
+constexpr int kGemmThreads = 64 + 32 * kEpiWarps;  // producer warp, MMA warp, epilogue warps
+
 template <int BN, int STAGES>
 struct GemmSmem {
     static constexpr size_t a_bytes = (size_t)BM * BK * 2;
     static constexpr size_t b_bytes = (size_t)BN * BK * 2;
     static constexpr size_t ring = STAGES * (a_bytes + b_bytes);
-    static constexpr size_t bars = (2 * STAGES + 1) * 8 + 16;
-    static constexpr size_t total = 1024 + ring + bars;  // + alignment slack
+    static constexpr size_t stage = (size_t)kEpiWarps * 32 * 33 * 4;  // per-warp 32 x 33 floats
+    static constexpr size_t bars = (2 * STAGES + 5) * 8 + 16;
+    static constexpr size_t total = 1024 + ring + stage + bars;  // + alignment slack
 };
 
+// Apply the epilogue to one 32-column chunk of one warp's 32 rows: stage the
+// values in shared memory, then write them back row by row (coalesced).
+__device__ __forceinline__ void epilogue_chunk(const EpiArgs &ep, const float (&v)[32], float *stg, int row0, int n0c,
+                                               int M, int N, int lane)
+{
+    const int row = row0 + lane;
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+        const int col = n0c + i;
+        const bool in = row < M && col < N;
+        const float z = v[i] + ((ep.bias && col < N) ? ep.bias[col] : 0.0f);
+        float y;
+        if (ep.epi == EPI_F32) {
+            y = z;
+        } else if (ep.epi == EPI_F32_CLAMP) {
+            y = fminf(fmaxf(z, 0.0f), 1.0f);
+        } else if (ep.epi == EPI_GELU) {
+            const __nv_bfloat16 zb = __float2bfloat16(z);
+            if (ep.aux && in) ep.aux[(long long)row * ep.ldo + col] = zb;
+            y = gelu(__bfloat162float(zb));
+        } else {  // EPI_DGELU
+            y = in ? v[i] * gelu_grad(__bfloat162float(ep.aux[(long long)row * ep.ldo + col])) : 0.0f;
+        }
+        if (ep.out_bfT && in)  // lanes hold consecutive rows: coalesced
+            ep.out_bfT[(long long)col * ep.ldoT + row] = __float2bfloat16(y);
+        stg[lane * 33 + i] = y;
+    }
+    __syncwarp();
+    const int col = n0c + lane;
+    if (col < N) {
+        for (int r = 0; r < 32; ++r) {
+            const int rr = row0 + r;
+            if (rr >= M) break;
+            const float y = stg[r * 33 + lane];
+            const long long o = (long long)rr * ep.ldo + col;
+            if (ep.epi == EPI_F32 || ep.epi == EPI_F32_CLAMP) ep.out_f32[o] = y;
+            else ep.out_bf[o] = __float2bfloat16(y);
+        }
+    }
+    __syncwarp();
+}
+
+// Persistent, warp-specialised kernel.  Tiles (128 x BN) are dealt round-robin
+// to the CTAs (one per SM); the accumulator is double-buffered in tensor
+// memory (2 x BN columns) so the epilogue of one tile overlaps the MMAs of the
+// next.  Barriers: full/empty per ring stage (TMA <-> MMA), acc_full/acc_empty
+// per accumulator (MMA <-> epilogue), done (MMA drain before teardown).
 template <int BN, int STAGES>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(kGemmThreads, 1)
     gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int N,
                      int K, EpiArgs ep)
 {
     using L = GemmSmem<BN, STAGES>;
-    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t *sA = smem;
     uint8_t *sB = smem + STAGES * L::a_bytes;
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem + L::ring);
+    float *stg_all = reinterpret_cast<float *>(smem + L::ring);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + L::ring + L::stage);
     uint64_t *empty = full + STAGES;
-    uint64_t *done = empty + STAGES;
+    uint64_t *acc_full = empty + STAGES;
+    uint64_t *acc_empty = acc_full + 2;
+    uint64_t *done = acc_empty + 2;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
+    int *s_fail = reinterpret_cast<int *>(tmem_slot + 1);
 
-    __shared__ int s_fail;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const int n_tiles = (N + BN - 1) / BN;
+    const int tiles = ((M + BM - 1) / BM) * n_tiles;
     const int nkb = (K + BK - 1) / BK;
-    constexpr uint32_t kCols = BN < 32 ? 32 : BN;  // power of two >= 32
+    constexpr uint32_t kCols = 2 * BN;  // power of two, <= 512
 
     if (threadIdx.x == 0) {
-        s_fail = 0;
+        *s_fail = 0;
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], kEpiWarps);
         }
         mbar_init(done, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
-    if (warp == 0) tmem_alloc(tmem_slot, kCols);
+    if (warp == 1) tmem_alloc(tmem_slot, kCols);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    bool ok = true;
-    if (warp == 0 && lane == 0) {
-        // producer: TMA into the ring
-        int issued = 0;
-        for (int kb = 0; kb < nkb && ok; ++kb) {
-            const int s = kb % STAGES;
-            if (kb >= STAGES && !mbar_wait(&empty[s], ((kb / STAGES) - 1) & 1, ep.err)) {
-                ok = false;
-                break;
+    if (warp == 0) {
+        if (lane == 0) {
+            // producer: TMA into the ring, across all tiles of this CTA
+            long long it = 0;
+            bool ok = true;
+            for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
+                const int m0 = (tile / n_tiles) * BM, n0 = (tile % n_tiles) * BN;
+                for (int kb = 0; kb < nkb; ++kb, ++it) {
+                    const int s = (int)(it % STAGES);
+                    if (it >= STAGES && !mbar_wait(&empty[s], (uint32_t)(((it / STAGES) - 1) & 1), ep.err)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_expect_tx(&full[s], (uint32_t)(L::a_bytes + L::b_bytes));
+                    tma_load_2d(sA + s * L::a_bytes, &tmA, &full[s], kb * BK, m0);
+                    tma_load_2d(sB + s * L::b_bytes, &tmB, &full[s], kb * BK, n0);
+                }
             }
-            mbar_expect_tx(&full[s], (uint32_t)(L::a_bytes + L::b_bytes));
-            tma_load_2d(sA + s * L::a_bytes, &tmA, &full[s], kb * BK, m0);
-            tma_load_2d(sB + s * L::b_bytes, &tmB, &full[s], kb * BK, n0);
-            issued = kb + 1;
+            // every issued load must land before the CTA may exit
+            for (long long j = (it > STAGES ? it - STAGES : 0); j < it; ++j)
+                if (!mbar_wait(&full[j % STAGES], (uint32_t)((j / STAGES) & 1), ep.err)) ok = false;
+            if (!ok) *s_fail = 1;
         }
-        // drain: every issued load must have landed before this CTA can exit
-        for (int kb = (issued > STAGES ? issued - STAGES : 0); kb < issued; ++kb)
-            if (!mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1, ep.err)) ok = false;
-    } else if (warp == 1 && lane == 0) {
-        // MMA issuer
-        constexpr uint32_t idesc = instr_desc_bf16(BM, BN);
-        for (int kb = 0; kb < nkb; ++kb) {
-            const int s = kb % STAGES;
-            if (!mbar_wait(&full[s], (kb / STAGES) & 1, ep.err)) {
-                ok = false;
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // MMA issuer
+            constexpr uint32_t idesc = instr_desc_bf16(BM, BN);
+            long long it = 0;
+            int t = 0;
+            bool ok = true;
+            for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x, ++t) {
+                const int buf = t & 1, use = t >> 1;
+                if (t >= 2 && !mbar_wait(&acc_empty[buf], (uint32_t)((use - 1) & 1), ep.err)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d = tmem + (uint32_t)(buf * BN);
+                for (int kb = 0; kb < nkb; ++kb, ++it) {
+                    const int s = (int)(it % STAGES);
+                    if (!mbar_wait(&full[s], (uint32_t)((it / STAGES) & 1), ep.err)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+#pragma unroll
+                    for (int k = 0; k < BK / UMMA_K; ++k) {
+                        const uint64_t ad = smem_desc_sw128(sA + s * L::a_bytes + k * UMMA_K * 2);
+                        const uint64_t bd = smem_desc_sw128(sB + s * L::b_bytes + k * UMMA_K * 2);
+                        umma_bf16(d, ad, bd, idesc, (kb | k) != 0 ? 1u : 0u);
+                    }
+                    umma_commit(&empty[s]);
+                }
+                if (ok) umma_commit(&acc_full[buf]);
+            }
+            // drain: every MMA issued above completes before teardown
+            umma_commit(done);
+            if (!mbar_wait(done, 0, ep.err)) ok = false;
+            if (!ok) *s_fail = 1;
+        }
+    } else {
+        // epilogue warps: lane quarter q of TMEM, half of the tile's columns
+        const int ew = warp - 2, q = warp & 3, half = ew >> 2;
+        float *stg = stg_all + ew * (32 * 33);
+        int t = 0;
+        for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++t) {
+            const int buf = t & 1, use = t >> 1;
+            const bool have = __all_sync(0xffffffffu, mbar_wait(&acc_full[buf], (uint32_t)(use & 1), ep.err));
+            if (!have) {
+                if (lane == 0) *s_fail = 1;
                 break;
             }
             tc_fence_after();
-#pragma unroll
-            for (int k = 0; k < BK / UMMA_K; ++k) {
-                const uint64_t ad = smem_desc_sw128(sA + s * L::a_bytes + k * UMMA_K * 2);
-                const uint64_t bd = smem_desc_sw128(sB + s * L::b_bytes + k * UMMA_K * 2);
-                umma_bf16(tmem, ad, bd, idesc, (kb | k) != 0 ? 1u : 0u);
+            const int m0 = (tile / n_tiles) * BM, n0 = (tile % n_tiles) * BN;
+            const int row0 = m0 + q * 32;
+            for (int c = half * (BN / 2); c < (half + 1) * (BN / 2); c += 32) {
+                float v[32];
+                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * BN + c), v);
+                epilogue_chunk(ep, v, stg, row0, n0 + c, M, N, lane);
             }
-            umma_commit(&empty[s]);
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[buf]);
         }
-        umma_commit(done);  // arrives once every MMA issued above has completed
     }
-    if (!ok) s_fail = 1;
     __syncthreads();
-
-    // epilogue: warp w owns TMEM lanes 32w .. 32w + 31 = tile rows
-    const bool have = __all_sync(0xffffffffu, mbar_wait(done, 0, ep.err)) && s_fail == 0;
-    if (!have && lane == 0) atomicExch(ep.err, 1);
+    if (threadIdx.x == 0 && *s_fail) atomicExch(ep.err, 1);
     tc_fence_after();
-    // Each warp stages its 32 rows x 32 columns in the (now idle) operand ring
-    // and writes them back row by row, so every store instruction covers
-    // consecutive addresses of one row.
-    const int row0 = m0 + warp * 32;
-    const int row = row0 + lane;
-    float *stage = reinterpret_cast<float *>(smem) + warp * (32 * 33);
-    if (have) {
-        for (int c = 0; c < BN; c += 32) {
-            float v[32];
-            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
-#pragma unroll
-            for (int i = 0; i < 32; ++i) {
-                const int col = n0 + c + i;
-                const bool in = row < M && col < N;
-                float z = v[i] + ((ep.bias && col < N) ? ep.bias[col] : 0.0f);
-                float y;
-                if (ep.epi == EPI_F32) {
-                    y = z;
-                } else if (ep.epi == EPI_F32_CLAMP) {
-                    y = fminf(fmaxf(z, 0.0f), 1.0f);
-                } else if (ep.epi == EPI_GELU) {
-                    const __nv_bfloat16 zb = __float2bfloat16(z);
-                    if (ep.aux && in) ep.aux[(long long)row * ep.ldo + col] = zb;
-                    y = gelu(__bfloat162float(zb));
-                } else {  // EPI_DGELU
-                    y = in ? v[i] * gelu_grad(__bfloat162float(ep.aux[(long long)row * ep.ldo + col])) : 0.0f;
-                }
-                if (ep.out_bfT && in)  // lanes hold consecutive rows: coalesced
-                    ep.out_bfT[(long long)col * ep.ldoT + row] = __float2bfloat16(y);
-                stage[lane * 33 + i] = y;
-            }
-            __syncwarp();
-            const int col = n0 + c + lane;
-            if (col < N) {
-                for (int r = 0; r < 32; ++r) {
-                    const int rr = row0 + r;
-                    if (rr >= M) break;
-                    const float y = stage[r * 33 + lane];
-                    const long long o = (long long)rr * ep.ldo + col;
-                    if (ep.epi == EPI_F32 || ep.epi == EPI_F32_CLAMP) ep.out_f32[o] = y;
-                    else ep.out_bf[o] = __float2bfloat16(y);
-                }
-            }
-            __syncwarp();
-        }
+    if (warp == 1) {
+        __syncwarp();  // lanes 1..31 waited while lane 0 issued: reconverge for the aligned dealloc
+        tmem_dealloc(tmem, kCols);
     }
-    tc_fence_before();
-    __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem, kCols);
 }
 
 }  // namespace gemm
