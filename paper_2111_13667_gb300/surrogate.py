@@ -157,3 +157,23 @@ def train(sur: Surrogate, d: torch.Tensor, R: torch.Tensor, steps: int, batch: i
             print(f"step {k} lr {lr:.2e} loss {float(loss.item()):.3e}", flush=True)
     torch.cuda.synchronize()
     return TrainReport(steps, batch, time.perf_counter() - t0, first or float("nan"), float(loss.item()))
+
+
+def _main():
+    import argparse
+    ap = argparse.ArgumentParser(description="run surrogate inference (profiling helper)")
+    ap.add_argument("--infer-batch", type=int, default=65536)
+    ap.add_argument("--repeat", type=int, default=4)
+    a = ap.parse_args()
+    abi.load()
+    sur = Surrogate()
+    d = random_thicknesses(a.infer_batch, seed=44)
+    out = torch.empty(a.infer_batch, sur.outputs, device="cuda")
+    for _ in range(a.repeat):
+        sur.infer(d, out=out)
+    torch.cuda.synchronize()
+    print("status", sur.status())
+
+
+if __name__ == "__main__":
+    _main()
