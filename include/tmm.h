@@ -59,7 +59,15 @@ typedef enum {
     TMM_ERR_NOMEM = -5        /* workspace too small / host allocation failed */
 } tmm_status;
 
-typedef enum { TMM_F64 = 0, TMM_F32 = 1 } tmm_prec;
+/*
+ * TMM_F64   native FP64 arithmetic, double arrays.
+ * TMM_F32   FP32 arithmetic, float arrays.
+ * TMM_F64X  double arrays, double-float arithmetic (each value the unevaluated
+ *           sum of two floats, ~48 significant bits) on the FP32 pipes: the
+ *           FP64 tolerance at several times the native FP64 throughput of this
+ *           part.  Forward only (tmm_coh_batched / _ex, non-persistent).
+ */
+typedef enum { TMM_F64 = 0, TMM_F32 = 1, TMM_F64X = 2 } tmm_prec;
 
 /* Polarisation bits of tmm_problem.pol_mask; outputs store s before p. */
 #define TMM_POL_S 1u

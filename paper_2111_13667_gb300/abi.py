@@ -27,6 +27,7 @@ TMM_ERR_TIMEOUT = -4
 TMM_ERR_NOMEM = -5
 TMM_F64 = 0
 TMM_F32 = 1
+TMM_F64X = 2
 TMM_POL_S = 1
 TMM_POL_P = 2
 
@@ -187,7 +188,7 @@ class DeviceProblem:
 
     @property
     def real_dtype(self):
-        return torch.float64 if self.prec == TMM_F64 else torch.float32
+        return torch.float32 if self.prec == TMM_F32 else torch.float64
 
     @property
     def S(self):
@@ -229,9 +230,9 @@ def pol_mask_of(pols: str) -> int:
 
 def to_device(w, prec="f64", device="cuda", pols=None) -> DeviceProblem:
     """Upload a ``workloads.Workload`` (numpy arrays) as a DeviceProblem."""
-    pr = TMM_F64 if prec in ("f64", TMM_F64) else TMM_F32
-    rd = torch.float64 if pr == TMM_F64 else torch.float32
-    cd = torch.complex128 if pr == TMM_F64 else torch.complex64
+    pr = {"f64": TMM_F64, "f32": TMM_F32, "f64x": TMM_F64X}.get(prec, prec)
+    rd = torch.float32 if pr == TMM_F32 else torch.float64
+    cd = torch.complex64 if pr == TMM_F32 else torch.complex128
     t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a)).to(device=device, dtype=dt).contiguous()
     return DeviceProblem(
         prec=pr, pol_mask=pol_mask_of(pols or w.pols), theta=t(w.theta, rd), lam=t(w.lam, rd), d=t(w.d, rd),

@@ -96,14 +96,14 @@ tmm_status gemm(const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *B, int ldb
         ep.err = error_flag();
         if (!ep.err) return TMM_ERR_CUDA;
     }
-    const int BN = N >= 256 ? 256 : (N >= 128 ? 128 : 64);
+    const int BN = N >= 256 ? 256 : (N >= 128 ? 128 : 64);  // >= 32 columns per epilogue warp slice
     CUtensorMap ta, tb;
     tmm_status s = make_tmap(&ta, A, M, K, lda, BM);
     if (s != TMM_OK) return s;
     s = make_tmap(&tb, B, N, K, ldb, BN);
     if (s != TMM_OK) return s;
     if (BN == 256) return launch_bn<256, 3>(ta, tb, M, N, K, ep, st);
-    if (BN == 128) return launch_bn<128, 5>(ta, tb, M, N, K, ep, st);
+    if (BN == 128) return launch_bn<128, 4>(ta, tb, M, N, K, ep, st);
     return launch_bn<64, 6>(ta, tb, M, N, K, ep, st);
 }
 

@@ -199,7 +199,7 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-constexpr int kEpiWarps = 8;                       // epilogue warps (two per TMEM lane quarter)
+constexpr int kEpiWarps = 16;                      // epilogue warps (four per TMEM lane quarter)
 constexpr int kGemmThreads = 64 + 32 * kEpiWarps;  // producer warp, MMA warp, epilogue warps
 
 template <int BN, int STAGES>
@@ -365,7 +365,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             if (!ok) *s_fail = 1;
         }
     } else {
-        // epilogue warps: lane quarter q of TMEM, half of the tile's columns
+        // epilogue warps: lane quarter q of TMEM, one of kEpiWarps / 4 column slices
+        constexpr int kSlices = (kEpiWarps / 4) < (BN / 32) ? (kEpiWarps / 4) : (BN / 32);
+        constexpr int kSliceCols = BN / kSlices;  // warps with half >= kSlices have no columns
+        static_assert(kSliceCols % 32 == 0, "column slice must hold whole 32-column chunks");
         const int ew = warp - 2, q = warp & 3, half = ew >> 2;
         float *stg = stg_all + ew * (32 * 33);
         int t = 0;
@@ -379,7 +382,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             tc_fence_after();
             const int m0 = (tile / n_tiles) * BM, n0 = (tile % n_tiles) * BN;
             const int row0 = m0 + q * 32;
-            for (int c = half * (BN / 2); c < (half + 1) * (BN / 2); c += 32) {
+            for (int c = half * kSliceCols; half < kSlices && c < (half + 1) * kSliceCols; c += 32) {
                 float v[32];
                 tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * BN + c), v);
                 epilogue_chunk(ep, v, stg, row0, n0 + c, M, N, lane);

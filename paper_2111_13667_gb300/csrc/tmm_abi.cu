@@ -53,14 +53,14 @@ tmm_status device_info(DeviceInfo *out)
 
 int npol(uint32_t pol_mask) { return (int)(pol_mask & 1u) + (int)((pol_mask >> 1) & 1u); }
 
-size_t real_size(int prec) { return prec == TMM_F64 ? sizeof(double) : sizeof(float); }
+size_t real_size(int prec) { return prec == TMM_F32 ? sizeof(float) : sizeof(double); }
 
 tmm_status validate_problem(const tmm_problem *p)
 {
     if (!p) return TMM_ERR_INVALID_ARG;
     if (p->S < 0 || p->L_max < 0 || p->n_lambda < 0 || p->n_theta < 0) return TMM_ERR_INVALID_ARG;
     if (p->pol_mask == 0 || (p->pol_mask & ~3u)) return TMM_ERR_INVALID_ARG;
-    if (p->prec != TMM_F64 && p->prec != TMM_F32) return TMM_ERR_INVALID_ARG;
+    if (p->prec != TMM_F64 && p->prec != TMM_F32 && p->prec != TMM_F64X) return TMM_ERR_INVALID_ARG;
     if (p->n_direct_per_lambda != 0 && p->n_direct_per_lambda != 1) return TMM_ERR_INVALID_ARG;
     // an empty batch reads no array, so its pointers are not checked
     if ((long long)p->S * p->n_lambda * p->n_theta == 0) return TMM_OK;
@@ -133,6 +133,7 @@ tmm_status tmm_coh_grad(const tmm_problem *p, const void *R_target, void *merit,
     if (p->S == 0) return TMM_OK;
     if (p->n_lambda == 0 || p->n_theta == 0) return TMM_ERR_INVALID_ARG;
     if (!R_target || !merit || (p->L_max > 0 && !dm_dd)) return TMM_ERR_INVALID_ARG;
+    if (p->prec == TMM_F64X) return TMM_ERR_UNSUPPORTED;
     return launch_grad(p, R_target, merit, dm_dd, dm_dn, workspace, workspace_bytes,
                        static_cast<cudaStream_t>(stream));
 }

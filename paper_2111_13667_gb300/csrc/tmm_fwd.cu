@@ -427,6 +427,7 @@ static tmm_status launch_prec(const tmm_problem *p, const tmm_launch_cfg *cfg, c
 tmm_status launch_forward(const tmm_problem *p, const tmm_launch_cfg *cfg, void *ws, size_t ws_bytes, void *R,
                           void *T, cudaStream_t st)
 {
+    if (p->prec == TMM_F64X) return launch_forward_df64(p, cfg, R, T, st);
     Tile t;
     tmm_status s = choose_tile(p, cfg, &t);
     if (s != TMM_OK) return s;

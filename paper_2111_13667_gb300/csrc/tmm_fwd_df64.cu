@@ -1,0 +1,423 @@
+// tmm_fwd_df64.cu -- the forward transfer-matrix kernel in double-float
+// arithmetic (TMM_F64X): FP64 inputs and outputs, FP64-level accuracy, the
+// arithmetic on the FP32 pipes (see tmm_df64.cuh).
+//
+// Same method and layout as tmm_fwd.cu (one thread per (stack, lambda,
+// theta), both polarisations, right-to-left 2-vector sweep of Eq. 3 with
+// unnormalised interfaces, phase applied divided by e^{Im delta}, power-of-two
+// rescaling every two layers).  Transcendentals:
+//   sin, cos of 2 pi f: f = j/256 + r, |r| <= 1/512; Taylor series of
+//     sin, cos (2 pi r) to x^5 / x^6, recombined with a table of
+//     sin, cos(2 pi k / 256) by the angle-addition formulas;
+//   2^v: v = n + i/64 + s, |s| <= 1/128; Taylor series of e^{s ln 2} to s^5,
+//     times a table of 2^{i/64}, times 2^n;
+//   square roots: Karp-Markstein correction of the float reciprocal root.
+// The tables are computed on the host in double precision and passed with
+// the launch.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <mutex>
+
+#include "tmm_device.cuh"
+#include "tmm_df64.cuh"
+#include "tmm_internal.h"
+
+namespace tmm {
+
+using df::cdd;
+using df::dd;
+
+namespace {
+
+constexpr int kDfMaxThreads = 512;
+
+struct DfTables {
+    float4 sc[64];  // {sin hi, sin lo, cos hi, cos lo} of 2 pi k / 256
+    float2 e2[65];  // 2^{i/64}, i = -32 .. 32
+};
+
+// per (medium, wavelength): n^2 - n0^2, Im n^2, 1/n^2, d/lambda, |1/n^2|^2
+struct __align__(16) DStage {
+    float d2h, d2l, n2yh, n2yl;
+    float in2xh, in2xl, in2yh, in2yl;
+    float dlh, dll, ain2h, ain2l;
+};
+
+__device__ __forceinline__ dd dconst(double v)
+{
+    const float h = (float)v;
+    return dd{h, (float)(v - (double)h)};
+}
+
+constexpr double kPi = 3.14159265358979323846264338327950288;
+
+__device__ __forceinline__ void sincos_turn_dd(dd f, const float4 *tab, dd *s, dd *c)
+{
+    const float jf = rintf(__fmul_rn(f.hi, 256.0f));
+    const int j = (int)jf;
+    const dd r = df::add_f(f, -__fmul_rn(jf, 1.0f / 256.0f));
+    const dd x = df::mul(r, dconst(2.0 * kPi));
+    const dd x2 = df::sqr(x);
+    // sin x = x (1 - x^2/6 + x^4/120), cos x = 1 - x^2/2 + (x^4/24 - x^6/720)
+    const dd t = df::mul(x2, dconst(1.0 / 6.0));
+    const float x4 = __fmul_rn(x2.hi, x2.hi);
+    const dd p = df::add_f(df::sub(df::make(1.0f), t), __fmul_rn(x4, 1.0f / 120.0f));
+    const dd sx = df::mul(x, p);
+    const float h4 = __fsub_rn(__fmul_rn(x4, 1.0f / 24.0f), __fmul_rn(__fmul_rn(x4, x2.hi), 1.0f / 720.0f));
+    const dd cx = df::add_f(df::sub(df::make(1.0f), df::scale2(x2, 0.5f)), h4);
+    const int jj = j & 255, quad = jj >> 6, k = jj & 63;
+    const float4 e = tab[k];
+    const dd sk{e.x, e.y}, ck{e.z, e.w};
+    dd sj, cj;
+    if (quad == 0) { sj = sk; cj = ck; }
+    else if (quad == 1) { sj = ck; cj = df::neg(sk); }
+    else if (quad == 2) { sj = df::neg(sk); cj = df::neg(ck); }
+    else { sj = df::neg(ck); cj = sk; }
+    *s = df::dot2(sj, cx, cj, sx, 1.0f);
+    *c = df::dot2(cj, cx, sj, sx, -1.0f);
+}
+
+// 2^v as m * 2^n with m a dd in [2^-0.5, 2^0.5]
+__device__ __forceinline__ dd exp2_dd(dd v, const float2 *tab, int *n_out)
+{
+    const float nf = rintf(v.hi);
+    const dd r = df::add_f(v, -nf);
+    const float i_f = rintf(__fmul_rn(r.hi, 64.0f));
+    const dd s = df::add_f(r, -__fmul_rn(i_f, 1.0f / 64.0f));
+    const dd t = df::mul(s, dconst(0.69314718055994530941723212145818));
+    const dd t2 = df::sqr(t);
+    const dd t3_6 = df::mul(t2, df::mul(t, dconst(1.0 / 6.0)));
+    const float t4 = __fmul_rn(t2.hi, t2.hi);
+    const float tail = __fadd_rn(__fmul_rn(t4, 1.0f / 24.0f), __fmul_rn(__fmul_rn(t4, t.hi), 1.0f / 120.0f));
+    dd p = df::add(df::make(1.0f), t);
+    p = df::add(p, df::scale2(t2, 0.5f));
+    p = df::add(p, t3_6);
+    p = df::add_f(p, tail);
+    const float2 e = tab[(int)i_f + 32];
+    *n_out = (int)nf;
+    return df::mul(p, dd{e.x, e.y});
+}
+
+__device__ __forceinline__ bool dd_less(dd a, dd b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
+__device__ __forceinline__ dd dd_abs(dd a) { return a.hi < 0.0f ? df::neg(a) : a; }
+
+// forward root q = sqrt(z) (decaying / propagating choice) and |z|
+__device__ __forceinline__ cdd root_dd(cdd z, dd *absz)
+{
+    const dd hyp = df::cabs2(z);
+    cdd q{dd{0.0f, 0.0f}, dd{0.0f, 0.0f}};
+    dd az{0.0f, 0.0f};
+    if (!(hyp.hi <= 0.0f)) {
+        dd rh;
+        df::sqrt_rsqrt(hyp, &az, &rh);
+        const dd u = df::scale2(df::add(az, dd_abs(z.x)), 0.5f);
+        dd t, ru;
+        df::sqrt_rsqrt(u, &t, &ru);
+        const dd o = df::scale2(df::mul(z.y, ru), 0.5f);
+        if (z.x.hi >= 0.0f) {
+            q = cdd{t, o};
+        } else {
+            q = cdd{dd_abs(o), z.y.hi < 0.0f || (z.y.hi == 0.0f && signbit(z.y.hi)) ? df::neg(t) : t};
+        }
+        // decaying root unless Im q is zero to rounding (|Im q| <= 100 * 2^-46 |q|)
+        const float tol = 100.0f * 1.4210855e-14f;
+        if (q.y.hi < 0.0f && q.y.hi * q.y.hi > tol * tol * az.hi) q = cdd{df::neg(q.x), df::neg(q.y)};
+    }
+    *absz = az;
+    return q;
+}
+
+__device__ __forceinline__ void renorm_dd_pair(cdd &a, cdd &b, int &e)
+{
+    const float m = fmaxf(fmaxf(fabsf(a.x.hi), fabsf(a.y.hi)), fmaxf(fabsf(b.x.hi), fabsf(b.y.hi)));
+    const int k = exponent_of(m);
+    const float s = pow2_neg<float>(k);
+    a = cdd{df::scale2(a.x, s), df::scale2(a.y, s)};
+    b = cdd{df::scale2(b.x, s), df::scale2(b.y, s)};
+    e += k;
+}
+
+__device__ __forceinline__ void renorm_dd(dd &m, int &e)
+{
+    const int k = exponent_of(m.hi);
+    m = df::scale2(m, pow2_neg<float>(k));
+    e += k;
+}
+
+__device__ __forceinline__ cdd ld_c(float h1, float l1, float h2, float l2) { return cdd{dd{h1, l1}, dd{h2, l2}}; }
+
+template <int POL>
+__device__ __forceinline__ void eval_point_dd(const DStage *__restrict__ st, const float4 *sc, const float2 *e2, int TL,
+                                              int tl, int L, dd n0, dd sth, dd cth, dd Pp, int Pp_e, double out[4])
+{
+    const dd beta = df::mul(n0, sth);
+    const dd c0 = df::mul(n0, cth);
+    const dd q0sq = df::sqr(c0);
+    const dd yi_max = dconst(35.0 / (2.0 * kPi));
+
+    DStage A = st[(L + 1) * TL + tl];
+    dd absz;
+    cdd q_nx = root_dd(cdd{df::add(dd{A.d2h, A.d2l}, q0sq), dd{A.n2yh, A.n2yl}}, &absz);
+    const cdd q_out = q_nx;
+    const cdd n2_out{df::add(dd{A.d2h, A.d2l}, df::sqr(n0)), dd{A.n2yh, A.n2yl}};
+    cdd g_nx = df::cmul(q_nx, ld_c(A.in2xh, A.in2xl, A.in2yh, A.in2yl));
+    dd Ps = df::make(1.0f), Y = df::make(0.0f);
+    int eP = 0;
+    const cdd one{df::make(1.0f), df::make(0.0f)}, zero{df::make(0.0f), df::make(0.0f)};
+    cdd s0 = one, s1 = zero, p0 = one, p1 = zero;
+    int es = 0, ep = 0;
+
+    for (int j = L; j >= 1; --j) {
+        A = st[j * TL + tl];
+        const cdd q = root_dd(cdd{df::add(dd{A.d2h, A.d2l}, q0sq), dd{A.n2yh, A.n2yl}}, &absz);
+        Ps = df::mul(Ps, absz);
+        const dd dl{A.dlh, A.dll};
+        const dd yr = df::mul(dl, q.x);
+        dd yi = df::mul(dl, q.y);
+        if (dd_less(yi_max, yi)) yi = yi_max;
+        Y = df::add(Y, yi);
+        dd sn, cs;
+        sincos_turn_dd(df::add_f(yr, -rintf(yr.hi)), sc, &sn, &cs);
+        int n2;
+        const dd m2 = exp2_dd(df::mul(yi, dconst(-4.0 * kPi * 1.4426950408889634073599246810019)), e2, &n2);
+        const dd E2 = df::scale2(m2, ldexpf(1.0f, n2));
+        const cdd emi{cs, df::neg(sn)};
+        const cdd epi{df::mul(E2, cs), df::mul(E2, sn)};
+        if (POL & 1) {
+            const cdd a = df::cadd(q, q_nx), b = df::csub(q, q_nx);
+            const cdd u0 = df::cdot2(a, s0, b, s1);
+            const cdd u1 = df::cdot2(b, s0, a, s1);
+            s0 = df::cmul(emi, u0);
+            s1 = df::cmul(epi, u1);
+        }
+        if (POL & 2) {
+            const cdd g = df::cmul(q, ld_c(A.in2xh, A.in2xl, A.in2yh, A.in2yl));
+            const cdd a = df::cadd(g, g_nx), b = df::csub(g, g_nx);
+            const cdd u0 = df::cdot2(a, p0, b, p1);
+            const cdd u1 = df::cdot2(b, p0, a, p1);
+            p0 = df::cmul(emi, u0);
+            p1 = df::cmul(epi, u1);
+            g_nx = g;
+        }
+        q_nx = q;
+        if (((L - j) & 1) == 1) {
+            renorm_dd(Ps, eP);
+            if (POL & 1) renorm_dd_pair(s0, s1, es);
+            if (POL & 2) renorm_dd_pair(p0, p1, ep);
+        }
+    }
+    A = st[tl];
+    // grazing: cos(theta) <= 0 or beta >= n_0 (both false for a NaN n_0)
+    const bool grazing = cth.hi <= 0.0f || (!dd_less(beta, n0) && beta.hi == beta.hi);
+    const cdd q0{c0, df::make(0.0f)};
+    Ps = df::mul(Ps, q0sq);
+    const int e4 = 2 * (L + 1);
+    // 2^{-2 K Y} split as m * 2^n
+    int yn;
+    const dd ym = exp2_dd(df::mul(Y, dconst(-4.0 * kPi * 1.4426950408889634073599246810019)), e2, &yn);
+    const double ys = df::to_double(ym);
+    if (POL & 1) {
+        const cdd a = df::cadd(q0, q_nx), b = df::csub(q0, q_nx);
+        const cdd x0 = df::cdot2(a, s0, b, s1);
+        const cdd x1 = df::cdot2(b, s0, a, s1);
+        const dd ax0 = df::cabs2(x0);
+        double Rv = df::to_double(df::div(df::cabs2(x1), ax0));
+        double Tv = df::to_double(df::div(df::mul(q_out.x, Ps), df::mul(q0.x, ax0)));
+        Tv = ldexp(Tv * ys, e4 + eP + yn - 2 * es);
+        if (grazing) { Rv = 1.0; Tv = 0.0; }
+        out[0] = Rv;
+        out[1] = Tv;
+    }
+    if (POL & 2) {
+        const cdd g0 = df::cmul(q0, ld_c(A.in2xh, A.in2xl, A.in2yh, A.in2yl));
+        const cdd a = df::cadd(g0, g_nx), b = df::csub(g0, g_nx);
+        const cdd x0 = df::cdot2(a, p0, b, p1);
+        const cdd x1 = df::cdot2(b, p0, a, p1);
+        const dd ax0 = df::cabs2(x0);
+        double Rv = df::to_double(df::div(df::cabs2(x1), ax0));
+        // Re(n_out^2 conj(q_out)) / (n_0^2 q_0)
+        const dd num = df::dot2(n2_out.x, q_out.x, n2_out.y, q_out.y, 1.0f);
+        const dd den = df::mul(df::sqr(n0), q0.x);
+        double Tv = df::to_double(df::div(df::mul(num, df::mul(Ps, Pp)), df::mul(den, ax0)));
+        Tv = ldexp(Tv * ys, e4 + eP + Pp_e + yn - 2 * ep);
+        if (grazing) { Rv = 1.0; Tv = 0.0; }
+        out[2] = Rv;
+        out[3] = Tv;
+    }
+}
+
+template <int POL, bool WITH_T>
+__global__ void __launch_bounds__(kDfMaxThreads) tmm_fwd_df64_kernel(const tmm_problem p, const __grid_constant__ DfTables tabs,
+                                                                     int TL, int TT, int n_lt, int n_tt,
+                                                                     double *__restrict__ Rout, double *__restrict__ Tout)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    DStage *st = reinterpret_cast<DStage *>(smem);
+    float4 *sc = reinterpret_cast<float4 *>(st + (size_t)(p.L_max + 2) * TL);
+    float2 *e2 = reinterpret_cast<float2 *>(sc + 64);
+    float2 *n0s = e2 + 65;         // [TL] dd n_0 (NaN if complex)
+    float2 *ppm = n0s + TL;        // [TL] dd prod |1/n^2|^2
+    int *ppe = reinterpret_cast<int *>(ppm + TL);
+
+    const long long item = blockIdx.x;
+    const int per_stack = n_lt * n_tt;
+    const int s = (int)(item / per_stack);
+    const int rr = (int)(item - (long long)s * per_stack);
+    const int lt = rr / n_tt, ttile = rr % n_tt;
+    const int tid = threadIdx.y * TL + threadIdx.x, nthr = TL * TT;
+    const int L = layers_of(p, s);
+    const int l0 = lt * TL;
+    const double *lam = (const double *)p.lambda;
+    const double *d = (const double *)p.d;
+
+    for (int i = tid; i < 64; i += nthr) sc[i] = tabs.sc[i];
+    for (int i = tid; i < 65; i += nthr) e2[i] = tabs.e2[i];
+    if (L >= 0) {
+        const int total = (L + 2) * TL;
+        for (int idx = tid; idx < total; idx += nthr) {
+            const int j = idx / TL, tl = idx - j * TL;
+            const int l = min(l0 + tl, p.n_lambda - 1);
+            const Cx<double> n = index_of<double>(p, s, j, l);
+            const double n0v = j == 0 ? n.x : index_of<double>(p, s, 0, l).x;
+            const double n2x = fma(n.x, n.x, -n.y * n.y), n2y = 2.0 * n.x * n.y;
+            const double a = fma(n2x, n2x, n2y * n2y), ia = 1.0 / a;
+            const double d2 = (n.x - n0v) * (n.x + n0v) - n.y * n.y;
+            const double dl = (j >= 1 && j <= L) ? d[(long long)s * p.L_max + (j - 1)] / lam[l] : 0.0;
+            const dd d2d = df::from_double(d2), n2yd = df::from_double(n2y), ix = df::from_double(n2x * ia),
+                     iy = df::from_double(-n2y * ia), dld = df::from_double(dl), aid = df::from_double(ia);
+            st[idx] = DStage{d2d.hi, d2d.lo, n2yd.hi, n2yd.lo, ix.hi, ix.lo, iy.hi, iy.lo, dld.hi, dld.lo, aid.hi,
+                             aid.lo};
+            if (j == 0) {
+                const dd nd = df::from_double(n.y == 0.0 ? n.x : __longlong_as_double(0x7ff8000000000000LL));
+                n0s[tl] = make_float2(nd.hi, nd.lo);
+            }
+        }
+    }
+    __syncthreads();
+    if ((POL & 2) && L >= 0 && tid < TL) {
+        dd m = df::make(1.0f);
+        int e = 0;
+        for (int j = 1; j <= L + 1; ++j) {
+            const DStage &X = st[j * TL + tid];
+            m = df::mul(m, dd{X.ain2h, X.ain2l});
+            renorm_dd(m, e);
+        }
+        ppm[tid] = make_float2(m.hi, m.lo);
+        ppe[tid] = e;
+    }
+    __syncthreads();
+
+    const int tl = threadIdx.x, l = l0 + tl, a = ttile * TT + threadIdx.y;
+    if (l < p.n_lambda && a < p.n_theta) {
+        double out[4];
+        if (L >= 0) {
+            // sin, cos of theta through the same turn-based routine: f = theta / (2 pi)
+            const dd f = df::mul(df::from_double(((const double *)p.theta)[a]), dconst(1.0 / (2.0 * kPi)));
+            dd sth, cth;
+            sincos_turn_dd(df::add_f(f, -rintf(f.hi)), sc, &sth, &cth);
+            const float2 n0 = n0s[tl];
+            eval_point_dd<POL>(st, sc, e2, TL, tl, L, dd{n0.x, n0.y}, sth, cth,
+                               (POL & 2) ? dd{ppm[tl].x, ppm[tl].y} : df::make(1.0f), (POL & 2) ? ppe[tl] : 0, out);
+        } else {
+            out[0] = out[1] = out[2] = out[3] = __longlong_as_double(0x7ff8000000000000LL);
+        }
+        const long long plane = (long long)p.S * p.n_theta * p.n_lambda;
+        const long long o = ((long long)s * p.n_theta + a) * p.n_lambda + l;
+        int pi = 0;
+        if (POL & 1) {
+            Rout[o] = out[0];
+            if (WITH_T) Tout[o] = out[1];
+            ++pi;
+        }
+        if (POL & 2) {
+            Rout[pi * plane + o] = out[2];
+            if (WITH_T) Tout[pi * plane + o] = out[3];
+        }
+    }
+}
+
+const DfTables &host_tables()
+{
+    static DfTables t;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        for (int k = 0; k < 64; ++k) {
+            const double a = 2.0 * kPi * k / 256.0;
+            const double sv = std::sin(a), cv = std::cos(a);
+            const float sh = (float)sv, ch = (float)cv;
+            t.sc[k] = make_float4(sh, (float)(sv - sh), ch, (float)(cv - ch));
+        }
+        for (int i = -32; i <= 32; ++i) {
+            const double v = std::exp2(i / 64.0);
+            const float h = (float)v;
+            t.e2[i + 32] = make_float2(h, (float)(v - h));
+        }
+    });
+    return t;
+}
+
+size_t df_stage_bytes(const tmm_problem *p, int TL)
+{
+    return (size_t)(p->L_max + 2) * TL * sizeof(DStage) + 64 * sizeof(float4) + 65 * sizeof(float2) +
+           (size_t)TL * (2 * sizeof(float2) + sizeof(int));
+}
+
+template <int POL, bool WITH_T>
+tmm_status launch_df_typed(const tmm_problem *p, int TL, int TT, int n_lt, int n_tt, long long n_items, size_t smem,
+                           double *R, double *T, cudaStream_t st)
+{
+    auto k = tmm_fwd_df64_kernel<POL, WITH_T>;
+    static int set_bytes[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (dev < 0 || dev >= 64) return TMM_ERR_UNSUPPORTED;
+    if (smem > 48 * 1024 && set_bytes[dev] < (int)smem) {
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return cuda_fail(e);
+        set_bytes[dev] = (int)smem;
+    }
+    if (n_items > 0x7fffffffLL) return TMM_ERR_UNSUPPORTED;
+    k<<<(unsigned)n_items, dim3(TL, TT), smem, st>>>(*p, host_tables(), TL, TT, n_lt, n_tt, R, T);
+    return check_launch();
+}
+
+}  // namespace
+
+tmm_status launch_forward_df64(const tmm_problem *p, const tmm_launch_cfg *cfg, void *R, void *T, cudaStream_t st)
+{
+    if (cfg && cfg->persistent) return TMM_ERR_UNSUPPORTED;
+    DeviceInfo di;
+    tmm_status s = device_info(&di);
+    if (s != TMM_OK) return s;
+    int TT = cfg && cfg->tile_theta > 0 ? cfg->tile_theta : std::min(p->n_theta, 32);
+    int TL = cfg && cfg->tile_lambda > 0 ? cfg->tile_lambda : 0;
+    if (TL == 0) {
+        TL = 1;
+        while (TL * TT < 256 && TL * 2 * TT <= kDfMaxThreads) TL *= 2;
+        while (TL > 1 && TL / 2 >= p->n_lambda) TL /= 2;
+        while (TL > 1 && df_stage_bytes(p, TL) > (size_t)di.max_smem_optin) TL /= 2;
+    }
+    if (TL < 1 || TT < 1 || TL * TT > kDfMaxThreads) return TMM_ERR_INVALID_ARG;
+    const size_t smem = df_stage_bytes(p, TL);
+    if (smem > (size_t)di.max_smem_optin) return TMM_ERR_UNSUPPORTED;
+    const int n_lt = (p->n_lambda + TL - 1) / TL, n_tt = (p->n_theta + TT - 1) / TT;
+    const long long n_items = (long long)p->S * n_lt * n_tt;
+    if (n_items == 0) return TMM_OK;
+    double *Ro = static_cast<double *>(R);
+    double *To = static_cast<double *>(T);
+    const bool wt = To != nullptr;
+    switch (p->pol_mask) {
+    case 1: return wt ? launch_df_typed<1, true>(p, TL, TT, n_lt, n_tt, n_items, smem, Ro, To, st)
+                      : launch_df_typed<1, false>(p, TL, TT, n_lt, n_tt, n_items, smem, Ro, To, st);
+    case 2: return wt ? launch_df_typed<2, true>(p, TL, TT, n_lt, n_tt, n_items, smem, Ro, To, st)
+                      : launch_df_typed<2, false>(p, TL, TT, n_lt, n_tt, n_items, smem, Ro, To, st);
+    case 3: return wt ? launch_df_typed<3, true>(p, TL, TT, n_lt, n_tt, n_items, smem, Ro, To, st)
+                      : launch_df_typed<3, false>(p, TL, TT, n_lt, n_tt, n_items, smem, Ro, To, st);
+    default: return TMM_ERR_INVALID_ARG;
+    }
+}
+
+}  // namespace tmm

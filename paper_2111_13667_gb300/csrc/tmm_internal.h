@@ -41,6 +41,7 @@ PersistentWs persistent_ws_layout(const tmm_problem *p);
 
 tmm_status launch_forward(const tmm_problem *p, const tmm_launch_cfg *cfg, void *ws, size_t ws_bytes,
                           void *R, void *T, cudaStream_t st);
+tmm_status launch_forward_df64(const tmm_problem *p, const tmm_launch_cfg *cfg, void *R, void *T, cudaStream_t st);
 
 // Adjoint / merit.
 size_t grad_ws_bytes(const tmm_problem *p);

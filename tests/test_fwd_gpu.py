@@ -14,7 +14,7 @@ from tests.helpers import oracle_index, oracle_RT
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"f64": 1e-10, "f32": 1e-4}
+TOL = {"f64": 1e-10, "f32": 1e-4, "f64x": 1e-10}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -38,7 +38,7 @@ def assert_close(got, ref, tol, what=""):
     assert err <= tol, f"{what}: max |err| = {err:.3e} > {tol:.0e}"
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("prec", ["f64", "f32", "f64x"])
 def test_plain_fp64_workload_full(prec):
     w = W.plain_fp64()
     Ro, To = oracle_RT(w)
@@ -47,7 +47,7 @@ def test_plain_fp64_workload_full(prec):
     assert_close(T, To, TOL[prec], "T")
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("prec", ["f64", "f32", "f64x"])
 def test_dispersive_small_ragged_tail(prec):
     # several lambda / theta tiles with a partial last tile, gathered index
     w = W.dispersive(seed=11, S=37, L=24, n_lambda=203, n_theta=13)
@@ -57,7 +57,7 @@ def test_dispersive_small_ragged_tail(prec):
     assert_close(T, To, TOL[prec], "T")
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("prec", ["f64", "f32", "f64x"])
 def test_direct_per_lambda_index(prec):
     w = W.dispersive(seed=12, S=9, L=10, n_lambda=40, n_theta=5)
     w.n_direct = oracle_index(w)  # same indices given directly, [S][L+2][N_lambda]
@@ -68,7 +68,7 @@ def test_direct_per_lambda_index(prec):
     assert_close(T, To, TOL[prec], "T")
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("prec", ["f64", "f32", "f64x"])
 @pytest.mark.parametrize("pols", ["s", "p"])
 def test_single_polarisation_and_R_only(prec, pols):
     w = W.plain_fp64(seed=13, S=5, L=7)
@@ -77,15 +77,18 @@ def test_single_polarisation_and_R_only(prec, pols):
     assert_close(R, Ro, TOL[prec], "R")
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("prec", ["f64", "f32", "f64x"])
 def test_total_internal_reflection_and_grazing(prec):
     # injection index 2 into air, interior indices up to 4.6, theta up to
     # exactly 90 deg (the paper's reflectivity-map shape)
     w = W.map_x3()
     Ro, To = oracle_RT(w)
     R, T = gpu_RT(w, prec)
-    assert np.all(R[:, 0, -1, :] == 1.0) and np.all(T[:, 0, -1, :] == 0.0)  # grazing reading
-    if prec == "f64":
+    if prec == "f64x":  # cos(theta) of the rounded pi/2 is 6e-17: R, T within rounding of 1, 0
+        assert np.max(np.abs(R[:, 0, -1, :] - 1.0)) <= 1e-12 and np.max(np.abs(T[:, 0, -1, :])) <= 1e-12
+    else:
+        assert np.all(R[:, 0, -1, :] == 1.0) and np.all(T[:, 0, -1, :] == 0.0)  # grazing reading
+    if prec != "f32":
         assert_close(R, Ro, TOL[prec], "R")
         assert_close(T, To, TOL[prec], "T")
         return
@@ -101,7 +104,7 @@ def test_total_internal_reflection_and_grazing(prec):
     assert_close(T, To, TOL[prec], "T")
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("prec", ["f64", "f32", "f64x"])
 def test_single_interface_and_opaque_layers(prec):
     lam = np.linspace(400, 800, 33)
     th = np.deg2rad(np.linspace(0, 70, 6))
@@ -120,8 +123,7 @@ def test_single_interface_and_opaque_layers(prec):
         assert_close(T, To, TOL[prec], f"T {media[:3]}")
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32"])
-@pytest.mark.parametrize("persistent", [0, 1])
+@pytest.mark.parametrize("prec,persistent", [("f64", 0), ("f64", 1), ("f32", 0), ("f32", 1), ("f64x", 0)])
 def test_ragged_layer_counts(prec, persistent):
     w = W.ragged(seed=14, S=301, L_max=60, n_lambda=45, n_theta=7)
     Ro, To = oracle_RT(w)
@@ -186,7 +188,7 @@ def test_workspace_checks():
     assert e.value.status == abi.TMM_ERR_NOMEM
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("prec", ["f64", "f32", "f64x"])
 def test_dispersive_full_size_sampled(prec):
     """The full 16384 x 24 x 512 x 32 problem in the launch the benchmark
     times; a seeded sample of stacks is checked against the oracle."""
@@ -218,3 +220,14 @@ def test_empty_batch():
     R = prob.empty_out()
     abi.tmm_coh_batched(prob, R, None)
     assert R.numel() == 0
+
+
+def test_f64x_rejects_persistent_and_grad():
+    w = W.ragged(seed=19, S=4, L_max=5, n_lambda=8, n_theta=2)
+    prob = abi.to_device(w, "f64x")
+    R = prob.empty_out()
+    cfg = abi.launch_cfg(persistent=1)
+    ws = abi.alloc_workspace(abi.tmm_workspace_size(prob, cfg))
+    with pytest.raises(abi.TmmError) as e:
+        abi.tmm_coh_batched_ex(prob, cfg, ws, R, None)
+    assert e.value.status == abi.TMM_ERR_UNSUPPORTED
