@@ -234,3 +234,19 @@ def test_f64x_rejects_persistent_and_grad():
     with pytest.raises(abi.TmmError) as e:
         abi.tmm_coh_batched_ex(prob, cfg, ws, R, None)
     assert e.value.status == abi.TMM_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("n_chunks", [1, 3, 8])
+def test_host_pipeline_matches_device_launch(n_chunks):
+    from paper_2111_13667_gb300.pipeline import HostPipeline
+    w = W.dispersive(seed=20, S=53, L=9, n_lambda=37, n_theta=6)
+    prob = abi.to_device(w, "f32")
+    Rd, Td = abi.coh_tmm(prob)
+    h_in = {k: getattr(prob, k).cpu().pin_memory() for k in ("theta", "lam", "d", "table", "mat_idx")}
+    hR = torch.zeros(Rd.shape, dtype=Rd.dtype).pin_memory()
+    hT = torch.zeros(Td.shape, dtype=Td.dtype).pin_memory()
+    pipe = HostPipeline(abi.to_device(w, "f32"), n_chunks=n_chunks)
+    for _ in range(2):
+        pipe.run(h_in, hR, hT)
+        torch.cuda.synchronize()
+        assert torch.equal(hR, Rd.cpu()) and torch.equal(hT, Td.cpu())
