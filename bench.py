@@ -256,9 +256,12 @@ def gpu_arm(args):
         torch.cuda.empty_cache()
 
     if not args.skip_extras:
-        out["ragged"] = bench_ragged(args, torch, abi, W, flush, world, max_over_ranks)
-        out["adjoint"] = bench_adjoint(args, torch, abi, W, flush, world, max_over_ranks)
-        if not args.skip_surrogate:
+        sections = {x.strip() for x in args.sections.split(",") if x.strip()}
+        if "ragged" in sections:
+            out["ragged"] = bench_ragged(args, torch, abi, W, flush, world, max_over_ranks)
+        if "adjoint" in sections:
+            out["adjoint"] = bench_adjoint(args, torch, abi, W, flush, world, max_over_ranks)
+        if "surrogate" in sections and not args.skip_surrogate:
             out["surrogate"] = bench_surrogate(args, torch, abi, W, flush, world, max_over_ranks)
 
     head = out["f32"]
@@ -491,6 +494,8 @@ def main():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-extras", action="store_true", help="headline only (no ragged / adjoint lines)")
     ap.add_argument("--skip-surrogate", action="store_true")
+    ap.add_argument("--sections", default="ragged,adjoint,surrogate",
+                    help="extra sections after the headline (comma list of ragged, adjoint, surrogate)")
     ap.add_argument("--sur-train", type=int, default=2_000_000, help="training spectra (GPU-generated)")
     ap.add_argument("--sur-steps", type=int, default=2000, help="training steps of 8192 spectra")
     ap.add_argument("--stacks", type=int, default=0, help="shrink the workload (profiling runs only)")
