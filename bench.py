@@ -129,8 +129,8 @@ class ClockSampler:
 
 # ---------------------------------------------------------------- GPU arm
 def dist_env():
-    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
-        int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_2111_13667_gb300 import dist as D
+    return D.env()
 
 
 def time_steps(fn, steps, warmup, torch, flush):
@@ -167,23 +167,20 @@ def gpu_arm(args):
     dev = torch.device("cuda", local)
     abi.load()
 
-    w = W.dispersive(S=args.stacks) if args.stacks else W.dispersive()
+    # every rank evaluates its own shard of independent stacks (weak scaling)
+    w = W.dispersive(S=args.stacks, shard=rank) if args.stacks else W.dispersive(shard=rank)
     evals = w.evals
     interfaces = w.L_max + 1
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
     out = {}
 
+    from paper_2111_13667_gb300 import dist as D
+
     def barrier():
-        if world > 1:
-            dist.barrier()
-        torch.cuda.synchronize()
+        D.barrier(dev)
 
     def max_over_ranks(v):
-        if world == 1:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return D.max_over_ranks(v, dev)
 
     for prec, steps, warmup in (("f32", args.steps, args.warmup), ("f64", args.f64_steps, 3),
                                 ("f64x", max(3, args.f64_steps), 3)):
@@ -261,6 +258,8 @@ def gpu_arm(args):
             out["ragged"] = bench_ragged(args, torch, abi, W, flush, world, max_over_ranks)
         if "adjoint" in sections:
             out["adjoint"] = bench_adjoint(args, torch, abi, W, flush, world, max_over_ranks)
+        if "paper" in sections:
+            out["paper_shapes"] = bench_paper_shapes(args, torch, abi, W, flush)
         if "surrogate" in sections and not args.skip_surrogate:
             out["surrogate"] = bench_surrogate(args, torch, abi, W, flush, world, max_over_ranks)
 
@@ -278,7 +277,7 @@ def gpu_arm(args):
         "roofline": head["roofline"], "clocks": head.get("clocks"), "e2e": head.get("e2e"),
         "gpu_launches": args.steps,
     }
-    for k in ("f64", "f64x", "ragged", "adjoint", "surrogate"):
+    for k in ("f64", "f64x", "ragged", "adjoint", "paper_shapes", "surrogate"):
         if k in out:
             line[k] = out[k]
     line["cpu_baseline"] = cpu_baseline(w, args) if (rank == 0 and world == 1 and not args.skip_cpu) else None
@@ -404,6 +403,34 @@ def bench_surrogate(args, torch, abi, W, flush, world, max_over_ranks):
             "status": status, "steps": steps}
 
 
+def bench_paper_shapes(args, torch, abi, W, flush):
+    """The paper's own timing workloads, for context (its numbers are CPU
+    times on unstated hardware): the speed-up run (10 stacks, 21 media, 100
+    lambda x 20 theta, s; TMM-Fast 0.168 s) and the dataset example (1e6
+    stacks x 10 layers, 100 lambda, normal incidence, s; ~40 min for a
+    similar 9-layer 10-angle set on 8 cores)."""
+    res = {}
+    for name, w, paper in (("speedup_x1", W.speedup_x1(), "TMM-Fast 0.168 +- 0.002 s, original TMM 17.5 s (CPU)"),
+                           ("dataset_x2", W.dataset_x2(), "about 40 min for 1e6 9-layer stacks x 100 lambda x 10 theta on 8 cores (Dask)")):
+        ent = {"evals": w.evals, "paper": paper}
+        for prec in ("f64", "f64x", "f32"):
+            prob = abi.to_device(w, prec)
+            R, T = prob.empty_out(), prob.empty_out()
+            t = time_steps(lambda: abi.tmm_coh_batched(prob, R, T), 5, 3, torch, flush)
+            ms = sum(t) / len(t)
+            ent[prec] = {"ms": ms, "evals_per_s": w.evals / (ms * 1e-3)}
+            del R, T, prob
+        if name == "speedup_x1" and not args.skip_cpu:
+            import oracle
+            n = oracle.assemble_index(w.n_direct, w.table, w.mat_idx, w.n_lambda)
+            t0 = time.perf_counter()
+            oracle.coh_tmm_pols(w.pols, n, w.d, w.theta, w.lam, nthreads=cpu_threads())
+            ent["oracle_cpu_ms"] = (time.perf_counter() - t0) * 1e3
+            ent["oracle_cores"] = cpu_threads()
+        res[name] = ent
+    return res
+
+
 def sur_shapes(sur):
     """(N, K) of every GEMM of one inference (K = 64-padded input for the first)."""
     shapes = [(sur.hidden, 64)] + [(sur.hidden, sur.hidden)] * (sur.depth - 1) + [(sur.outputs, sur.hidden)]
@@ -494,8 +521,8 @@ def main():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-extras", action="store_true", help="headline only (no ragged / adjoint lines)")
     ap.add_argument("--skip-surrogate", action="store_true")
-    ap.add_argument("--sections", default="ragged,adjoint,surrogate",
-                    help="extra sections after the headline (comma list of ragged, adjoint, surrogate)")
+    ap.add_argument("--sections", default="ragged,adjoint,paper,surrogate",
+                    help="extra sections after the headline (comma list of ragged, adjoint, paper, surrogate)")
     ap.add_argument("--sur-train", type=int, default=2_000_000, help="training spectra (GPU-generated)")
     ap.add_argument("--sur-steps", type=int, default=2000, help="training steps of 8192 spectra")
     ap.add_argument("--stacks", type=int, default=0, help="shrink the workload (profiling runs only)")

@@ -161,10 +161,15 @@ def plain_fp64(seed=0, S=64, L=12):
                     d=d, n_direct=nd)
 
 
-def dispersive(seed=1, S=16384, L=24, n_lambda=512, n_theta=32):
+def dispersive(seed=1, S=16384, L=24, n_lambda=512, n_theta=32, shard=0):
+    """``shard`` r > 0 draws its own stacks (materials, thicknesses) from a
+    stream of its own, with the same material table: the r-th GPU's share of a
+    larger batch of independent stacks.  Shard 0 is the single-GPU workload."""
     rng = np.random.default_rng(seed)
     lam = np.linspace(300.0, 1200.0, n_lambda)
     table = cauchy_table(rng, lam)
+    if shard:
+        rng = np.random.default_rng([seed, shard])
     mat = _mat_rows(rng, S, L)
     d = rng.uniform(5.0, 400.0, (S, L))
     return Workload(f"dispersive ({S} stacks x {L} layers, {n_lambda} lambda x {n_theta} theta, 8 materials)",
