@@ -48,10 +48,17 @@ template <typename R> __device__ __forceinline__ R warp_sum(R v)
     return v;
 }
 
-template <typename R> __device__ __forceinline__ R pow2_w(int e)
+// 2^e built from the exponent bits (0 below the normal range, which only
+// happens for the masked lanes whose contributions are discarded).
+__device__ __forceinline__ float pow2_bits(int e, float)
 {
-    return ldexp_w(R(1), e);
+    return e < -126 ? 0.0f : __int_as_float(min(e, 127) + 127 << 23);
 }
+__device__ __forceinline__ double pow2_bits(int e, double)
+{
+    return e < -1022 ? 0.0 : __longlong_as_double((long long)(min(e, 1023) + 1023) << 52);
+}
+template <typename R> __device__ __forceinline__ R pow2_w(int e) { return pow2_bits(e, R(0)); }
 
 // Per-medium quantities of one point: root q, a_s = q, a_p = q / n^2 and
 // their derivatives with respect to n (dq/dn = n / q, da_p/dn = (1/n)(1/q - 2 q / n^2)).
@@ -143,28 +150,33 @@ __global__ void __launch_bounds__(kGradThreads) tmm_grad_kernel(const tmm_proble
         Cx<R> s0 = {R(1), R(0)}, s1 = {R(0), R(0)}, p0 = s0, p1 = s1;
         int es = 0, ep = 0;
         X[L + 1] = XState<R>{s0, s1, p0, p1, 0, 0};
+        // The phase matrix is applied divided by its real factor e^{Im delta}
+        // (one exponential per layer).  Stored states and, below, the row
+        // cotangents then carry inverse scales, so every gradient term --
+        // always a cotangent times a state -- is unchanged.
         for (int j = L; j >= 1; --j) {
             const StageA<R> A = sa[j * TL + tl];
             const StageB<R> B = sb[j * TL + tl];
             const Medium<R> m = medium_at(A, sn[j * TL + tl], q0sq, false);
             const R yr = B.dl * m.q.x, yi = fmin(B.dl * m.q.y, yi_max);
-            R sn_, cs, Ep, Em;
+            R sn_, cs;
             sincos_turn(yr - rint_w(yr), &sn_, &cs);
-            exp_pm_turn(yi, &Ep, &Em);
-            const Cx<R> emi = {Ep * cs, -Ep * sn_}, epi = {Em * cs, Em * sn_};
+            const R E2 = exp_m2_turn(yi);
+            const Cx<R> emi = {cs, -sn_}, epi = {E2 * cs, E2 * sn_};
+            const bool rn = ((L - j) & 1) == 1;
             if (do_s) {
                 const Cx<R> A_ = m.q + nx.q, B_ = m.q - nx.q;
                 const Cx<R> u0 = cfma(A_, s0, cmul(B_, s1)), u1 = cfma(B_, s0, cmul(A_, s1));
                 s0 = cmul(emi, u0);
                 s1 = cmul(epi, u1);
-                renorm_pair(s0, s1, es);
+                if (rn) renorm_pair(s0, s1, es);
             }
             if (do_p) {
                 const Cx<R> A_ = m.ap + nx.ap, B_ = m.ap - nx.ap;
                 const Cx<R> u0 = cfma(A_, p0, cmul(B_, p1)), u1 = cfma(B_, p0, cmul(A_, p1));
                 p0 = cmul(emi, u0);
                 p1 = cmul(epi, u1);
-                renorm_pair(p0, p1, ep);
+                if (rn) renorm_pair(p0, p1, ep);
             }
             X[j] = XState<R>{s0, s1, p0, p1, es, ep};
             nx = m;
@@ -220,22 +232,22 @@ __global__ void __launch_bounds__(kGradThreads) tmm_grad_kernel(const tmm_proble
         // cur = medium j, nx = medium j+1 (with n-derivatives when it is a layer)
         nx = medium_at(sa[1 * TL + tl], sn[1 * TL + tl], q0sq, L >= 1);
         R dn_carry = R(0);  // right-side F term for layer j+1, from step j
+        XState<R> Xc = X[1];  // the state of the current layer (x_j); unused at j = 0
         for (int j = 0; j <= L; ++j) {
             const XState<R> Xn = X[j + 1];
             R dd = R(0), dn = dn_carry;
             dn_carry = R(0);
             Cx<R> emi = {R(1), R(0)}, epi = {R(1), R(0)};
             Cx<R> ddel_d = {R(0), R(0)}, ddel_n = {R(0), R(0)};
-            XState<R> Xc;
             if (j >= 1) {
                 const StageB<R> B = sb[j * TL + tl];
                 const R yr = B.dl * cur.q.x, yi_raw = B.dl * cur.q.y;
                 const bool clamped = yi_raw > yi_max;
-                R sn_, cs, Ep, Em;
+                R sn_, cs;
                 sincos_turn(yr - rint_w(yr), &sn_, &cs);
-                exp_pm_turn(fmin(yi_raw, yi_max), &Ep, &Em);
-                emi = Cx<R>{Ep * cs, -Ep * sn_};
-                epi = Cx<R>{Em * cs, Em * sn_};
+                const R E2 = exp_m2_turn(fmin(yi_raw, yi_max));
+                emi = Cx<R>{cs, -sn_};
+                epi = Cx<R>{E2 * cs, E2 * sn_};
                 // d delta / d d = 2 pi q / lambda; d delta / d n = 2 pi (d/lambda) n / q
                 ddel_d = scale(two_pi_inv_lam, cur.q);
                 ddel_n = scale(R(kTwoPi) * B.dl, cur.dq);
@@ -243,8 +255,8 @@ __global__ void __launch_bounds__(kGradThreads) tmm_grad_kernel(const tmm_proble
                     ddel_d.y = R(0);
                     ddel_n.y = R(0);
                 }
-                Xc = X[j];
             }
+            const bool rn = (j & 1) == 1;
             // s polarisation
             if (do_s) {
                 const Cx<R> v0 = cmul(ws0, emi), v1 = cmul(ws1, epi);
@@ -260,7 +272,7 @@ __global__ void __launch_bounds__(kGradThreads) tmm_grad_kernel(const tmm_proble
                 const Cx<R> A_ = cur.q + nx.q, B_ = cur.q - nx.q;
                 ws0 = cfma(v0, A_, cmul(v1, B_));
                 ws1 = cfma(v0, B_, cmul(v1, A_));
-                renorm_pair(ws0, ws1, ews);
+                if (rn) renorm_pair(ws0, ws1, ews);
             }
             if (do_p) {
                 const Cx<R> v0 = cmul(wp0, emi), v1 = cmul(wp1, epi);
@@ -276,7 +288,7 @@ __global__ void __launch_bounds__(kGradThreads) tmm_grad_kernel(const tmm_proble
                 const Cx<R> A_ = cur.ap + nx.ap, B_ = cur.ap - nx.ap;
                 wp0 = cfma(v0, A_, cmul(v1, B_));
                 wp1 = cfma(v0, B_, cmul(v1, A_));
-                renorm_pair(wp0, wp1, ewp);
+                if (rn) renorm_pair(wp0, wp1, ewp);
             }
             if (j >= 1) {
                 dd = warp_sum(active ? dd : R(0));
@@ -291,6 +303,7 @@ __global__ void __launch_bounds__(kGradThreads) tmm_grad_kernel(const tmm_proble
                 const int jn = j + 2;
                 nx = medium_at(sa[jn * TL + tl], sn[jn * TL + tl], q0sq, jn <= L);
             }
+            Xc = Xn;
         }
         (void)P;
     }
