@@ -279,16 +279,19 @@ __global__ void __launch_bounds__(kDfMaxThreads) tmm_fwd_df64_kernel(const tmm_p
         for (int idx = tid; idx < total; idx += nthr) {
             const int j = idx / TL, tl = idx - j * TL;
             const int l = min(l0 + tl, p.n_lambda - 1);
+            // inputs split into float pairs once; the rest in dd arithmetic on the
+            // FP32 pipes (the FP64 pipe would dominate when few angles share it)
             const Cx<double> n = index_of<double>(p, s, j, l);
-            const double n0v = j == 0 ? n.x : index_of<double>(p, s, 0, l).x;
-            const double n2x = fma(n.x, n.x, -n.y * n.y), n2y = 2.0 * n.x * n.y;
-            const double a = fma(n2x, n2x, n2y * n2y), ia = 1.0 / a;
-            const double d2 = (n.x - n0v) * (n.x + n0v) - n.y * n.y;
-            const double dl = (j >= 1 && j <= L) ? d[(long long)s * p.L_max + (j - 1)] / lam[l] : 0.0;
-            const dd d2d = df::from_double(d2), n2yd = df::from_double(n2y), ix = df::from_double(n2x * ia),
-                     iy = df::from_double(-n2y * ia), dld = df::from_double(dl), aid = df::from_double(ia);
-            st[idx] = DStage{d2d.hi, d2d.lo, n2yd.hi, n2yd.lo, ix.hi, ix.lo, iy.hi, iy.lo, dld.hi, dld.lo, aid.hi,
-                             aid.lo};
+            const dd nx = df::from_double(n.x), ny = df::from_double(n.y);
+            const dd n0d = j == 0 ? nx : df::from_double(index_of<double>(p, s, 0, l).x);
+            const dd n2x = df::sub(df::sqr(nx), df::sqr(ny)), n2y = df::scale2(df::mul(nx, ny), 2.0f);
+            const dd ia = df::div(df::make(1.0f), df::dot2(n2x, n2x, n2y, n2y, 1.0f));
+            const dd d2 = df::sub(df::mul(df::sub(nx, n0d), df::add(nx, n0d)), df::sqr(ny));
+            const dd ix = df::mul(n2x, ia), iy = df::neg(df::mul(n2y, ia));
+            const dd dld = (j >= 1 && j <= L)
+                               ? df::div(df::from_double(d[(long long)s * p.L_max + (j - 1)]), df::from_double(lam[l]))
+                               : df::make(0.0f);
+            st[idx] = DStage{d2.hi, d2.lo, n2y.hi, n2y.lo, ix.hi, ix.lo, iy.hi, iy.lo, dld.hi, dld.lo, ia.hi, ia.lo};
             if (j == 0) {
                 const dd nd = df::from_double(n.y == 0.0 ? n.x : __longlong_as_double(0x7ff8000000000000LL));
                 n0s[tl] = make_float2(nd.hi, nd.lo);
