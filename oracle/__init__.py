@@ -45,22 +45,43 @@ def build(force: bool = False) -> str:
     return _LIB_PATH
 
 
+def _bind(path):
+    lib = ctypes.CDLL(path)
+    dp = ctypes.POINTER(ctypes.c_double)
+    ip = ctypes.POINTER(ctypes.c_int32)
+    up = ctypes.POINTER(ctypes.c_uint32)
+    i = ctypes.c_int
+    lib.oracle_coh_tmm.argtypes = [i, i, i, i, i, dp, dp, ip, dp, dp, up, dp, dp, i]
+    lib.oracle_coh_tmm.restype = i
+    lib.oracle_merit_grad.argtypes = [i, i, i, i, i, dp, dp, ip, dp, dp, dp, dp, dp, dp, i]
+    lib.oracle_merit_grad.restype = i
+    return lib
+
+
 def _load():
     global _lib
     with _lock:
         if _lib is None:
             build()
-            lib = ctypes.CDLL(_LIB_PATH)
-            dp = ctypes.POINTER(ctypes.c_double)
-            ip = ctypes.POINTER(ctypes.c_int32)
-            up = ctypes.POINTER(ctypes.c_uint32)
-            i = ctypes.c_int
-            lib.oracle_coh_tmm.argtypes = [i, i, i, i, i, dp, dp, ip, dp, dp, up, dp, dp, i]
-            lib.oracle_coh_tmm.restype = i
-            lib.oracle_merit_grad.argtypes = [i, i, i, i, i, dp, dp, ip, dp, dp, dp, dp, dp, dp, i]
-            lib.oracle_merit_grad.restype = i
-            _lib = lib
+            _lib = _bind(_LIB_PATH)
     return _lib
+
+
+def build_variant(src_text: str, out_path: str):
+    """Compile a modified copy of tmm_oracle.c (used by the mutation tests,
+    which plant mistakes in the oracle to show that the pins catch them) and
+    return its loaded library."""
+    src = out_path + ".c"
+    with open(src, "w") as fh:
+        fh.write(src_text)
+    subprocess.run(["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fPIC", "-shared", "-pthread", src, "-o",
+                    out_path, "-lm"], check=True)
+    return _bind(out_path)
+
+
+def source() -> str:
+    with open(_SRC) as fh:
+        return fh.read()
 
 
 def _ptr(a, ctype):
@@ -93,14 +114,15 @@ def _prep(n, d, theta, lam, L_per_stack):
     return n, d, theta, lam, L_per_stack, S, L_max, Nl
 
 
-def coh_tmm(pol, n, d, theta, lam, L_per_stack=None, flip_mask=None, nthreads=None):
+def coh_tmm(pol, n, d, theta, lam, L_per_stack=None, flip_mask=None, nthreads=None, lib=None):
     """R, T (each float64 [S][N_theta][N_lambda]) for one polarisation.
 
     ``pol`` is ``'s'`` or ``'p'``; ``n`` is complex [S][L_max+2][N_lambda]
     (media 0..L+1, index 0 the injection medium), ``d`` [S][L_max] in nm,
     ``theta`` radians in medium 0, ``lam`` nm.  Follows Sec. 2, Eqs. 1-6.
+    ``lib`` selects another build of the oracle (mutation tests only).
     """
-    lib = _load()
+    lib = lib or _load()
     n, d, theta, lam, L_per_stack, S, L_max, Nl = _prep(n, d, theta, lam, L_per_stack)
     Nt = theta.shape[0]
     if flip_mask is not None:
@@ -118,23 +140,23 @@ def coh_tmm(pol, n, d, theta, lam, L_per_stack=None, flip_mask=None, nthreads=No
     return R, T
 
 
-def coh_tmm_pols(pols, n, d, theta, lam, L_per_stack=None, nthreads=None):
+def coh_tmm_pols(pols, n, d, theta, lam, L_per_stack=None, nthreads=None, lib=None):
     """R, T stacked as [P][S][N_theta][N_lambda] for the polarisations in ``pols``."""
     Rs, Ts = [], []
     for p in pols:
-        R, T = coh_tmm(p, n, d, theta, lam, L_per_stack=L_per_stack, nthreads=nthreads)
+        R, T = coh_tmm(p, n, d, theta, lam, L_per_stack=L_per_stack, nthreads=nthreads, lib=lib)
         Rs.append(R)
         Ts.append(T)
     return np.stack(Rs), np.stack(Ts)
 
 
-def merit_grad(pols, n, d, theta, lam, R_target, L_per_stack=None, nthreads=None):
+def merit_grad(pols, n, d, theta, lam, R_target, L_per_stack=None, nthreads=None, lib=None):
     """Per-stack MSE merit and its gradients wrt d_j and a real offset of n_j.
 
     Returns ``(merit [S], dm_dd [S][L_max], dm_dn [S][L_max])``; ``R_target``
     is [P][N_theta][N_lambda] with P = len(pols), s before p.
     """
-    lib = _load()
+    lib = lib or _load()
     n, d, theta, lam, L_per_stack, S, L_max, Nl = _prep(n, d, theta, lam, L_per_stack)
     Nt = theta.shape[0]
     mask = (1 if "s" in pols else 0) | (2 if "p" in pols else 0)
@@ -156,9 +178,9 @@ def merit_grad(pols, n, d, theta, lam, R_target, L_per_stack=None, nthreads=None
     return merit, dd, dn
 
 
-def merit(pols, n, d, theta, lam, R_target, L_per_stack=None, nthreads=None):
+def merit(pols, n, d, theta, lam, R_target, L_per_stack=None, nthreads=None, lib=None):
     """Per-stack merit from the plain forward: mean of (R - R_target)^2."""
-    R, _ = coh_tmm_pols(pols, n, d, theta, lam, L_per_stack=L_per_stack, nthreads=nthreads)
+    R, _ = coh_tmm_pols(pols, n, d, theta, lam, L_per_stack=L_per_stack, nthreads=nthreads, lib=lib)
     e = R - np.asarray(R_target)[:, None, :, :]
     return np.mean(e * e, axis=(0, 2, 3))
 

@@ -248,7 +248,7 @@ def test_many_opaque_layers_stay_finite():
 
 # ---------------------------------------------------------------- second formulation
 @pytest.mark.parametrize("pol", ["s", "p"])
-@pytest.mark.parametrize("case", ["lossless", "absorbing", "dispersive", "tir"])
+@pytest.mark.parametrize("case", ["lossless", "absorbing", "dispersive", "tir", "metal_substrate"])
 def test_matches_characteristic_matrix_form(pol, case):
     if case == "dispersive":
         w = W.dispersive(S=6, L=15, n_lambda=33, n_theta=7)
@@ -258,8 +258,10 @@ def test_matches_characteristic_matrix_form(pol, case):
         n, d = oracle_index(w), w.d
         th, lam = w.theta[::7], w.lam
     else:
-        rng = np.random.default_rng(18 if case == "lossless" else 19)
-        nn, d = _random_stack(rng, 21, absorbing=(case == "absorbing"))
+        rng = np.random.default_rng({"lossless": 18, "absorbing": 19, "metal_substrate": 20}[case])
+        nn, d = _random_stack(rng, 21, absorbing=(case != "lossless"))
+        if case == "metal_substrate":  # absorbing outcoupling medium: T needs the conjugates of Eq. 2's reading
+            nn[:, -1] = 0.3 + 2.5j
         n, th, lam = _full(nn), THETA, LAM
     # Under total internal reflection with evanescent interior layers (index
     # up to 4.6 next to 1.2) the two forms round differently near grazing
