@@ -285,7 +285,8 @@ TMM_API tmm_status tmm_coh_batched_noalloc(const tmm_problem *p, const tmm_launc
  *   D[M][N] = sum_k A[M][k] B[N][k];  A, B device bf16, row-major, K a
  *   multiple of 8 and both base addresses 16-byte aligned.
  *   epilogue 0: out f32 [M][N] = D + bias        (bias device [N] or NULL)
- *            1: aux bf16 [M][N] = D + bias; out bf16 = GELU(aux)   (erf form)
+ *            1: aux bf16 [M][N] = D + bias; out bf16 = GELU(aux), tanh form
+ *               0.5 z (1 + tanh(sqrt(2/pi) (z + 0.044715 z^3)))
  *            2: out bf16 = D * GELU'(aux)        (aux device bf16 [M][N], read)
  *            3: out f32 = clamp(D + bias, 0, 1)
  * Synchronises `stream` and reports TMM_ERR_TIMEOUT if a pipeline wait of the
@@ -293,6 +294,17 @@ TMM_API tmm_status tmm_coh_batched_noalloc(const tmm_problem *p, const tmm_launc
  */
 TMM_API tmm_status tmm_gemm_bf16(const void *A, const void *B, const float *bias, int32_t M, int32_t N,
                                  int32_t K, int32_t epilogue, void *out, void *aux, void *stream);
+
+/*
+ * tmm_gemm_bf16 with epilogue 1 or 2 that also writes the transposed copy
+ * outT bf16 [N][ldoT] (outT[n][m] = out[m][n], ldoT >= M; the columns past M
+ * are left untouched), as the surrogate's training step does for its weight
+ * gradients.  Exported for testing; no paper counterpart.  Other epilogues and
+ * a NULL outT return TMM_ERR_INVALID_ARG.
+ */
+TMM_API tmm_status tmm_gemm_bf16_t(const void *A, const void *B, const float *bias, int32_t M, int32_t N,
+                                   int32_t K, int32_t epilogue, void *out, void *aux, void *outT, int32_t ldoT,
+                                   void *stream);
 
 #ifdef __cplusplus
 }

@@ -2,10 +2,13 @@
 
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).  The network is not in
 the paper; this restates its definition -- x = 2 (d - d_min)/(d_max - d_min) - 1
-zero-padded to 64 inputs, hidden layers z = W h + b, h' = GELU(z) (erf form),
+zero-padded to 64 inputs, hidden layers z = W h + b, h' = GELU(z) in its tanh
+form 0.5 z (1 + tanh(sqrt(2/pi) (z + 0.044715 z^3))),
 linear head y = W h + b, loss = mean (y - t)^2 -- and differentiates it with
 autograd.  The GPU kernels store GEMM operands and activations in bf16; the
-reference rounds at the same points so that only accumulation order differs.
+reference rounds the network input and the weights the same way and keeps
+activations in fp64, so the two differ by the bf16 rounding of stored
+activations and by accumulation order.
 """
 from __future__ import annotations
 
@@ -17,13 +20,13 @@ def bf(t):
 
 
 def gelu(z):
-    return 0.5 * z * (1.0 + torch.erf(z / 2.0 ** 0.5))
+    return 0.5 * z * (1.0 + torch.tanh((2.0 / torch.pi) ** 0.5 * (z + 0.044715 * z ** 3)))
 
 
 def forward_backward(layers, d, target, d_min, d_max, kin=64):
     """layers: list of (W [N][K] fp32, b [N] fp32) tensors (CPU).  Returns
-    (loss, [(dW, db)], y) in fp64, rounding GEMM operands and stored
-    activations to bf16 like the kernels do."""
+    (loss, [(dW, db)], y) in fp64, with the input and the weights rounded to
+    bf16 like the kernels' operands."""
     B, L = d.shape
     x = torch.zeros(B, kin, dtype=torch.float64)
     x[:, :L] = 2.0 * (d.double() - d_min) / (d_max - d_min) - 1.0
@@ -36,4 +39,4 @@ def forward_backward(layers, d, target, d_min, d_max, kin=64):
     y = h @ Ws[-1].T + bs[-1]
     loss = ((y - target.double()) ** 2).mean()
     loss.backward()
-    return float(loss), [(W.grad, b.grad) for W, b in zip(Ws, bs)], y.detach()
+    return float(loss.detach()), [(W.grad, b.grad) for W, b in zip(Ws, bs)], y.detach()

@@ -33,7 +33,7 @@ TMM_POL_P = 2
 
 EXPORTED = ("tmm_coh_batched", "tmm_coh_batched_ex", "tmm_workspace_size", "tmm_workspace_status",
             "tmm_coh_grad", "tmm_status_string", "tmm_last_cuda_error", "tmm_version",
-            "tmm_probe_fma_rate", "tmm_gemm_bf16", "tmm_coh_batched_noalloc",
+            "tmm_probe_fma_rate", "tmm_gemm_bf16", "tmm_gemm_bf16_t", "tmm_coh_batched_noalloc",
             "tmm_surrogate_create", "tmm_surrogate_destroy", "tmm_surrogate_outputs", "tmm_surrogate_parameters",
             "tmm_surrogate_generate", "tmm_surrogate_train_step", "tmm_surrogate_infer", "tmm_surrogate_layer",
             "tmm_surrogate_status", "tmm_surrogate_save", "tmm_surrogate_load")
@@ -113,6 +113,8 @@ def load(path: Optional[str] = None):
                                            ctypes.POINTER(ctypes.c_float), vp]
         lib.tmm_gemm_bf16.argtypes = [vp, vp, vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                       vp, vp, vp]
+        lib.tmm_gemm_bf16_t.argtypes = [vp, vp, vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                        vp, vp, vp, ctypes.c_int32, vp]
         lib.tmm_coh_batched_noalloc.argtypes = [P, C, vp, vp, vp]
         i32, f32 = ctypes.c_int32, ctypes.c_float
         lib.tmm_surrogate_create.argtypes = [ctypes.POINTER(TmmSurrogateDesc), ctypes.POINTER(vp)]
@@ -135,7 +137,7 @@ def load(path: Optional[str] = None):
             getattr(lib, name).restype = ctypes.c_int
         for name in ("tmm_coh_batched", "tmm_coh_batched_ex", "tmm_workspace_size",
                      "tmm_workspace_status", "tmm_coh_grad", "tmm_probe_fma_rate", "tmm_gemm_bf16",
-                     "tmm_coh_batched_noalloc"):
+                     "tmm_gemm_bf16_t", "tmm_coh_batched_noalloc"):
             getattr(lib, name).restype = ctypes.c_int
         if path is None:
             _lib = lib
@@ -310,6 +312,15 @@ def tmm_gemm_bf16(A: torch.Tensor, B: torch.Tensor, bias: Optional[torch.Tensor]
     N = B.shape[0]
     _check("tmm_gemm_bf16", load().tmm_gemm_bf16(_ptr(A), _ptr(B), _ptr(bias), M, N, K, epilogue, _ptr(out),
                                                  _ptr(aux), _stream(stream)))
+
+
+def tmm_gemm_bf16_t(A: torch.Tensor, B: torch.Tensor, bias: Optional[torch.Tensor], epilogue: int,
+                    out: torch.Tensor, aux: Optional[torch.Tensor], outT: torch.Tensor, stream=None):
+    """tmm_gemm_bf16 (GELU or GELU' epilogue) plus the transposed copy outT [N][ldoT]."""
+    M, K = A.shape
+    N = B.shape[0]
+    _check("tmm_gemm_bf16_t", load().tmm_gemm_bf16_t(_ptr(A), _ptr(B), _ptr(bias), M, N, K, epilogue, _ptr(out),
+                                                     _ptr(aux), _ptr(outT), int(outT.stride(0)), _stream(stream)))
 
 
 def tmm_version() -> int:

@@ -97,6 +97,10 @@ tmm_status gemm(const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *B, int ldb
         if (!ep.err) return TMM_ERR_CUDA;
     }
     const int BN = N >= 256 ? 256 : (N >= 128 ? 128 : 64);  // >= 32 columns per epilogue warp slice
+    auto al16 = [](const void *p) { return reinterpret_cast<uintptr_t>(p) % 16 == 0; };
+    const bool f32 = ep.epi == EPI_F32 || ep.epi == EPI_F32_CLAMP;
+    ep.vec = (f32 ? (ep.ldo % 4 == 0 && al16(ep.out_f32)) : (ep.ldo % 8 == 0 && al16(ep.out_bf))) && al16(ep.bias) &&
+             al16(ep.aux) && (!ep.out_bfT || (ep.ldoT % 8 == 0 && al16(ep.out_bfT)));
     CUtensorMap ta, tb;
     tmm_status s = make_tmap(&ta, A, M, K, lda, BM);
     if (s != TMM_OK) return s;
@@ -131,8 +135,8 @@ tmm_status gemm_status(cudaStream_t st)
 
 using namespace tmm;
 
-extern "C" TMM_API tmm_status tmm_gemm_bf16(const void *A, const void *B, const float *bias, int32_t M, int32_t N,
-                                            int32_t K, int32_t epilogue, void *out, void *aux, void *stream)
+static tmm_status gemm_entry(const void *A, const void *B, const float *bias, int32_t M, int32_t N, int32_t K,
+                             int32_t epilogue, void *out, void *aux, void *outT, int32_t ldoT, void *stream)
 {
     if (!A || !B || !out || M < 0 || N < 0 || K < 0 || epilogue < 0 || epilogue > 3) return TMM_ERR_INVALID_ARG;
     if ((epilogue == gemm::EPI_DGELU) && !aux) return TMM_ERR_INVALID_ARG;
@@ -143,11 +147,27 @@ extern "C" TMM_API tmm_status tmm_gemm_bf16(const void *A, const void *B, const 
     if (epilogue == gemm::EPI_F32 || epilogue == gemm::EPI_F32_CLAMP) ep.out_f32 = static_cast<float *>(out);
     else ep.out_bf = static_cast<__nv_bfloat16 *>(out);
     ep.aux = static_cast<__nv_bfloat16 *>(aux);
+    ep.out_bfT = static_cast<__nv_bfloat16 *>(outT);
+    ep.ldoT = ldoT;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     tmm_status s = gemm::clear_error(st);
     if (s != TMM_OK) return s;
-    s = gemm::gemm(static_cast<const __nv_bfloat16 *>(A), K, static_cast<const __nv_bfloat16 *>(B), K, M,
-                              N, K, ep, st);
+    s = gemm::gemm(static_cast<const __nv_bfloat16 *>(A), K, static_cast<const __nv_bfloat16 *>(B), K, M, N, K, ep,
+                   st);
     if (s != TMM_OK) return s;
     return gemm::gemm_status(st);
+}
+
+extern "C" TMM_API tmm_status tmm_gemm_bf16(const void *A, const void *B, const float *bias, int32_t M, int32_t N,
+                                            int32_t K, int32_t epilogue, void *out, void *aux, void *stream)
+{
+    return gemm_entry(A, B, bias, M, N, K, epilogue, out, aux, nullptr, 0, stream);
+}
+
+extern "C" TMM_API tmm_status tmm_gemm_bf16_t(const void *A, const void *B, const float *bias, int32_t M, int32_t N,
+                                              int32_t K, int32_t epilogue, void *out, void *aux, void *outT,
+                                              int32_t ldoT, void *stream)
+{
+    if (!outT || (epilogue != gemm::EPI_GELU && epilogue != gemm::EPI_DGELU) || ldoT < M) return TMM_ERR_INVALID_ARG;
+    return gemm_entry(A, B, bias, M, N, K, epilogue, out, aux, outT, ldoT, stream);
 }

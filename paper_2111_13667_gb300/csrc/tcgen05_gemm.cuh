@@ -3,15 +3,17 @@
 //
 //   D[M][N] = sum_k A[M][K] * B[N][K]          (both operands K-major, bf16)
 //
-// One CTA of 128 threads computes a 128 x BN tile:
+// One persistent CTA per SM (576 threads) computes 128 x BN tiles:
 //   * warp 0 / lane 0 loads K-blocks of 64 (128-byte rows, 128-byte swizzle)
 //     of A and B with TMA into an S-stage shared-memory ring (mbarrier
 //     transaction counts);
-//   * warp 1 / lane 0 issues tcgen05.mma (M = 128, N = BN, K = 16) into an
-//     fp32 accumulator in tensor memory and frees each stage with
+//   * warp 1 / lane 0 issues tcgen05.mma (M = 128, N = BN, K = 16) into one of
+//     two fp32 accumulators in tensor memory and frees each stage with
 //     tcgen05.commit;
-//   * all four warps read their 32 TMEM lanes back with tcgen05.ld and apply
-//     the epilogue (bias, GELU, GELU derivative, clamp) before storing.
+//   * sixteen epilogue warps (four per 32-lane TMEM quarter, each a column
+//     slice) read the other accumulator back with tcgen05.ld, apply the
+//     epilogue (bias, GELU, GELU derivative, clamp) and store through a
+//     per-warp staging buffer with 16-byte stores.
 // Every wait is bounded by %globaltimer: on expiry the CTA records an error,
 // drains what it issued (again bounded), frees its tensor memory and returns.
 #pragma once
@@ -45,6 +47,7 @@ struct EpiArgs {
     __nv_bfloat16 *aux;     // [M][ldo] pre-activation (written by GELU, read by DGELU)
     __nv_bfloat16 *out_bfT; // [N][ldoT] transposed copy of out_bf, or null
     int ldo, ldoT;
+    int vec;                // 1: pointers 16-byte aligned and ldo, ldoT multiples of 16 bytes
     int *err;               // error flag (device)
 };
 
@@ -185,14 +188,54 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float v[32])
     tmem_ld16(taddr + 16, v + 16);
 }
 
-// GELU, erf form (CUDA's erff), and its derivative.
-__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+// GELU, tanh form: gelu(z) = 0.5 z (1 + tanh u), u = sqrt(2/pi) (z + 0.044715 z^3),
+// evaluated as z * sigma(2u) (0.5 (1 + tanh u) = sigma(2u)) with one ex2.approx
+// and one rcp.approx.  kG0, kG1: -2 sqrt(2/pi) log2(e) and its product with
+// 0.044715, so that sigma(2u) = 1 / (1 + 2^(z (kG0 + kG1 z^2))).
+constexpr float kG0 = -2.3022082f;
+constexpr float kG1 = -0.10294324f;
+constexpr float kW0 = 1.5957691f;   // d(2u)/dz = kW0 + kW1 z^2: 2 sqrt(2/pi), and its product with 3 * 0.044715
+constexpr float kW1 = 0.21406445f;
+
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float gelu_sigma(float z)
+{
+    const float z2 = z * z;
+    return rcp_approx(1.0f + ex2_approx(z * fmaf(kG1, z2, kG0)));
+}
+
+__device__ __forceinline__ float gelu(float z) { return z * gelu_sigma(z); }
+
+// d/dz [z sigma(2u)] = s + z s (1 - s) d(2u)/dz
 __device__ __forceinline__ float gelu_grad(float z)
 {
-    const float cdf = 0.5f * (1.0f + erff(z * 0.70710678118654752f));
-    const float pdf = 0.39894228040143268f * __expf(-0.5f * z * z);
-    return cdf + z * pdf;
+    const float s = gelu_sigma(z);
+    const float w = fmaf(kW1, z * z, kW0);
+    return fmaf(z * s * (1.0f - s), w, s);
 }
+
+// Two floats to one word of two bf16 (round to nearest even), a in the low half.
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b)
+{
+    uint32_t r;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(b), "f"(a));
+    return r;
+}
+__device__ __forceinline__ float bf_lo(uint32_t w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf_hi(uint32_t w) { return __uint_as_float(w & 0xFFFF0000u); }
 
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
 {
@@ -202,20 +245,199 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
 constexpr int kEpiWarps = 16;                      // epilogue warps (four per TMEM lane quarter)
 constexpr int kGemmThreads = 64 + 32 * kEpiWarps;  // producer warp, MMA warp, epilogue warps
 
+
 template <int BN, int STAGES>
 struct GemmSmem {
     static constexpr size_t a_bytes = (size_t)BM * BK * 2;
     static constexpr size_t b_bytes = (size_t)BN * BK * 2;
     static constexpr size_t ring = STAGES * (a_bytes + b_bytes);
-    static constexpr size_t stage = (size_t)kEpiWarps * 32 * 33 * 4;  // per-warp 32 x 33 floats
+    static constexpr size_t stage = (size_t)kEpiWarps * 32 * 33 * 4;  // per warp 32 x 33 floats (16-byte multiple)
     static constexpr size_t bars = (2 * STAGES + 5) * 8 + 16;
     static constexpr size_t total = 1024 + ring + stage + bars;  // + alignment slack
 };
 
-// Apply the epilogue to one 32-column chunk of one warp's 32 rows: stage the
-// values in shared memory, then write them back row by row (coalesced).
-__device__ __forceinline__ void epilogue_chunk(const EpiArgs &ep, const float (&v)[32], float *stg, int row0, int n0c,
-                                               int M, int N, int lane)
+// ---- epilogue -------------------------------------------------------------
+// Each epilogue warp owns 32 accumulator rows (its TMEM lane quarter); after a
+// 32x32b tcgen05.ld lane i holds 32 consecutive columns of row row0 + i.  The
+// warp's staging buffer (32 rows of 128 bytes) turns these per-row registers
+// into 16-byte stores that are contiguous across lanes, and into the
+// transposed copy.  Rows are stored as 16-byte groups at a row-dependent XOR
+// position so that row-wise 16-byte accesses and the column-wise 4-byte reads
+// of the transpose meet no bank conflicts.
+
+// word offset of group g (0..7) of fp32 row r; of group g (0..3) of bf16 row r
+__device__ __forceinline__ int stg_f32(int r, int g) { return r * 32 + 4 * (g ^ (r & 7)); }
+__device__ __forceinline__ int stg_bf(int r, int g) { return r * 16 + 4 * (g ^ ((r >> 1) & 3)); }
+
+// this lane's row of 16 bf16 pairs into the staging buffer
+__device__ __forceinline__ void stage_row_bf(uint32_t *stg, const uint32_t (&w)[16], int lane)
+{
+#pragma unroll
+    for (int g = 0; g < 4; ++g)
+        *reinterpret_cast<uint4 *>(stg + stg_bf(lane, g)) = make_uint4(w[4 * g], w[4 * g + 1], w[4 * g + 2], w[4 * g + 3]);
+}
+
+// staged bf16 rows -> out[row0 + r][col0 ...]: four lanes per 64-byte row
+__device__ __forceinline__ void store_rows_bf(const uint32_t *stg, __nv_bfloat16 *out, int ldo, int row0, int col0,
+                                              int M, int lane)
+{
+    const int g = lane & 3;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int r = 8 * k + (lane >> 2);
+        if (row0 + r < M)
+            *reinterpret_cast<uint4 *>(out + (long long)(row0 + r) * ldo + col0 + 8 * g) =
+                *reinterpret_cast<const uint4 *>(stg + stg_bf(r, g));
+    }
+}
+
+// staged bf16 rows -> outT[col0 + c][row0 ... row0 + 31] (all 32 rows valid).
+// Lane (cp, h) reads word cp (columns 2cp, 2cp+1) of rows 16h .. 16h+15 and
+// splits each pair of rows into one word per column with a byte permute;
+// lanes with h = 1 visit the rows in swapped pairs so that both halves of the
+// warp read different banks.
+__device__ __forceinline__ void store_cols_bf(const uint32_t *stg, __nv_bfloat16 *outT, int ldoT, int row0, int col0,
+                                              int lane)
+{
+    const int cp = lane & 15, h = lane >> 4;
+    uint32_t w[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        const int r = 16 * h + (j ^ h);
+        w[j] = stg[r * 16 + 4 * ((cp >> 2) ^ ((r >> 1) & 3)) + (cp & 3)];
+    }
+    const uint32_t sel0 = h ? 0x1054u : 0x5410u;  // low halves of the two rows, in row order
+    const uint32_t sel1 = h ? 0x3276u : 0x7632u;  // high halves
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {  // w[2k]: column 2cp, w[2k+1]: column 2cp+1, rows 2k and 2k+1
+        const uint32_t a = w[2 * k], b = w[2 * k + 1];
+        w[2 * k] = __byte_perm(a, b, sel0);
+        w[2 * k + 1] = __byte_perm(a, b, sel1);
+    }
+    uint4 *p0 = reinterpret_cast<uint4 *>(outT + (long long)(col0 + 2 * cp) * ldoT + row0 + 16 * h);
+    uint4 *p1 = reinterpret_cast<uint4 *>(outT + (long long)(col0 + 2 * cp + 1) * ldoT + row0 + 16 * h);
+    p0[0] = make_uint4(w[0], w[2], w[4], w[6]);
+    p0[1] = make_uint4(w[8], w[10], w[12], w[14]);
+    p1[0] = make_uint4(w[1], w[3], w[5], w[7]);
+    p1[1] = make_uint4(w[9], w[11], w[13], w[15]);
+}
+
+// transposed copy of a partial row block (rows past M skipped): each lane
+// takes its own staged row back and stores it one element at a time (lanes
+// hold consecutive rows, so each warp store covers 64 contiguous bytes)
+__device__ __forceinline__ void store_cols_bf_tail(const uint32_t *stg, __nv_bfloat16 *outT, int ldoT, int row0,
+                                                   int col0, int M, int lane)
+{
+    const int row = row0 + lane;
+    if (row >= M) return;
+    uint32_t w[16];
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+        const uint4 t = *reinterpret_cast<const uint4 *>(stg + stg_bf(lane, g));
+        w[4 * g] = t.x, w[4 * g + 1] = t.y, w[4 * g + 2] = t.z, w[4 * g + 3] = t.w;
+    }
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        outT[(long long)(col0 + 2 * i) * ldoT + row] = __ushort_as_bfloat16((unsigned short)(w[i] & 0xFFFFu));
+        outT[(long long)(col0 + 2 * i + 1) * ldoT + row] = __ushort_as_bfloat16((unsigned short)(w[i] >> 16));
+    }
+}
+
+// bias[col0 + 4j .. col0 + 4j + 3] (zeros without a bias); the address is the
+// same in every lane, so the load is a broadcast
+__device__ __forceinline__ float4 bias4(const float *bias, int col0, int j)
+{
+    return bias ? __ldg(reinterpret_cast<const float4 *>(bias + col0) + j) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+}
+
+// bf16 packed outputs of a full 32-column chunk: row-major out, optional transposed copy
+__device__ __forceinline__ void write_bf_chunk(const EpiArgs &ep, const uint32_t (&y)[16], uint32_t *stg, int row0,
+                                               int col0, int M, int lane)
+{
+    stage_row_bf(stg, y, lane);
+    __syncwarp();
+    store_rows_bf(stg, ep.out_bf, ep.ldo, row0, col0, M, lane);
+    if (ep.out_bfT) {
+        if (row0 + 32 <= M) store_cols_bf(stg, ep.out_bfT, ep.ldoT, row0, col0, lane);
+        else store_cols_bf_tail(stg, ep.out_bfT, ep.ldoT, row0, col0, M, lane);
+    }
+    __syncwarp();
+}
+
+// Full 32-column chunk, 16-byte aligned outputs.
+template <int EPI>
+__device__ __forceinline__ void epilogue_chunk_vec(const EpiArgs &ep, const float (&v)[32], uint32_t *stg, int row0,
+                                                   int col0, int M, int lane)
+{
+    if (EPI == EPI_F32 || EPI == EPI_F32_CLAMP) {
+#pragma unroll
+        for (int g = 0; g < 8; ++g) {
+            float4 t = bias4(ep.bias, col0, g);
+            t.x += v[4 * g], t.y += v[4 * g + 1], t.z += v[4 * g + 2], t.w += v[4 * g + 3];
+            if (EPI == EPI_F32_CLAMP) {
+                t.x = fminf(fmaxf(t.x, 0.0f), 1.0f), t.y = fminf(fmaxf(t.y, 0.0f), 1.0f);
+                t.z = fminf(fmaxf(t.z, 0.0f), 1.0f), t.w = fminf(fmaxf(t.w, 0.0f), 1.0f);
+            }
+            *reinterpret_cast<float4 *>(stg + stg_f32(lane, g)) = t;
+        }
+        __syncwarp();
+        const int g = lane & 7;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int r = 4 * k + (lane >> 3);
+            if (row0 + r < M)
+                *reinterpret_cast<float4 *>(ep.out_f32 + (long long)(row0 + r) * ep.ldo + col0 + 4 * g) =
+                    *reinterpret_cast<const float4 *>(stg + stg_f32(r, g));
+        }
+        __syncwarp();
+    } else if (EPI == EPI_GELU) {
+        uint32_t w[16];  // bf16 pre-activations, then activations
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const float4 b = bias4(ep.bias, col0, j);
+            w[2 * j] = pack_bf16(v[4 * j] + b.x, v[4 * j + 1] + b.y);
+            w[2 * j + 1] = pack_bf16(v[4 * j + 2] + b.z, v[4 * j + 3] + b.w);
+        }
+        if (ep.aux) {
+            stage_row_bf(stg, w, lane);
+            __syncwarp();
+            store_rows_bf(stg, ep.aux, ep.ldo, row0, col0, M, lane);
+            __syncwarp();
+        }
+#pragma unroll
+        for (int i = 0; i < 16; ++i) w[i] = pack_bf16(gelu(bf_lo(w[i])), gelu(bf_hi(w[i])));
+        write_bf_chunk(ep, w, stg, row0, col0, M, lane);
+    } else {  // EPI_DGELU: y = acc * gelu'(aux); rows of aux read through the staging buffer
+        {
+            const int g = lane & 3;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int r = 8 * k + (lane >> 2);
+                uint4 t = make_uint4(0u, 0u, 0u, 0u);
+                if (row0 + r < M)
+                    t = __ldg(reinterpret_cast<const uint4 *>(ep.aux + (long long)(row0 + r) * ep.ldo + col0 + 8 * g));
+                *reinterpret_cast<uint4 *>(stg + stg_bf(r, g)) = t;
+            }
+        }
+        __syncwarp();
+        uint32_t zw[16];
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+            const uint4 t = *reinterpret_cast<const uint4 *>(stg + stg_bf(lane, g));
+            zw[4 * g] = t.x, zw[4 * g + 1] = t.y, zw[4 * g + 2] = t.z, zw[4 * g + 3] = t.w;
+        }
+        __syncwarp();
+#pragma unroll
+        for (int i = 0; i < 16; ++i)
+            zw[i] = pack_bf16(v[2 * i] * gelu_grad(bf_lo(zw[i])), v[2 * i + 1] * gelu_grad(bf_hi(zw[i])));
+        write_bf_chunk(ep, zw, stg, row0, col0, M, lane);
+    }
+}
+
+// Any chunk (ragged columns, unaligned outputs): element by element, staged
+// through shared memory (stride 33 floats) for row-wise stores.
+__device__ __forceinline__ void epilogue_chunk_scalar(const EpiArgs &ep, const float (&v)[32], float *stg, int row0,
+                                                      int n0c, int M, int N, int lane)
 {
     const int row = row0 + lane;
 #pragma unroll
@@ -252,6 +474,21 @@ __device__ __forceinline__ void epilogue_chunk(const EpiArgs &ep, const float (&
         }
     }
     __syncwarp();
+}
+
+__device__ __forceinline__ void epilogue_chunk(const EpiArgs &ep, const float (&v)[32], float *stg, int row0, int n0c,
+                                               int M, int N, int lane)
+{
+    if (ep.vec && n0c + 32 <= N) {
+        uint32_t *sw = reinterpret_cast<uint32_t *>(stg);
+        switch (ep.epi) {
+        case EPI_F32: epilogue_chunk_vec<EPI_F32>(ep, v, sw, row0, n0c, M, lane); return;
+        case EPI_F32_CLAMP: epilogue_chunk_vec<EPI_F32_CLAMP>(ep, v, sw, row0, n0c, M, lane); return;
+        case EPI_GELU: epilogue_chunk_vec<EPI_GELU>(ep, v, sw, row0, n0c, M, lane); return;
+        default: epilogue_chunk_vec<EPI_DGELU>(ep, v, sw, row0, n0c, M, lane); return;
+        }
+    }
+    epilogue_chunk_scalar(ep, v, stg, row0, n0c, M, N, lane);
 }
 
 // Persistent, warp-specialised kernel.  Tiles (128 x BN) are dealt round-robin
@@ -382,6 +619,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             tc_fence_after();
             const int m0 = (tile / n_tiles) * BM, n0 = (tile % n_tiles) * BN;
             const int row0 = m0 + q * 32;
+#pragma unroll 1
             for (int c = half * kSliceCols; half < kSlices && c < (half + 1) * kSliceCols; c += 32) {
                 float v[32];
                 tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * BN + c), v);

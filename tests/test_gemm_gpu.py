@@ -1,5 +1,6 @@
 """The tcgen05 bf16 GEMM (surrogate building block) against an fp32 matmul of
-the same bf16 operands, for every fused epilogue, tile width and a ragged M."""
+the same bf16 operands, for every fused epilogue, tile width, ragged M and N
+(the element-wise tail path) and the transposed copy of the training step."""
 import pytest
 import torch
 
@@ -16,7 +17,9 @@ def _lib():
 
 
 def ref_gelu(z):
-    return 0.5 * z * (1 + torch.erf(z / 2 ** 0.5))
+    """GELU, tanh form, in fp64."""
+    z = z.double()
+    return 0.5 * z * (1 + torch.tanh((2 / torch.pi) ** 0.5 * (z + 0.044715 * z ** 3)))
 
 
 def operands(M, N, K, seed):
@@ -28,32 +31,77 @@ def operands(M, N, K, seed):
 
 
 @pytest.mark.parametrize("M,N,K", [(128, 256, 64), (300, 256, 1024), (256, 1024, 1024), (130, 128, 192),
-                                   (512, 64, 256), (1000, 4096, 128)])
-def test_gemm_f32_epilogue(M, N, K):
+                                   (512, 64, 256), (1000, 4096, 128), (257, 200, 128), (70, 96, 64)])
+@pytest.mark.parametrize("with_bias", [True, False])
+def test_gemm_f32_epilogue(M, N, K, with_bias):
     A, B, bias = operands(M, N, K, M + N + K)
+    if not with_bias:
+        bias = None
     out = torch.empty(M, N, device="cuda")
     abi.tmm_gemm_bf16(A, B, bias, 0, out)
-    ref = A.float() @ B.float().T + bias
+    ref = A.float() @ B.float().T + (bias if bias is not None else 0.0)
     err = (out - ref).abs().max().item()
     assert err <= 1e-4 * max(1.0, ref.abs().max().item()), err
 
 
-def test_gemm_gelu_and_dgelu_and_clamp():
-    M, N, K = 384, 256, 512
-    A, B, bias = operands(M, N, K, 7)
+def check_gelu(M, N, K, seed):
+    A, B, bias = operands(M, N, K, seed)
     z = A.float() @ B.float().T + bias
     out = torch.empty(M, N, dtype=torch.bfloat16, device="cuda")
     aux = torch.empty(M, N, dtype=torch.bfloat16, device="cuda")
-    abi.tmm_gemm_bf16(A, B, bias, 1, out, aux)
-    assert (aux.float() - z).abs().max().item() <= 1e-2 * max(1.0, z.abs().max().item())
-    assert (out.float() - ref_gelu(aux.float())).abs().max().item() <= 2e-2
+    ldoT = (M + 7) // 8 * 8 + 8
+    outT = torch.full((N, ldoT), 7.0, dtype=torch.bfloat16, device="cuda")
+    abi.tmm_gemm_bf16_t(A, B, bias, 1, out, aux, outT)
+    # pre-activation: bf16 of the fp32 accumulator
+    assert (aux.float() - z).abs().max().item() <= 4e-3 * max(1.0, z.abs().max().item())
+    # activation: bf16 of GELU(aux), within bf16 rounding of the fp64 value
+    ref = ref_gelu(aux.float())
+    dev = (out.double() - ref).abs() - (4e-3 * ref.abs() + 2e-6 * (aux.double().abs() + 1))
+    assert dev.max().item() <= 0, dev.max().item()
+    # transposed copy: the same bits, columns past M untouched
+    assert torch.equal(outT[:, :M], out.T)
+    assert bool((outT[:, M:] == 7.0).all())
     # derivative epilogue reads the saved pre-activation
     out2 = torch.empty(M, N, dtype=torch.bfloat16, device="cuda")
-    abi.tmm_gemm_bf16(A, B, None, 2, out2, aux)
-    zz = aux.float().requires_grad_(True)
+    out2T = torch.full((N, ldoT), 7.0, dtype=torch.bfloat16, device="cuda")
+    abi.tmm_gemm_bf16_t(A, B, None, 2, out2, aux, out2T)
+    zz = aux.double().requires_grad_(True)
     ref_gelu(zz).sum().backward()
-    ref2 = (A.float() @ B.float().T) * zz.grad
-    assert (out2.float() - ref2).abs().max().item() <= 2e-2 * max(1.0, ref2.abs().max().item())
+    ref2 = (A.float() @ B.float().T).double() * zz.grad
+    tol = 4e-3 * ref2.abs() + 1e-4 * max(1.0, ref2.abs().max().item())
+    assert bool(((out2.double() - ref2).abs() <= tol).all())
+    assert torch.equal(out2T[:, :M], out2.T)
+    assert bool((out2T[:, M:] == 7.0).all())
+    # clamp epilogue
     out3 = torch.empty(M, N, device="cuda")
     abi.tmm_gemm_bf16(A, B, bias, 3, out3)
     assert (out3 - z.clamp(0, 1)).abs().max().item() <= 1e-4 * max(1.0, z.abs().max().item())
+
+
+@pytest.mark.parametrize("M,N,K", [(384, 256, 512), (300, 1024, 256), (97, 200, 64), (640, 64, 128)])
+def test_gemm_gelu_dgelu_transpose_and_clamp(M, N, K):
+    check_gelu(M, N, K, M * 7 + N)
+
+
+def test_gemm_gelu_without_transposed_copy_matches():
+    M, N, K = 256, 512, 256
+    A, B, bias = operands(M, N, K, 11)
+    out = torch.empty(M, N, dtype=torch.bfloat16, device="cuda")
+    aux = torch.empty(M, N, dtype=torch.bfloat16, device="cuda")
+    abi.tmm_gemm_bf16(A, B, bias, 1, out, aux)
+    out_t = torch.empty_like(out)
+    aux_t = torch.empty_like(aux)
+    outT = torch.empty(N, M, dtype=torch.bfloat16, device="cuda")
+    abi.tmm_gemm_bf16_t(A, B, bias, 1, out_t, aux_t, outT)
+    assert torch.equal(out, out_t) and torch.equal(aux, aux_t) and torch.equal(outT, out.T)
+
+
+def test_gemm_transposed_entry_rejects_bad_arguments():
+    A, B, bias = operands(64, 64, 64, 1)
+    out = torch.empty(64, 64, dtype=torch.bfloat16, device="cuda")
+    outT = torch.empty(64, 32, dtype=torch.bfloat16, device="cuda")  # ldoT < M
+    with pytest.raises(RuntimeError):
+        abi.tmm_gemm_bf16_t(A, B, bias, 1, out, None, outT)
+    outT = torch.empty(64, 64, dtype=torch.bfloat16, device="cuda")
+    with pytest.raises(RuntimeError):
+        abi.tmm_gemm_bf16_t(A, B, bias, 0, torch.empty(64, 64, device="cuda"), None, outT)

@@ -1,0 +1,113 @@
+"""Pins of the surrogate-network oracle (``oracle/mlp.py``) on the CPU.
+
+The network is a design of this project (the paper defines none), so its pins
+are mathematical: the tanh-form GELU against the exact GELU z Phi(z) (a
+different function, within the known 5e-4 of the approximation), its odd
+symmetry, a brute-force forward pass of a tiny network, and finite differences
+of the loss for every bias and for weights at bf16-exact values."""
+import math
+
+import numpy as np
+import pytest
+import torch
+from scipy.special import ndtr
+
+from oracle import mlp
+
+
+def test_gelu_tanh_form_tracks_exact_gelu():
+    z = torch.linspace(-8.0, 8.0, 16001, dtype=torch.float64)
+    exact = z * torch.as_tensor(ndtr(z.numpy()))
+    dev = (mlp.gelu(z) - exact).abs()
+    # the tanh form is within 4.8e-4 of z Phi(z), largest near z = -2.7 ...
+    assert float(dev.max()) < 4.8e-4
+    # ... and is not the erf form itself
+    assert float(dev.max()) > 4.0e-4
+    assert abs(float(z[dev.argmax()]) + 2.7) < 0.05
+
+
+def test_gelu_odd_part_is_half_identity():
+    # 0.5 z (1 + tanh u(z)) with u odd: gelu(z) - gelu(-z) = z exactly
+    z = torch.linspace(-6.0, 6.0, 1201, dtype=torch.float64)
+    assert float((mlp.gelu(z) - mlp.gelu(-z) - z).abs().max()) < 1e-14
+    assert float(mlp.gelu(torch.tensor(0.0, dtype=torch.float64))) == 0.0
+
+
+def _net(sizes, seed, kin=64):
+    g = torch.Generator().manual_seed(seed)
+    layers = []
+    k = kin
+    for n in sizes:
+        W = (torch.randn(n, k, generator=g) / k ** 0.5).to(torch.bfloat16).float()
+        b = torch.randn(n, generator=g) * 0.3
+        layers.append((W, b))
+        k = n
+    return layers
+
+
+def test_forward_matches_brute_force_loops():
+    layers = _net([5, 4, 3], seed=1)
+    d = torch.tensor([[30.0, 100.0, 240.0], [25.0, 60.0, 200.0]])
+    t = torch.zeros(2, 3)
+    _, _, y = mlp.forward_backward(layers, d, t, 20.0, 250.0)
+    c = math.sqrt(2.0 / math.pi)
+    for b in range(2):
+        h = [0.0] * 64
+        for i in range(3):
+            x = 2.0 * (float(d[b, i]) - 20.0) / 230.0 - 1.0
+            h[i] = float(torch.tensor(x).to(torch.bfloat16))
+        for li, (W, bias) in enumerate(layers):
+            out = []
+            for n in range(W.shape[0]):
+                s = float(bias[n]) + sum(float(W[n, k]) * h[k] for k in range(len(h)))
+                if li < len(layers) - 1:
+                    s = 0.5 * s * (1.0 + math.tanh(c * (s + 0.044715 * s ** 3)))
+                out.append(s)
+            h = out
+        assert np.allclose(h, y[b].numpy(), rtol=1e-12, atol=1e-12)
+
+
+def _loss(layers, d, t):
+    return mlp.forward_backward(layers, d, t, 20.0, 250.0)[0]
+
+
+@pytest.fixture(scope="module")
+def problem():
+    layers = _net([6, 6, 4], seed=2)
+    g = torch.Generator().manual_seed(3)
+    d = 20.0 + 230.0 * torch.rand(7, 5, generator=g)
+    t = torch.rand(7, 4, generator=g)
+    return layers, d, t
+
+
+def test_bias_gradients_match_finite_differences(problem):
+    layers, d, t = problem
+    _, grads, _ = mlp.forward_backward(layers, d, t, 20.0, 250.0)
+    h = 1e-5
+    for li, (W, b) in enumerate(layers):
+        for n in range(b.shape[0]):
+            plus = [(W_, b_.double().clone()) for W_, b_ in layers]
+            minus = [(W_, b_.double().clone()) for W_, b_ in layers]
+            plus[li][1][n] += h
+            minus[li][1][n] -= h
+            fd = (_loss(plus, d, t) - _loss(minus, d, t)) / (2 * h)
+            assert abs(fd - float(grads[li][1][n])) <= 1e-7 + 1e-6 * abs(fd), (li, n)
+
+
+def test_weight_gradients_match_finite_differences(problem):
+    # weights pass through bf16 rounding, so the step is one bf16 spacing at a
+    # bf16-exact value (0.5: spacing 2^-8); central differences stay smooth
+    layers, d, t = problem
+    for li, (n, k) in enumerate([(1, 2), (3, 0), (2, 5)]):
+        base = [(W.clone(), b) for W, b in layers]
+        base[li][0][n, k] = 0.5
+        _, grads, _ = mlp.forward_backward(base, d, t, 20.0, 250.0)
+        h = 2.0 ** -8
+        plus = [(W.clone(), b) for W, b in base]
+        minus = [(W.clone(), b) for W, b in base]
+        plus[li][0][n, k] = 0.5 + h
+        minus[li][0][n, k] = 0.5 - h
+        fd = (_loss(plus, d, t) - _loss(minus, d, t)) / (2 * h)
+        g = float(grads[li][0][n, k])
+        assert abs(fd - g) <= 1e-6 + 1e-3 * abs(g), (li, fd, g)
+        assert abs(g) > 1e-6
