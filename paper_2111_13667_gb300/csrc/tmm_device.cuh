@@ -34,6 +34,11 @@ template <typename R> __device__ __forceinline__ Cx<R> cfma(Cx<R> a, Cx<R> b, Cx
 {
     return {fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y))};
 }
+// c - a * b
+template <typename R> __device__ __forceinline__ Cx<R> cfnma(Cx<R> a, Cx<R> b, Cx<R> c)
+{
+    return {fma(-a.x, b.x, fma(a.y, b.y, c.x)), fma(-a.x, b.y, fma(-a.y, b.x, c.y))};
+}
 template <typename R> __device__ __forceinline__ Cx<R> conj(Cx<R> a) { return {a.x, -a.y}; }
 template <typename R> __device__ __forceinline__ R abs2(Cx<R> a) { return fma(a.x, a.x, a.y * a.y); }
 template <typename R> __device__ __forceinline__ Cx<R> scale(R s, Cx<R> a) { return {s * a.x, s * a.y}; }

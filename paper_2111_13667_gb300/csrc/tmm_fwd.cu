@@ -37,6 +37,62 @@ constexpr int kMaxThreads = 512;
 // e^{Im delta}: diag(e^{-i Re delta}, e^{-2 Im delta} e^{i Re delta}).  R does
 // not see the factor; for T the product of all factors enters |t|^2 as
 // 2^{-2 K Y}, Y = sum of Im(delta) / (2 pi), K = 2 pi log2(e).
+// Interface j | j+1 applied to the amplitude pair (x0, x1) carried from the
+// right, in sum/difference form: with a = k + k', b = k - k' (k = q_j for s,
+// q_j / n_j^2 for p; k' the same for medium j+1),
+//   a x0 + b x1 = k (x0 + x1) + k' (x0 - x1),  b x0 + a x1 = k (x0 + x1) - k' (x0 - x1).
+template <typename R>
+__device__ __forceinline__ void interface_pair(Cx<R> k, Cx<R> kn, Cx<R> &x0, Cx<R> &x1)
+{
+    const Cx<R> sg = x0 + x1, df = x0 - x1;
+    const Cx<R> X = cmul(k, sg);
+    x0 = cfma(kn, df, X);
+    x1 = cfnma(kn, df, X);
+}
+
+// Running state of one point's right-to-left sweep.
+template <typename R> struct Sweep {
+    Cx<R> q_nx, g_nx;        // q and q / n^2 of the medium to the right
+    Cx<R> s0, s1, p0, p1;    // s and p amplitude pairs (scaled)
+    R Ps, Y;                 // prod |q_j|^2 (scaled), sum of Im delta_j / (2 pi)
+};
+
+// Layer j (1..L): its interface with medium j+1, then its phase (Eq. 3).
+template <typename R, int POL>
+__device__ __forceinline__ void layer_step(const StageA<R> *__restrict__ sa, const StageB<R> *__restrict__ sb, int TL,
+                                           int tl, int j, R q0sq, R yi_max, Sweep<R> &w)
+{
+    const StageA<R> A = sa[j * TL + tl];
+    const StageB<R> B = sb[j * TL + tl];
+    R absz;
+    const Cx<R> q = forward_root(Cx<R>{A.d2x + q0sq, A.n2y}, &absz);
+    w.Ps *= absz;
+    // layer phase in turns: delta / (2 pi) = (d / lambda) q, Im clamped
+    const R yr = B.dl * q.x;
+    const R yi = fmin(B.dl * q.y, yi_max);
+    w.Y += yi;
+    R sn, cs;
+    sincos_turn(yr - rint_w(yr), &sn, &cs);
+    const R E2 = exp_m2_turn(yi);
+    const Cx<R> emi = {cs, -sn};            // e^{-i delta} / e^{Im delta}
+    const Cx<R> epi = {E2 * cs, E2 * sn};   // e^{+i delta} / e^{Im delta}
+    if (POL & 1) {
+        interface_pair(q, w.q_nx, w.s0, w.s1);
+        w.s0 = cmul(emi, w.s0);
+        w.s1 = cmul(epi, w.s1);
+    }
+    if (POL & 2) {
+        const Cx<R> g = cmul(q, Cx<R>{A.in2x, A.in2y});
+        interface_pair(g, w.g_nx, w.p0, w.p1);
+        w.p0 = cmul(emi, w.p0);
+        w.p1 = cmul(epi, w.p1);
+        w.g_nx = g;
+    }
+    w.q_nx = q;
+}
+
+// Evaluate one (lambda, theta) point: right-to-left product (Eq. 4) applied to
+// the vector (1, 0) of the exit medium, then r, t (Eqs. 5-6) and R, T.
 template <typename R, int POL>
 __device__ __forceinline__ void eval_point(const StageA<R> *__restrict__ sa, const StageB<R> *__restrict__ sb,
                                            int TL, int tl, int L, R n0, R sin_theta, R cos_theta, R Pp_m,
@@ -50,57 +106,33 @@ __device__ __forceinline__ void eval_point(const StageA<R> *__restrict__ sa, con
 
     StageA<R> A = sa[(L + 1) * TL + tl];
     R absz;
-    Cx<R> q_nx = forward_root(Cx<R>{A.d2x + q0sq, A.n2y}, &absz);
-    const Cx<R> q_out = q_nx, n2_out = {A.d2x + n0 * n0, A.n2y};
-    Cx<R> g_nx = cmul(q_nx, Cx<R>{A.in2x, A.in2y});
-    R Ps = R(1), Y = R(0);
+    Sweep<R> w;
+    w.q_nx = forward_root(Cx<R>{A.d2x + q0sq, A.n2y}, &absz);
+    const Cx<R> q_out = w.q_nx, n2_out = {A.d2x + n0 * n0, A.n2y};
+    w.g_nx = cmul(w.q_nx, Cx<R>{A.in2x, A.in2y});
+    w.Ps = R(1), w.Y = R(0);
     int eP = 0;
-    Cx<R> s0 = {R(1), R(0)}, s1 = {R(0), R(0)}, p0 = {R(1), R(0)}, p1 = {R(0), R(0)};
+    w.s0 = {R(1), R(0)}, w.s1 = {R(0), R(0)}, w.p0 = {R(1), R(0)}, w.p1 = {R(0), R(0)};
     int es = 0, ep = 0;
 
-    for (int j = L; j >= 1; --j) {
-        A = sa[j * TL + tl];
-        const StageB<R> B = sb[j * TL + tl];
-        const Cx<R> q = forward_root(Cx<R>{A.d2x + q0sq, A.n2y}, &absz);
-        Ps *= absz;
-        // layer phase in turns: delta / (2 pi) = (d / lambda) q, Im clamped
-        const R yr = B.dl * q.x;
-        const R yi = fmin(B.dl * q.y, yi_max);
-        Y += yi;
-        R sn, cs;
-        sincos_turn(yr - rint_w(yr), &sn, &cs);
-        const R E2 = exp_m2_turn(yi);
-        const Cx<R> emi = {cs, -sn};            // e^{-i delta} / e^{Im delta}
-        const Cx<R> epi = {E2 * cs, E2 * sn};   // e^{+i delta} / e^{Im delta}
-        if (POL & 1) {
-            const Cx<R> a = q + q_nx, b = q - q_nx;
-            const Cx<R> u0 = cfma(a, s0, cmul(b, s1));
-            const Cx<R> u1 = cfma(b, s0, cmul(a, s1));
-            s0 = cmul(emi, u0);
-            s1 = cmul(epi, u1);
-        }
-        if (POL & 2) {
-            const Cx<R> g = cmul(q, Cx<R>{A.in2x, A.in2y});
-            const Cx<R> a = g + g_nx, b = g - g_nx;
-            const Cx<R> u0 = cfma(a, p0, cmul(b, p1));
-            const Cx<R> u1 = cfma(b, p0, cmul(a, p1));
-            p0 = cmul(emi, u0);
-            p1 = cmul(epi, u1);
-            g_nx = g;
-        }
-        q_nx = q;
-        if ((L - j) % RN == RN - 1) {
-            renorm_scalar(Ps, eP);
-            if (POL & 1) renorm_pair(s0, s1, es);
-            if (POL & 2) renorm_pair(p0, p1, ep);
-        }
+    // groups of RN layers, each followed by a power-of-two rescale
+    int j = L;
+    for (; j >= RN; j -= RN) {
+#pragma unroll
+        for (int k = 0; k < RN; ++k) layer_step<R, POL>(sa, sb, TL, tl, j - k, q0sq, yi_max, w);
+        renorm_scalar(w.Ps, eP);
+        if (POL & 1) renorm_pair(w.s0, w.s1, es);
+        if (POL & 2) renorm_pair(w.p0, w.p1, ep);
     }
-    // interface 0 -> 1; the injection medium is real, so q_0 = n_0 cos(theta)
+    for (; j >= 1; --j) layer_step<R, POL>(sa, sb, TL, tl, j, q0sq, yi_max, w);
+    const Cx<R> q_nx = w.q_nx, g_nx = w.g_nx;
+    const R Ps0 = w.Ps, Y = w.Y;
+// interface 0 -> 1; the injection medium is real, so q_0 = n_0 cos(theta)
     // (computed directly: n_0^2 - beta^2 cancels near grazing incidence)
     A = sa[tl];
     const bool grazing = beta >= n0;  // false for a NaN (complex, rejected) n_0
     const Cx<R> q0 = {c0, R(0)};
-    Ps *= q0.x * q0.x;
+    const R Ps = Ps0 * (q0.x * q0.x);
     const int e4 = 2 * (L + 1);  // the factors 2 of every 2a
     // 2^{-2 K Y} = 2^{yf} 2^{yn}, yn integer
     R u = R(-2.0 * kTwoPi * kLog2e) * Y;
@@ -109,9 +141,8 @@ __device__ __forceinline__ void eval_point(const StageA<R> *__restrict__ sa, con
     const R yscale = exp2_w(u - un);
     const int yn = (int)un;
     if (POL & 1) {
-        const Cx<R> a = q0 + q_nx, b = q0 - q_nx;
-        const Cx<R> x0 = cfma(a, s0, cmul(b, s1));
-        const Cx<R> x1 = cfma(b, s0, cmul(a, s1));
+        Cx<R> x0 = w.s0, x1 = w.s1;
+        interface_pair(q0, q_nx, x0, x1);
         const R ax0 = abs2(x0);
         R Rv = abs2(x1) / ax0;
         R Tv = q_out.x / q0.x * ldexp_w(Ps * yscale / ax0, e4 + eP + yn - 2 * es);
@@ -121,9 +152,8 @@ __device__ __forceinline__ void eval_point(const StageA<R> *__restrict__ sa, con
     }
     if (POL & 2) {
         const Cx<R> g0 = cmul(q0, Cx<R>{A.in2x, A.in2y});
-        const Cx<R> a = g0 + g_nx, b = g0 - g_nx;
-        const Cx<R> x0 = cfma(a, p0, cmul(b, p1));
-        const Cx<R> x1 = cfma(b, p0, cmul(a, p1));
+        Cx<R> x0 = w.p0, x1 = w.p1;
+        interface_pair(g0, g_nx, x0, x1);
         const R ax0 = abs2(x0);
         R Rv = abs2(x1) / ax0;
         const R num = cmul(n2_out, conj(q_out)).x;
