@@ -45,6 +45,19 @@ template <typename R> __device__ __forceinline__ Cx<R> scale(R s, Cx<R> a) { ret
 // i * a
 template <typename R> __device__ __forceinline__ Cx<R> mul_i(Cx<R> a) { return {-a.y, a.x}; }
 
+// Interface j | j+1 applied to the amplitude pair (x0, x1) carried from the
+// right, in sum/difference form: with a = k + k', b = k - k' (k = q_j for s,
+// q_j / n_j^2 for p; k' the same for medium j+1),
+//   a x0 + b x1 = k (x0 + x1) + k' (x0 - x1),  b x0 + a x1 = k (x0 + x1) - k' (x0 - x1).
+template <typename R>
+__device__ __forceinline__ void interface_pair(Cx<R> k, Cx<R> kn, Cx<R> &x0, Cx<R> &x1)
+{
+    const Cx<R> sg = x0 + x1, df = x0 - x1;
+    const Cx<R> X = cmul(k, sg);
+    x0 = cfma(kn, df, X);
+    x1 = cfnma(kn, df, X);
+}
+
 // ---------------------------------------------------------------- precision-specific math
 __device__ __forceinline__ float rsqrt_w(float v) { return rsqrtf(v); }
 __device__ __forceinline__ double rsqrt_w(double v) { return rsqrt(v); }

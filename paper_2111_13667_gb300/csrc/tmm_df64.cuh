@@ -119,28 +119,6 @@ __device__ __forceinline__ dd dot2(dd a, dd b, dd c, dd d, float sgn)
     return fast_two_sum(s.hi, e);
 }
 
-// sum of four products a_k b_k (signs folded into the operands)
-__device__ __forceinline__ dd dot4(dd a0, dd b0, dd a1, dd b1, dd a2, dd b2, dd a3, dd b3)
-{
-    const float p0 = __fmul_rn(a0.hi, b0.hi), p1 = __fmul_rn(a1.hi, b1.hi);
-    const float p2 = __fmul_rn(a2.hi, b2.hi), p3 = __fmul_rn(a3.hi, b3.hi);
-    float e = __fadd_rn(__fadd_rn(fmaf(a0.hi, b0.hi, -p0), fmaf(a1.hi, b1.hi, -p1)),
-                        __fadd_rn(fmaf(a2.hi, b2.hi, -p2), fmaf(a3.hi, b3.hi, -p3)));
-    dd s01 = two_sum(p0, p1);
-    dd s23 = two_sum(p2, p3);
-    dd s = two_sum(s01.hi, s23.hi);
-    e = __fadd_rn(e, __fadd_rn(__fadd_rn(s01.lo, s23.lo), s.lo));
-    e = fmaf(a0.hi, b0.lo, e);
-    e = fmaf(a0.lo, b0.hi, e);
-    e = fmaf(a1.hi, b1.lo, e);
-    e = fmaf(a1.lo, b1.hi, e);
-    e = fmaf(a2.hi, b2.lo, e);
-    e = fmaf(a2.lo, b2.hi, e);
-    e = fmaf(a3.hi, b3.lo, e);
-    e = fmaf(a3.lo, b3.hi, e);
-    return fast_two_sum(s.hi, e);
-}
-
 // sqrt and 1/sqrt (Karp and Markstein: one correction of the float estimate)
 __device__ __forceinline__ void sqrt_rsqrt(dd a, dd *s, dd *r)
 {
@@ -170,13 +148,17 @@ __device__ __forceinline__ cdd cmul(cdd a, cdd b)
 {
     return cdd{dot2(a.x, b.x, a.y, b.y, -1.0f), dot2(a.x, b.y, a.y, b.x, 1.0f)};
 }
-// a u + b v
-__device__ __forceinline__ cdd cdot2(cdd a, cdd u, cdd b, cdd v)
-{
-    return cdd{dot4(a.x, u.x, neg(a.y), u.y, b.x, v.x, neg(b.y), v.y),
-               dot4(a.x, u.y, a.y, u.x, b.x, v.y, b.y, v.x)};
-}
 __device__ __forceinline__ dd cabs2(cdd a) { return dot2(a.x, a.x, a.y, a.y, 1.0f); }
+
+// (x0, x1) <- (a x0 + b x1, b x0 + a x1) with a = k + k', b = k - k', in
+// sum/difference form: X = k (x0 + x1), Z = k' (x0 - x1), (X + Z, X - Z).
+__device__ __forceinline__ void interface_pair(cdd k, cdd kn, cdd &x0, cdd &x1)
+{
+    const cdd X = cmul(k, cadd(x0, x1));
+    const cdd Z = cmul(kn, csub(x0, x1));
+    x0 = cadd(X, Z);
+    x1 = csub(X, Z);
+}
 
 }  // namespace df
 }  // namespace tmm

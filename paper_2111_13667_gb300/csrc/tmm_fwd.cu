@@ -37,19 +37,6 @@ constexpr int kMaxThreads = 512;
 // e^{Im delta}: diag(e^{-i Re delta}, e^{-2 Im delta} e^{i Re delta}).  R does
 // not see the factor; for T the product of all factors enters |t|^2 as
 // 2^{-2 K Y}, Y = sum of Im(delta) / (2 pi), K = 2 pi log2(e).
-// Interface j | j+1 applied to the amplitude pair (x0, x1) carried from the
-// right, in sum/difference form: with a = k + k', b = k - k' (k = q_j for s,
-// q_j / n_j^2 for p; k' the same for medium j+1),
-//   a x0 + b x1 = k (x0 + x1) + k' (x0 - x1),  b x0 + a x1 = k (x0 + x1) - k' (x0 - x1).
-template <typename R>
-__device__ __forceinline__ void interface_pair(Cx<R> k, Cx<R> kn, Cx<R> &x0, Cx<R> &x1)
-{
-    const Cx<R> sg = x0 + x1, df = x0 - x1;
-    const Cx<R> X = cmul(k, sg);
-    x0 = cfma(kn, df, X);
-    x1 = cfnma(kn, df, X);
-}
-
 // Running state of one point's right-to-left sweep.
 template <typename R> struct Sweep {
     Cx<R> q_nx, g_nx;        // q and q / n^2 of the medium to the right

@@ -186,19 +186,15 @@ __device__ __forceinline__ void eval_point_dd(const DStage *__restrict__ st, con
         const cdd emi{cs, df::neg(sn)};
         const cdd epi{df::mul(E2, cs), df::mul(E2, sn)};
         if (POL & 1) {
-            const cdd a = df::cadd(q, q_nx), b = df::csub(q, q_nx);
-            const cdd u0 = df::cdot2(a, s0, b, s1);
-            const cdd u1 = df::cdot2(b, s0, a, s1);
-            s0 = df::cmul(emi, u0);
-            s1 = df::cmul(epi, u1);
+            df::interface_pair(q, q_nx, s0, s1);
+            s0 = df::cmul(emi, s0);
+            s1 = df::cmul(epi, s1);
         }
         if (POL & 2) {
             const cdd g = df::cmul(q, ld_c(A.in2xh, A.in2xl, A.in2yh, A.in2yl));
-            const cdd a = df::cadd(g, g_nx), b = df::csub(g, g_nx);
-            const cdd u0 = df::cdot2(a, p0, b, p1);
-            const cdd u1 = df::cdot2(b, p0, a, p1);
-            p0 = df::cmul(emi, u0);
-            p1 = df::cmul(epi, u1);
+            df::interface_pair(g, g_nx, p0, p1);
+            p0 = df::cmul(emi, p0);
+            p1 = df::cmul(epi, p1);
             g_nx = g;
         }
         q_nx = q;
@@ -219,9 +215,8 @@ __device__ __forceinline__ void eval_point_dd(const DStage *__restrict__ st, con
     const dd ym = exp2_dd(df::mul(Y, dconst(-4.0 * kPi * 1.4426950408889634073599246810019)), e2, &yn);
     const double ys = df::to_double(ym);
     if (POL & 1) {
-        const cdd a = df::cadd(q0, q_nx), b = df::csub(q0, q_nx);
-        const cdd x0 = df::cdot2(a, s0, b, s1);
-        const cdd x1 = df::cdot2(b, s0, a, s1);
+        cdd x0 = s0, x1 = s1;
+        df::interface_pair(q0, q_nx, x0, x1);
         const dd ax0 = df::cabs2(x0);
         double Rv = df::to_double(df::div(df::cabs2(x1), ax0));
         double Tv = df::to_double(df::div(df::mul(q_out.x, Ps), df::mul(q0.x, ax0)));
@@ -232,9 +227,8 @@ __device__ __forceinline__ void eval_point_dd(const DStage *__restrict__ st, con
     }
     if (POL & 2) {
         const cdd g0 = df::cmul(q0, ld_c(A.in2xh, A.in2xl, A.in2yh, A.in2yl));
-        const cdd a = df::cadd(g0, g_nx), b = df::csub(g0, g_nx);
-        const cdd x0 = df::cdot2(a, p0, b, p1);
-        const cdd x1 = df::cdot2(b, p0, a, p1);
+        cdd x0 = p0, x1 = p1;
+        df::interface_pair(g0, g_nx, x0, x1);
         const dd ax0 = df::cabs2(x0);
         double Rv = df::to_double(df::div(df::cabs2(x1), ax0));
         // Re(n_out^2 conj(q_out)) / (n_0^2 q_0)

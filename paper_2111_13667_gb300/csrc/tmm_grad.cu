@@ -165,17 +165,15 @@ __global__ void __launch_bounds__(kGradThreads) tmm_grad_kernel(const tmm_proble
             const Cx<R> emi = {cs, -sn_}, epi = {E2 * cs, E2 * sn_};
             const bool rn = ((L - j) & 1) == 1;
             if (do_s) {
-                const Cx<R> A_ = m.q + nx.q, B_ = m.q - nx.q;
-                const Cx<R> u0 = cfma(A_, s0, cmul(B_, s1)), u1 = cfma(B_, s0, cmul(A_, s1));
-                s0 = cmul(emi, u0);
-                s1 = cmul(epi, u1);
+                interface_pair(m.q, nx.q, s0, s1);
+                s0 = cmul(emi, s0);
+                s1 = cmul(epi, s1);
                 if (rn) renorm_pair(s0, s1, es);
             }
             if (do_p) {
-                const Cx<R> A_ = m.ap + nx.ap, B_ = m.ap - nx.ap;
-                const Cx<R> u0 = cfma(A_, p0, cmul(B_, p1)), u1 = cfma(B_, p0, cmul(A_, p1));
-                p0 = cmul(emi, u0);
-                p1 = cmul(epi, u1);
+                interface_pair(m.ap, nx.ap, p0, p1);
+                p0 = cmul(emi, p0);
+                p1 = cmul(epi, p1);
                 if (rn) renorm_pair(p0, p1, ep);
             }
             X[j] = XState<R>{s0, s1, p0, p1, es, ep};
@@ -196,8 +194,8 @@ __global__ void __launch_bounds__(kGradThreads) tmm_grad_kernel(const tmm_proble
         {
             int pi = 0;
             if (do_s) {
-                const Cx<R> A_ = cur.q + nx.q, B_ = cur.q - nx.q;
-                const Cx<R> x0 = cfma(A_, s0, cmul(B_, s1)), x1 = cfma(B_, s0, cmul(A_, s1));
+                Cx<R> x0 = s0, x1 = s1;
+                interface_pair(cur.q, nx.q, x0, x1);
                 const R ia = R(1) / abs2(x0);
                 const R Rv = grazing ? R(1) : abs2(x1) * ia;
                 const R e = Rv - Rt[((long long)pi * p.n_theta + ac) * p.n_lambda + lc];
@@ -210,8 +208,8 @@ __global__ void __launch_bounds__(kGradThreads) tmm_grad_kernel(const tmm_proble
                 ++pi;
             }
             if (do_p) {
-                const Cx<R> A_ = cur.ap + nx.ap, B_ = cur.ap - nx.ap;
-                const Cx<R> x0 = cfma(A_, p0, cmul(B_, p1)), x1 = cfma(B_, p0, cmul(A_, p1));
+                Cx<R> x0 = p0, x1 = p1;
+                interface_pair(cur.ap, nx.ap, x0, x1);
                 const R ia = R(1) / abs2(x0);
                 const R Rv = grazing ? R(1) : abs2(x1) * ia;
                 const R e = Rv - Rt[((long long)pi * p.n_theta + ac) * p.n_lambda + lc];
@@ -269,9 +267,9 @@ __global__ void __launch_bounds__(kGradThreads) tmm_grad_kernel(const tmm_proble
                     dn += R(2) * cmul(cmul(v0 + v1, Xn.s0 + Xn.s1), cur.dq).x * sc_b;
                 }
                 if (j + 1 <= L) dn_carry += R(2) * cmul(cmul(v0 - v1, Xn.s0 - Xn.s1), nx.dq).x * sc_b;
-                const Cx<R> A_ = cur.q + nx.q, B_ = cur.q - nx.q;
-                ws0 = cfma(v0, A_, cmul(v1, B_));
-                ws1 = cfma(v0, B_, cmul(v1, A_));
+                // (ws0, ws1) <- (v0 a + v1 b, v0 b + v1 a), a, b = q_j +- q_{j+1}
+                ws0 = v0, ws1 = v1;
+                interface_pair(cur.q, nx.q, ws0, ws1);
                 if (rn) renorm_pair(ws0, ws1, ews);
             }
             if (do_p) {
@@ -285,9 +283,8 @@ __global__ void __launch_bounds__(kGradThreads) tmm_grad_kernel(const tmm_proble
                     dn += R(2) * cmul(cmul(v0 + v1, Xn.p0 + Xn.p1), cur.dap).x * sc_b;
                 }
                 if (j + 1 <= L) dn_carry += R(2) * cmul(cmul(v0 - v1, Xn.p0 - Xn.p1), nx.dap).x * sc_b;
-                const Cx<R> A_ = cur.ap + nx.ap, B_ = cur.ap - nx.ap;
-                wp0 = cfma(v0, A_, cmul(v1, B_));
-                wp1 = cfma(v0, B_, cmul(v1, A_));
+                wp0 = v0, wp1 = v1;
+                interface_pair(cur.ap, nx.ap, wp0, wp1);
                 if (rn) renorm_pair(wp0, wp1, ewp);
             }
             if (j >= 1) {
