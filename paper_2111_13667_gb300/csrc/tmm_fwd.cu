@@ -61,6 +61,11 @@ __device__ __forceinline__ void layer_step(const StageA<R> *__restrict__ sa, con
     R sn, cs;
     sincos_turn(yr - rint_w(yr), &sn, &cs);
     const R E2 = exp_m2_turn(yi);
+    // Both components turn, by conjugate factors: dropping the common phase
+    // e^{-i Re delta} (R and T do not see it) would leave the rounding of
+    // |(cs, sn)| on x1 alone, a spurious gain or loss per layer that high-Q
+    // guided modes under total internal reflection amplify (in FP32 emulation
+    // of a reflectivity map: |R - 1| from 7e-6 to 2e-3).
     const Cx<R> emi = {cs, -sn};            // e^{-i delta} / e^{Im delta}
     const Cx<R> epi = {E2 * cs, E2 * sn};   // e^{+i delta} / e^{Im delta}
     if (POL & 1) {
