@@ -89,15 +89,20 @@ __device__ __forceinline__ float sin_w(float v) { return sinf(v); }
 __device__ __forceinline__ double sin_w(double v) { return sin(v); }
 __device__ __forceinline__ void sincos_w(float v, float *s, float *c) { sincosf(v, s, c); }
 __device__ __forceinline__ void sincos_w(double v, double *s, double *c) { sincos(v, s, c); }
-// Layers between two rescalings of the running products: the per-layer growth
+// Layers between two rescalings of the amplitude pairs: the per-layer growth
 // is below 2^63 (|n| <= 32 and the Im(delta) <= 35 clamp), so FP32 can take
-// two layers and FP64 eight before the exponent range is at risk.
+// two layers and FP64 eight before the exponent range is at risk.  The scalar
+// product of |q_j|^2 (a factor in [2^-31, 2^11] per layer unless it is 0) is
+// rescaled every second interval.
 template <typename R> struct RenormEvery;
 template <> struct RenormEvery<float> { static constexpr int value = 2; };
 template <> struct RenormEvery<double> { static constexpr int value = 8; };
 template <typename R> __device__ __forceinline__ R eps_w();
 template <> __device__ __forceinline__ float eps_w<float>() { return 1.1920929e-7f; }
 template <> __device__ __forceinline__ double eps_w<double>() { return 2.220446049250313e-16; }
+template <typename R> __device__ __forceinline__ R min_normal();
+template <> __device__ __forceinline__ float min_normal<float>() { return 1.17549435e-38f; }
+template <> __device__ __forceinline__ double min_normal<double>() { return 2.2250738585072014e-308; }
 template <typename R> __device__ __forceinline__ R nan_w();
 template <> __device__ __forceinline__ float nan_w<float>() { return __int_as_float(0x7fc00000); }
 template <> __device__ __forceinline__ double nan_w<double>() { return __longlong_as_double(0x7ff8000000000000LL); }
@@ -136,22 +141,21 @@ template <typename R> __device__ __forceinline__ void renorm_pair(Cx<R> &x0, Cx<
 // returns |q|^2 = |z|.  z = 0 gives q = 0.
 template <typename R> __device__ __forceinline__ Cx<R> forward_root(Cx<R> z, R *absz_out)
 {
+    // Branch-free: the reciprocal roots take max(., smallest normal), which
+    // leaves every normal input unchanged and turns z = 0 into q = 0, |z| = 0
+    // (no 0 * inf); a NaN z still reaches q and |z| through u and o.
     const R hyp = fma(z.x, z.x, z.y * z.y);
-    Cx<R> q = {R(0), R(0)};
-    R absz = R(0);
-    if (!(hyp <= R(0))) {  // also taken for NaN, so a poisoned index stays NaN
-        const R rh = rsqrt_w(hyp);
-        absz = hyp * rh;
-        const R u = R(0.5) * (absz + fabs(z.x));
-        const R ru = rsqrt_w(u);
-        const R t = u * ru;             // sqrt(u)
-        const R o = R(0.5) * z.y * ru;  // Im z / (2 sqrt(u))
-        q = z.x >= R(0) ? Cx<R>{t, o} : Cx<R>{fabs(o), copysign(t, z.y)};
-        // principal root has Re >= 0; take the decaying one unless Im q is
-        // zero to rounding (|Im q| <= 100 eps |q|, compared squared)
-        const R tol = R(100) * eps_w<R>();
-        if (q.y < R(0) && q.y * q.y > tol * tol * absz) q = -q;
-    }
+    const R tiny = min_normal<R>();
+    const R absz = hyp * rsqrt_w(fmax(hyp, tiny));
+    const R u = R(0.5) * (absz + fabs(z.x));
+    const R ru = rsqrt_w(fmax(u, tiny));
+    const R t = u * ru;             // sqrt(u)
+    const R o = R(0.5) * z.y * ru;  // Im z / (2 sqrt(u))
+    Cx<R> q = z.x >= R(0) ? Cx<R>{t, o} : Cx<R>{fabs(o), copysign(t, z.y)};
+    // principal root has Re >= 0; take the decaying one unless Im q is zero to
+    // rounding (|Im q| <= 100 eps |q|, compared squared)
+    const R tol = R(100) * eps_w<R>();
+    if (q.y < R(0) && q.y * q.y > tol * tol * absz) q = -q;
     *absz_out = absz;
     return q;
 }

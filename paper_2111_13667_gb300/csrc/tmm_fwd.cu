@@ -107,8 +107,20 @@ __device__ __forceinline__ void eval_point(const StageA<R> *__restrict__ sa, con
     w.s0 = {R(1), R(0)}, w.s1 = {R(0), R(0)}, w.p0 = {R(1), R(0)}, w.p1 = {R(0), R(0)};
     int es = 0, ep = 0;
 
-    // groups of RN layers, each followed by a power-of-two rescale
+    // groups of RN layers, each followed by a power-of-two rescale of the
+    // pairs; the |q|^2 product every second group
     int j = L;
+    for (; j >= 2 * RN; j -= 2 * RN) {
+#pragma unroll
+        for (int k = 0; k < RN; ++k) layer_step<R, POL>(sa, sb, TL, tl, j - k, q0sq, yi_max, w);
+        if (POL & 1) renorm_pair(w.s0, w.s1, es);
+        if (POL & 2) renorm_pair(w.p0, w.p1, ep);
+#pragma unroll
+        for (int k = RN; k < 2 * RN; ++k) layer_step<R, POL>(sa, sb, TL, tl, j - k, q0sq, yi_max, w);
+        renorm_scalar(w.Ps, eP);
+        if (POL & 1) renorm_pair(w.s0, w.s1, es);
+        if (POL & 2) renorm_pair(w.p0, w.p1, ep);
+    }
     for (; j >= RN; j -= RN) {
 #pragma unroll
         for (int k = 0; k < RN; ++k) layer_step<R, POL>(sa, sb, TL, tl, j - k, q0sq, yi_max, w);
