@@ -29,19 +29,22 @@ namespace tmm {
 // Largest block of the forward kernels (threads); keeps 128 registers per thread.
 constexpr int kMaxThreads = 512;
 
-// One (lambda, theta) point of one stack, both polarisations as requested.
-// out = {R_s, T_s, R_p, T_p}.  Pp_m * 2^Pp_e = prod_{j=1..L+1} |1/n_j^2|^2 for
-// this wavelength (theta-independent, computed while staging).
+// One (lambda, theta) point of one stack, both polarisations as requested:
+// out = {R_s, T_s, R_p, T_p}.
 //
 // Each layer's phase matrix is applied divided by its real factor
 // e^{Im delta}: diag(e^{-i Re delta}, e^{-2 Im delta} e^{i Re delta}).  R does
 // not see the factor; for T the product of all factors enters |t|^2 as
-// 2^{-2 K Y}, Y = sum of Im(delta) / (2 pi), K = 2 pi log2(e).
+// 2^{-2 K Y}, Y = sum of Im(delta) / (2 pi), K = 2 pi log2(e).  The p
+// interfaces are kept unnormalised by 1/n_j^2 products; T_p takes back
+// prod_{j=1..L+1} |1/n_j^2|^2, accumulated along the sweep.
+
 // Running state of one point's right-to-left sweep.
 template <typename R> struct Sweep {
     Cx<R> q_nx, g_nx;        // q and q / n^2 of the medium to the right
     Cx<R> s0, s1, p0, p1;    // s and p amplitude pairs (scaled)
     R Ps, Y;                 // prod |q_j|^2 (scaled), sum of Im delta_j / (2 pi)
+    R Pp;                    // prod |1/n_j^2|^2 (scaled)
 };
 
 // Layer j (1..L): its interface with medium j+1, then its phase (Eq. 3).
@@ -74,6 +77,7 @@ __device__ __forceinline__ void layer_step(const StageA<R> *__restrict__ sa, con
         w.s1 = cmul(epi, w.s1);
     }
     if (POL & 2) {
+        w.Pp *= B.ain2;
         const Cx<R> g = cmul(q, Cx<R>{A.in2x, A.in2y});
         interface_pair(g, w.g_nx, w.p0, w.p1);
         w.p0 = cmul(emi, w.p0);
@@ -87,8 +91,7 @@ __device__ __forceinline__ void layer_step(const StageA<R> *__restrict__ sa, con
 // the vector (1, 0) of the exit medium, then r, t (Eqs. 5-6) and R, T.
 template <typename R, int POL>
 __device__ __forceinline__ void eval_point(const StageA<R> *__restrict__ sa, const StageB<R> *__restrict__ sb,
-                                           int TL, int tl, int L, R n0, R sin_theta, R cos_theta, R Pp_m,
-                                           int Pp_e, R out[4])
+                                           int TL, int tl, int L, R n0, R sin_theta, R cos_theta, R out[4])
 {
     constexpr int RN = RenormEvery<R>::value;
     const R beta = n0 * sin_theta;
@@ -104,6 +107,8 @@ __device__ __forceinline__ void eval_point(const StageA<R> *__restrict__ sa, con
     w.g_nx = cmul(w.q_nx, Cx<R>{A.in2x, A.in2y});
     w.Ps = R(1), w.Y = R(0);
     int eP = 0;
+    w.Pp = (POL & 2) ? sb[(L + 1) * TL + tl].ain2 : R(1);
+    int ePp = 0;
     w.s0 = {R(1), R(0)}, w.s1 = {R(0), R(0)}, w.p0 = {R(1), R(0)}, w.p1 = {R(0), R(0)};
     int es = 0, ep = 0;
 
@@ -118,6 +123,7 @@ __device__ __forceinline__ void eval_point(const StageA<R> *__restrict__ sa, con
 #pragma unroll
         for (int k = RN; k < 2 * RN; ++k) layer_step<R, POL>(sa, sb, TL, tl, j - k, q0sq, yi_max, w);
         renorm_scalar(w.Ps, eP);
+        if (POL & 2) renorm_scalar(w.Pp, ePp);
         if (POL & 1) renorm_pair(w.s0, w.s1, es);
         if (POL & 2) renorm_pair(w.p0, w.p1, ep);
     }
@@ -125,6 +131,7 @@ __device__ __forceinline__ void eval_point(const StageA<R> *__restrict__ sa, con
 #pragma unroll
         for (int k = 0; k < RN; ++k) layer_step<R, POL>(sa, sb, TL, tl, j - k, q0sq, yi_max, w);
         renorm_scalar(w.Ps, eP);
+        if (POL & 2) renorm_scalar(w.Pp, ePp);
         if (POL & 1) renorm_pair(w.s0, w.s1, es);
         if (POL & 2) renorm_pair(w.p0, w.p1, ep);
     }
@@ -162,7 +169,7 @@ __device__ __forceinline__ void eval_point(const StageA<R> *__restrict__ sa, con
         R Rv = abs2(x1) / ax0;
         const R num = cmul(n2_out, conj(q_out)).x;
         const R den = n0 * n0 * q0.x;
-        R Tv = num / den * ldexp_w(Ps * Pp_m * yscale / ax0, e4 + eP + Pp_e + yn - 2 * ep);
+        R Tv = num / den * ldexp_w(Ps * w.Pp * yscale / ax0, e4 + eP + ePp + yn - 2 * ep);
         if (grazing) { Rv = R(1); Tv = R(0); }
         out[2] = Rv;
         out[3] = Tv;
@@ -170,7 +177,7 @@ __device__ __forceinline__ void eval_point(const StageA<R> *__restrict__ sa, con
 }
 
 // Stage one work item and evaluate it.  Every thread of the block calls this;
-// it contains two barriers.
+// it contains one barrier.
 template <typename R, int POL, bool WITH_T>
 __device__ __forceinline__ void run_item(const tmm_problem &p, int s, int lt, int tt, int TL, int TT,
                                          unsigned char *smem, R *__restrict__ Rout, R *__restrict__ Tout)
@@ -178,26 +185,12 @@ __device__ __forceinline__ void run_item(const tmm_problem &p, int s, int lt, in
     StageA<R> *sa = reinterpret_cast<StageA<R> *>(smem);
     StageB<R> *sb = reinterpret_cast<StageB<R> *>(sa + (size_t)(p.L_max + 2) * TL);
     R *n0s = reinterpret_cast<R *>(sb + (size_t)(p.L_max + 2) * TL);
-    R *ppm = n0s + TL;
-    int *ppe = reinterpret_cast<int *>(ppm + TL);
 
     const int tid = threadIdx.y * TL + threadIdx.x;
     const int nthr = TL * TT;
     const int L = layers_of(p, s);
     const int l0 = lt * TL, t0 = tt * TT;
     if (L >= 0) fill_stage<R>(p, s, L, l0, TL, sa, sb, n0s, tid, nthr);
-    __syncthreads();
-    if ((POL & 2) && L >= 0 && tid < TL) {
-        // prod_{j=1..L+1} |1/n_j^2|^2 for this wavelength
-        R m = R(1);
-        int e = 0;
-        for (int j = 1; j <= L + 1; ++j) {
-            m *= sb[j * TL + tid].ain2;
-            renorm_scalar(m, e);
-        }
-        ppm[tid] = m;
-        ppe[tid] = e;
-    }
     __syncthreads();
 
     const int tl = threadIdx.x, l = l0 + tl, a = t0 + threadIdx.y;
@@ -206,8 +199,7 @@ __device__ __forceinline__ void run_item(const tmm_problem &p, int s, int lt, in
         if (L >= 0) {
             R sth, cth;
             sincos_w(((const R *)p.theta)[a], &sth, &cth);
-            eval_point<R, POL>(sa, sb, TL, tl, L, n0s[tl], sth, cth, (POL & 2) ? ppm[tl] : R(1),
-                               (POL & 2) ? ppe[tl] : 0, out);
+            eval_point<R, POL>(sa, sb, TL, tl, L, n0s[tl], sth, cth, out);
         } else {
             out[0] = out[1] = out[2] = out[3] = nan_w<R>();
         }
@@ -321,7 +313,7 @@ PersistentWs persistent_ws_layout(const tmm_problem *p)
 static size_t stage_bytes(const tmm_problem *p, int TL)
 {
     const size_t r = real_size(p->prec);
-    return (size_t)(p->L_max + 2) * TL * (6 * r) + (size_t)TL * (2 * r + sizeof(int));
+    return (size_t)(p->L_max + 2) * TL * (6 * r) + (size_t)TL * r;
 }
 
 tmm_status choose_tile(const tmm_problem *p, const tmm_launch_cfg *cfg, Tile *t)
