@@ -285,8 +285,8 @@ TMM_API tmm_status tmm_coh_batched_noalloc(const tmm_problem *p, const tmm_launc
  *   D[M][N] = sum_k A[M][k] B[N][k];  A, B device bf16, row-major, K a
  *   multiple of 8 and both base addresses 16-byte aligned.
  *   epilogue 0: out f32 [M][N] = D + bias        (bias device [N] or NULL)
- *            1: aux bf16 [M][N] = D + bias; out bf16 = GELU(aux), tanh form
- *               0.5 z (1 + tanh(sqrt(2/pi) (z + 0.044715 z^3)))
+ *            1: aux bf16 [M][N] = D + bias; out bf16 = GELU(aux), erf form
+ *               z Phi(z) = 0.5 z (1 + erf(z / sqrt 2))
  *            2: out bf16 = D * GELU'(aux)        (aux device bf16 [M][N], read)
  *            3: out f32 = clamp(D + bias, 0, 1)
  * Synchronises `stream` and reports TMM_ERR_TIMEOUT if a pipeline wait of the

@@ -1,9 +1,9 @@
 """Reference forward/backward of the surrogate MLP (plain torch on the CPU, fp64).
 
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).  The network is not in
-the paper; this restates its definition -- x = 2 (d - d_min)/(d_max - d_min) - 1
-zero-padded to 64 inputs, hidden layers z = W h + b, h' = GELU(z) in its tanh
-form 0.5 z (1 + tanh(sqrt(2/pi) (z + 0.044715 z^3))),
+the paper; this restates its definition -- x = (d - d_min)/(d_max - d_min) in
+[0, 1], zero-padded to 64 inputs, hidden layers z = W h + b, h' = GELU(z) in
+its erf form z Phi(z) = 0.5 z (1 + erf(z / sqrt 2)),
 linear head y = W h + b, loss = mean (y - t)^2 -- and differentiates it with
 autograd.  The GPU kernels store GEMM operands and activations in bf16; the
 reference rounds the network input and the weights the same way and keeps
@@ -20,7 +20,7 @@ def bf(t):
 
 
 def gelu(z):
-    return 0.5 * z * (1.0 + torch.tanh((2.0 / torch.pi) ** 0.5 * (z + 0.044715 * z ** 3)))
+    return 0.5 * z * (1.0 + torch.erf(z / 2.0 ** 0.5))
 
 
 def forward_backward(layers, d, target, d_min, d_max, kin=64):
@@ -29,7 +29,7 @@ def forward_backward(layers, d, target, d_min, d_max, kin=64):
     bf16 like the kernels' operands."""
     B, L = d.shape
     x = torch.zeros(B, kin, dtype=torch.float64)
-    x[:, :L] = 2.0 * (d.double() - d_min) / (d_max - d_min) - 1.0
+    x[:, :L] = (d.double() - d_min) / (d_max - d_min)
     h = bf(x)
     Ws = [bf(W.double()).requires_grad_(True) for W, _ in layers]
     bs = [b.double().requires_grad_(True) for _, b in layers]

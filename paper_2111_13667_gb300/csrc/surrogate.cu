@@ -86,7 +86,7 @@ __global__ void normalize_input(const float *d, int B, int L, float lo, float in
     if (i >= (long long)B * KIN) return;
     const int r = (int)(i / KIN), k = (int)(i % KIN);
     float x = 0.0f;
-    if (k < L) x = 2.0f * (d[(long long)r * L + k] - lo) * inv_span - 1.0f;
+    if (k < L) x = (d[(long long)r * L + k] - lo) * inv_span;  // in [0, 1]
     const __nv_bfloat16 v = __float2bfloat16(x);
     X[i] = v;
     if (XT) XT[(long long)k * B + r] = v;

@@ -188,43 +188,14 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float v[32])
     tmem_ld16(taddr + 16, v + 16);
 }
 
-// GELU, tanh form: gelu(z) = 0.5 z (1 + tanh u), u = sqrt(2/pi) (z + 0.044715 z^3),
-// evaluated as z * sigma(2u) (0.5 (1 + tanh u) = sigma(2u)) with one ex2.approx
-// and one rcp.approx.  kG0, kG1: -2 sqrt(2/pi) log2(e) and its product with
-// 0.044715, so that sigma(2u) = 1 / (1 + 2^(z (kG0 + kG1 z^2))).
-constexpr float kG0 = -2.3022082f;
-constexpr float kG1 = -0.10294324f;
-constexpr float kW0 = 1.5957691f;   // d(2u)/dz = kW0 + kW1 z^2: 2 sqrt(2/pi), and its product with 3 * 0.044715
-constexpr float kW1 = 0.21406445f;
-
-__device__ __forceinline__ float ex2_approx(float x)
-{
-    float y;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-__device__ __forceinline__ float rcp_approx(float x)
-{
-    float y;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-__device__ __forceinline__ float gelu_sigma(float z)
-{
-    const float z2 = z * z;
-    return rcp_approx(1.0f + ex2_approx(z * fmaf(kG1, z2, kG0)));
-}
-
-__device__ __forceinline__ float gelu(float z) { return z * gelu_sigma(z); }
-
-// d/dz [z sigma(2u)] = s + z s (1 - s) d(2u)/dz
+// GELU, erf form: gelu(z) = z Phi(z) = 0.5 z (1 + erf(z / sqrt 2)), with CUDA's
+// erff; its derivative Phi(z) + z phi(z), phi(z) = exp(-z^2 / 2) / sqrt(2 pi).
+__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
 __device__ __forceinline__ float gelu_grad(float z)
 {
-    const float s = gelu_sigma(z);
-    const float w = fmaf(kW1, z * z, kW0);
-    return fmaf(z * s * (1.0f - s), w, s);
+    const float cdf = 0.5f * (1.0f + erff(z * 0.70710678118654752f));
+    const float pdf = 0.39894228040143268f * __expf(-0.5f * z * z);
+    return fmaf(z, pdf, cdf);
 }
 
 // Two floats to one word of two bf16 (round to nearest even), a in the low half.
