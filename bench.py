@@ -29,11 +29,17 @@ sys.path.insert(0, ROOT)
 
 L2_BYTES = 129 * 1024 * 1024
 FLUSH_BYTES = 512 * 1024 * 1024
-# Algorithmic work per (eval, interface): real flops of the vector sweep with
-# both polarisations sharing Snell's law and the phase, FMA = 2, transcendental
-# instructions not counted.  Breakdown per (lambda, theta, interface): shared
-# 21 (n^2 - beta^2, root, phase, |q|^2 product), s 44, p 51 -> 116 / 2 pols.
-FLOPS_PER_EVAL_INTERFACE = 58.0
+# Algorithmic work per (eval, interface), the standard count of the
+# vector-sweep method with per-interface Fresnel coefficients (real flops,
+# FMA = 2): Snell (complex div + sqrt, shared by the pols, half charged),
+# Fresnel (complex reciprocal + ~4 complex products), phase (complex exp,
+# shared) and the vector update (6 complex products + 2 adds): 88 per layer,
+# about 2.2 kflop per eval over the 25 interfaces of the dispersive workload.
+FLOPS_PER_EVAL_INTERFACE = 88.0
+# What this kernel executes per (eval, interface) with unnormalised interfaces
+# (no complex division), both polarisations sharing root and phase: shared 21
+# (n^2 - beta^2, root, phase, |q|^2 product), s 44, p 51 -> 116 / 2 pols.
+EXECUTED_FLOPS_PER_EVAL_INTERFACE = 58.0
 # Unit-count peaks (152 SMs, max SM clock 2070 MHz): FP32 128 FMA lanes / SM;
 # FP64 from the nominal 1.25 TFLOP/s of the part.
 SMS = 152
@@ -214,7 +220,10 @@ def gpu_arm(args):
                               "unit": "TFLOP/s", "frac": achieved / peak, "traffic": stored_traffic(key),
                               "kernel": key,
                               "work": f"{FLOPS_PER_EVAL_INTERFACE:g} flop per eval-interface x {interfaces} "
-                                      f"interfaces x {evals} evals"}}
+                                      f"interfaces x {evals} evals (standard count of the vector-sweep "
+                                      f"method)",
+                              "executed_frac": achieved / peak * EXECUTED_FLOPS_PER_EVAL_INTERFACE
+                              / FLOPS_PER_EVAL_INTERFACE}}
         try:
             f, pms = abi.tmm_probe_fma_rate(abi.TMM_F64 if prec == "f64" else abi.TMM_F32)
             entry["roofline"]["probe_peak"] = f / 1e12
@@ -449,11 +458,11 @@ def cpu_threads():
         return os.cpu_count() or 1
 
 
-def oracle_sample_rate(w, target_s, max_stacks=None):
+def oracle_sample_rate(w, target_s, max_stacks=None, threads=None):
     """Time the oracle (as it stands) on the first k stacks of w, k chosen so
     the run takes roughly target_s seconds.  Returns (evals/s, k, seconds)."""
     import oracle
-    threads = cpu_threads()
+    threads = threads or cpu_threads()
 
     def run(k):
         sub = w.subset(np.arange(k))
@@ -472,10 +481,17 @@ def oracle_sample_rate(w, target_s, max_stacks=None):
 
 
 def cpu_baseline(w, args):
+    from paper_2111_13667_gb300 import workloads as W
     rate, k, t = oracle_sample_rate(w, args.cpu_seconds)
+    rate1, k1, t1 = oracle_sample_rate(w, min(3.0, args.cpu_seconds / 4), threads=1)
+    w0 = W.plain_fp64()
+    rate0, k0, t0 = oracle_sample_rate(w0, 1e9, max_stacks=w0.S)  # every stack
     return {"value": rate, "unit": "evals/s", "cores": cpu_threads(), "kind": "oracle",
             "sample": f"first {k} of {w.S} stacks, all {w.n_lambda} lambda x {w.n_theta} theta x 2 pol, "
-                      f"FP64 C oracle, {t:.1f} s"}
+                      f"FP64 C oracle, {t:.1f} s",
+            "single_core": {"value": rate1, "sample": f"first {k1} stacks on 1 thread, {t1:.1f} s"},
+            "plain_fp64_full": {"value": rate0, "evals": k0 * w0.n_lambda * w0.n_theta * w0.n_pol,
+                                "seconds": t0, "cores": cpu_threads()}}
 
 
 def reference_arm(args):

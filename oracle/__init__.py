@@ -15,6 +15,10 @@ Two independent formulations live here:
 * ``admittance.py`` is the textbook characteristic-matrix (tilted admittance)
   form of the same thin-film problem, written independently in numpy; it is
   used only to pin the first formulation on random stacks.
+
+Beside them: ``mlp.py`` (the surrogate network's reference forward/backward)
+and ``optimize.py`` (many-start Adam over the thicknesses on top of
+``merit_grad``, the merit-driven optimisation of the paper's Fig. 1c).
 """
 from __future__ import annotations
 
