@@ -180,6 +180,41 @@ TMM_API tmm_status tmm_coh_grad(const tmm_problem *p, const void *R_target, void
                         void *dm_dd, void *dm_dn, void *workspace, size_t workspace_bytes,
                         void *stream);
 
+/*
+ * Merit-driven thickness optimisation: the use case of the paper's Fig. 1c
+ * (a merit of R over wavelength and angle minimised over the thicknesses with
+ * the gradients of Sec. 4).  The paper fixes no optimiser; this runs Adam
+ * (Kingma and Ba, 2015) on every stack at once, each stack an independent
+ * start.  One step evaluates merit and dm/dd exactly as tmm_coh_grad does at
+ * the current thicknesses, then updates every finite layer j < L_s:
+ *   m = beta1 m + (1 - beta1) g,   v = beta2 v + (1 - beta2) g^2,
+ *   d = clip(d - lr (m / (1 - beta1^t)) / (sqrt(v / (1 - beta2^t)) + eps),
+ *            d_min, d_max)
+ * with t = step0 + 1, step0 + 2, ...  Layers past L_s keep their values.
+ *   p           the problem; p->d (device [S][L_max], the real type of
+ *               p->prec) is READ AND OVERWRITTEN in place.  prec TMM_F64 or
+ *               TMM_F32 (TMM_F64X: TMM_ERR_UNSUPPORTED).
+ *   R_target    device [P][n_theta][n_lambda], as for tmm_coh_grad
+ *   cfg         host: lr > 0, 0 <= beta1, beta2 < 1, eps > 0,
+ *               d_min <= d_max (nm); step0 >= 0 = steps already taken with
+ *               this workspace (0 resets the moment estimates m, v)
+ *   steps       >= 0 Adam steps in this call
+ *   merit_hist  device [steps][S] or NULL: merit at the start of each step
+ *   workspace   device, >= tmm_optimize_workspace_size bytes, 256-byte
+ *               aligned, caller-owned; keeps m and v between calls
+ * Asynchronous on `stream`; argument errors are returned before any launch.
+ */
+typedef struct {
+    double lr, beta1, beta2, eps, d_min, d_max;
+    int32_t step0;
+    int32_t reserved; /* 0 */
+} tmm_adam_cfg;
+
+TMM_API tmm_status tmm_optimize_workspace_size(const tmm_problem *p, size_t *bytes);
+TMM_API tmm_status tmm_optimize_adam(const tmm_problem *p, const void *R_target, const tmm_adam_cfg *cfg,
+                                     int32_t steps, void *merit_hist, void *workspace,
+                                     size_t workspace_bytes, void *stream);
+
 /* Short description of a status code (static string). */
 TMM_API const char *tmm_status_string(int status);
 

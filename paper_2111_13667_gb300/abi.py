@@ -34,7 +34,7 @@ TMM_POL_P = 2
 EXPORTED = ("tmm_coh_batched", "tmm_coh_batched_ex", "tmm_workspace_size", "tmm_workspace_status",
             "tmm_coh_grad", "tmm_status_string", "tmm_last_cuda_error", "tmm_version",
             "tmm_probe_fma_rate", "tmm_gemm_bf16", "tmm_gemm_bf16_t", "tmm_coh_batched_noalloc",
-            "tmm_surrogate_create", "tmm_surrogate_destroy", "tmm_surrogate_outputs", "tmm_surrogate_parameters",
+            "tmm_optimize_workspace_size", "tmm_optimize_adam", "tmm_surrogate_create", "tmm_surrogate_destroy", "tmm_surrogate_outputs", "tmm_surrogate_parameters",
             "tmm_surrogate_generate", "tmm_surrogate_train_step", "tmm_surrogate_infer", "tmm_surrogate_layer",
             "tmm_surrogate_status", "tmm_surrogate_save", "tmm_surrogate_load")
 
@@ -56,6 +56,13 @@ class TmmLaunchCfg(ctypes.Structure):
     _fields_ = [("tile_lambda", ctypes.c_int32), ("tile_theta", ctypes.c_int32),
                 ("persistent", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
                 ("max_items_per_block", ctypes.c_int32)]
+
+
+class TmmAdamCfg(ctypes.Structure):
+    """Mirror of ``tmm_adam_cfg``."""
+    _fields_ = [("lr", ctypes.c_double), ("beta1", ctypes.c_double), ("beta2", ctypes.c_double),
+                ("eps", ctypes.c_double), ("d_min", ctypes.c_double), ("d_max", ctypes.c_double),
+                ("step0", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class TmmSurrogateDesc(ctypes.Structure):
@@ -116,6 +123,8 @@ def load(path: Optional[str] = None):
         lib.tmm_gemm_bf16_t.argtypes = [vp, vp, vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                         vp, vp, vp, ctypes.c_int32, vp]
         lib.tmm_coh_batched_noalloc.argtypes = [P, C, vp, vp, vp]
+        lib.tmm_optimize_workspace_size.argtypes = [P, ctypes.POINTER(sz)]
+        lib.tmm_optimize_adam.argtypes = [P, vp, ctypes.POINTER(TmmAdamCfg), ctypes.c_int32, vp, vp, sz, vp]
         i32, f32 = ctypes.c_int32, ctypes.c_float
         lib.tmm_surrogate_create.argtypes = [ctypes.POINTER(TmmSurrogateDesc), ctypes.POINTER(vp)]
         lib.tmm_surrogate_destroy.argtypes = [vp]
@@ -137,7 +146,8 @@ def load(path: Optional[str] = None):
             getattr(lib, name).restype = ctypes.c_int
         for name in ("tmm_coh_batched", "tmm_coh_batched_ex", "tmm_workspace_size",
                      "tmm_workspace_status", "tmm_coh_grad", "tmm_probe_fma_rate", "tmm_gemm_bf16",
-                     "tmm_gemm_bf16_t", "tmm_coh_batched_noalloc"):
+                     "tmm_gemm_bf16_t", "tmm_coh_batched_noalloc", "tmm_optimize_workspace_size",
+                     "tmm_optimize_adam"):
             getattr(lib, name).restype = ctypes.c_int
         if path is None:
             _lib = lib
@@ -321,6 +331,33 @@ def tmm_gemm_bf16_t(A: torch.Tensor, B: torch.Tensor, bias: Optional[torch.Tenso
     N = B.shape[0]
     _check("tmm_gemm_bf16_t", load().tmm_gemm_bf16_t(_ptr(A), _ptr(B), _ptr(bias), M, N, K, epilogue, _ptr(out),
                                                      _ptr(aux), _ptr(outT), int(outT.stride(0)), _stream(stream)))
+
+
+def adam_cfg(lr, beta1=0.9, beta2=0.999, eps=1e-8, d_min=0.0, d_max=1e30, step0=0) -> TmmAdamCfg:
+    return TmmAdamCfg(float(lr), float(beta1), float(beta2), float(eps), float(d_min), float(d_max), int(step0), 0)
+
+
+def tmm_optimize_workspace_size(prob: DeviceProblem) -> int:
+    s = prob.struct()
+    n = ctypes.c_size_t(0)
+    _check("tmm_optimize_workspace_size", load().tmm_optimize_workspace_size(ctypes.byref(s), ctypes.byref(n)))
+    return n.value
+
+
+def tmm_optimize_adam(prob: DeviceProblem, R_target: torch.Tensor, cfg: TmmAdamCfg, steps: int,
+                      merit_hist: Optional[torch.Tensor] = None, workspace: Optional[torch.Tensor] = None,
+                      stream=None) -> Optional[torch.Tensor]:
+    """``steps`` Adam steps on prob.d (updated in place).  Returns the
+    workspace (holding the moment estimates) for a later call with
+    cfg.step0 = steps taken so far."""
+    if workspace is None:
+        workspace = alloc_workspace(tmm_optimize_workspace_size(prob), device=prob.d.device)
+    nbytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
+    s = prob.struct()
+    _check("tmm_optimize_adam", load().tmm_optimize_adam(ctypes.byref(s), _ptr(R_target), ctypes.byref(cfg),
+                                                         int(steps), _ptr(merit_hist), _ptr(workspace), nbytes,
+                                                         _stream(stream)))
+    return workspace
 
 
 def tmm_version() -> int:

@@ -43,7 +43,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_struct_layout_matches_header(tmp_path, lib):
-    from paper_2111_13667_gb300.abi import TmmLaunchCfg, TmmProblem
+    from paper_2111_13667_gb300.abi import TmmAdamCfg, TmmLaunchCfg, TmmProblem
     src = tmp_path / "layout.c"
     src.write_text("""
 #include <stdio.h>
@@ -53,6 +53,7 @@ int main(void) {
   printf("%zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(tmm_problem), offsetof(tmm_problem, n_direct),
          offsetof(tmm_problem, mat_table), offsetof(tmm_problem, n_materials), offsetof(tmm_problem, d),
          offsetof(tmm_problem, lambda), sizeof(tmm_launch_cfg), offsetof(tmm_launch_cfg, max_items_per_block));
+  printf("%zu %zu %zu\\n", sizeof(tmm_adam_cfg), offsetof(tmm_adam_cfg, d_max), offsetof(tmm_adam_cfg, step0));
   return 0;
 }
 """)
@@ -61,7 +62,8 @@ int main(void) {
     got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
     want = [ctypes.sizeof(TmmProblem), TmmProblem.n_direct.offset, TmmProblem.mat_table.offset,
             TmmProblem.n_materials.offset, TmmProblem.d.offset, TmmProblem.lambda_.offset,
-            ctypes.sizeof(TmmLaunchCfg), TmmLaunchCfg.max_items_per_block.offset]
+            ctypes.sizeof(TmmLaunchCfg), TmmLaunchCfg.max_items_per_block.offset,
+            ctypes.sizeof(TmmAdamCfg), TmmAdamCfg.d_max.offset, TmmAdamCfg.step0.offset]
     assert got == want
 
 
