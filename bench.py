@@ -267,6 +267,8 @@ def gpu_arm(args):
             out["ragged"] = bench_ragged(args, torch, abi, W, flush, world, max_over_ranks)
         if "adjoint" in sections:
             out["adjoint"] = bench_adjoint(args, torch, abi, W, flush, world, max_over_ranks)
+        if "optimize" in sections:
+            out["optimize"] = bench_optimize(args, torch, abi, W, flush, world, max_over_ranks)
         if "paper" in sections:
             out["paper_shapes"] = bench_paper_shapes(args, torch, abi, W, flush)
         if "surrogate" in sections and not args.skip_surrogate:
@@ -286,7 +288,7 @@ def gpu_arm(args):
         "roofline": head["roofline"], "clocks": head.get("clocks"), "e2e": head.get("e2e"),
         "gpu_launches": args.steps,
     }
-    for k in ("f64", "f64x", "ragged", "adjoint", "paper_shapes", "surrogate"):
+    for k in ("f64", "f64x", "ragged", "adjoint", "optimize", "paper_shapes", "surrogate"):
         if k in out:
             line[k] = out[k]
     line["cpu_baseline"] = cpu_baseline(w, args) if (rank == 0 and world == 1 and not args.skip_cpu) else None
@@ -354,6 +356,38 @@ def bench_adjoint(args, torch, abi, W, flush, world, max_over_ranks):
         ms = max_over_ranks(sum(t) / len(t))
         res[prec] = {"value": w.evals * world / (ms * 1e-3), "ms_per_step": ms, "steps": steps}
     return res
+
+
+def bench_optimize(args, torch, abi, W, flush, world, max_over_ranks):
+    """Merit-driven thickness optimisation (the paper's Fig. 1c use case):
+    many-start Adam over d on the adjoint workload (4096 starts x 40 layers,
+    band-stop target), FP32; one step = merit + gradient + update."""
+    w = W.adjoint()
+    prob = abi.to_device(w, "f32")
+    Rt = torch.as_tensor(w.R_target).to(device=prob.d.device, dtype=prob.real_dtype).contiguous()
+    ws = abi.alloc_workspace(abi.tmm_optimize_workspace_size(prob), device=prob.d.device)
+    n_steps = 20
+    hist = torch.empty(n_steps, w.S, dtype=prob.real_dtype, device=prob.d.device)
+    state = {"done": 0}
+
+    def run():
+        cfg = abi.adam_cfg(2.0, d_min=5.0, d_max=400.0, step0=state["done"])
+        abi.tmm_optimize_adam(prob, Rt, cfg, n_steps, merit_hist=hist, workspace=ws)
+        state["done"] += n_steps
+
+    t = time_steps(run, 3, 3, torch, flush)
+    ms = max_over_ranks(sum(t) / len(t)) / n_steps
+    # a fresh run from the seeded starts for the merit trajectory
+    prob2 = abi.to_device(w, "f32")
+    hist2 = torch.empty(100, w.S, dtype=prob.real_dtype, device=prob.d.device)
+    abi.tmm_optimize_adam(prob2, Rt, abi.adam_cfg(2.0, d_min=5.0, d_max=400.0), 100, merit_hist=hist2, workspace=ws)
+    torch.cuda.synchronize()
+    h = hist2.double().cpu().numpy()
+    return {"workload": w.name + ", Adam lr 2 nm, d in [5, 400] nm", "dtype": "f32",
+            "ms_per_adam_step": ms, "adam_steps_per_s": 1e3 / ms,
+            "stack_steps_per_s": w.S * world * 1e3 / ms, "evals_per_s": w.evals * world / (ms * 1e-3),
+            "merit_mean_step0": float(h[0].mean()), "merit_mean_step99": float(h[-1].mean()),
+            "merit_best_step99": float(h[-1].min()), "steps_timed": 3 * n_steps}
 
 
 def bench_surrogate(args, torch, abi, W, flush, world, max_over_ranks):
@@ -537,8 +571,8 @@ def main():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-extras", action="store_true", help="headline only (no ragged / adjoint lines)")
     ap.add_argument("--skip-surrogate", action="store_true")
-    ap.add_argument("--sections", default="ragged,adjoint,paper,surrogate",
-                    help="extra sections after the headline (comma list of ragged, adjoint, paper, surrogate)")
+    ap.add_argument("--sections", default="ragged,adjoint,optimize,paper,surrogate",
+                    help="extra sections after the headline (comma list of ragged, adjoint, optimize, paper, surrogate)")
     ap.add_argument("--sur-train", type=int, default=2_000_000, help="training spectra (GPU-generated)")
     ap.add_argument("--sur-steps", type=int, default=2000, help="training steps of 8192 spectra")
     ap.add_argument("--stacks", type=int, default=0, help="shrink the workload (profiling runs only)")
