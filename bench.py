@@ -449,15 +449,21 @@ def bench_surrogate(args, torch, abi, W, flush, world, max_over_ranks):
 def bench_paper_shapes(args, torch, abi, W, flush):
     """The paper's own timing workloads, for context (its numbers are CPU
     times on unstated hardware): the speed-up run (10 stacks, 21 media, 100
-    lambda x 20 theta, s; TMM-Fast 0.168 s) and the dataset example (1e6
+    lambda x 20 theta, s; TMM-Fast 0.168 s), the dataset example (1e6
     stacks x 10 layers, 100 lambda, normal incidence, s; ~40 min for a
-    similar 9-layer 10-angle set on 8 cores)."""
+    similar 9-layer 10-angle set on 8 cores) and the Fig. 2 reflectivity map
+    (1 stack, 300 x 300, unpolarised)."""
     res = {}
-    for name, w, paper in (("speedup_x1", W.speedup_x1(), "TMM-Fast 0.168 +- 0.002 s, original TMM 17.5 s (CPU)"),
-                           ("dataset_x2", W.dataset_x2(), "about 40 min for 1e6 9-layer stacks x 100 lambda x 10 theta on 8 cores (Dask)")):
+    for name, w, paper, pols in (
+            ("speedup_x1", W.speedup_x1(), "TMM-Fast 0.168 +- 0.002 s, original TMM 17.5 s (CPU)", None),
+            ("dataset_x2", W.dataset_x2(), "about 40 min for 1e6 9-layer stacks x 100 lambda x 10 theta on 8 cores (Dask)",
+             None),
+            ("map_x3_unpolarised", W.map_x3(), "Fig. 2 map, s and p averaged (no time given)", "u")):
         ent = {"evals": w.evals, "paper": paper}
+        if pols:
+            ent["output"] = "one plane of (R_s + R_p) / 2 and (T_s + T_p) / 2 (pol_mask 7)"
         for prec in ("f64", "f64x", "f32"):
-            prob = abi.to_device(w, prec)
+            prob = abi.to_device(w, prec, pols=pols)
             R, T = prob.empty_out(), prob.empty_out()
             t = time_steps(lambda: abi.tmm_coh_batched(prob, R, T), 5, 3, torch, flush)
             ms = sum(t) / len(t)

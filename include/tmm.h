@@ -69,9 +69,13 @@ typedef enum {
  */
 typedef enum { TMM_F64 = 0, TMM_F32 = 1, TMM_F64X = 2 } tmm_prec;
 
-/* Polarisation bits of tmm_problem.pol_mask; outputs store s before p. */
+/* Polarisation bits of tmm_problem.pol_mask; outputs store s before p.
+ * TMM_POL_AVG, only together with both TMM_POL_S and TMM_POL_P (pol_mask 7),
+ * writes one plane holding (R_s + R_p) / 2 and (T_s + T_p) / 2: unpolarised
+ * light, as the paper averages s and p for its reflectivity map (Fig. 2). */
 #define TMM_POL_S 1u
 #define TMM_POL_P 2u
+#define TMM_POL_AVG 4u
 
 /*
  * One batched problem: S stacks, each with up to L_max finite layers,
@@ -132,7 +136,8 @@ typedef struct {
 
 /*
  * R and T for every (pol, stack, theta, lambda) (Sec. 2, Eqs. 1-6).
- *   R  device [P][S][n_theta][n_lambda], P = number of bits in pol_mask
+ *   R  device [P][S][n_theta][n_lambda], P = number of polarisation bits in
+ *      pol_mask (s, p), or 1 with TMM_POL_AVG
  *   T  same layout, or NULL to skip it
  * Equivalent to tmm_coh_batched_ex with the default launch shape and no
  * workspace.

@@ -30,6 +30,7 @@ TMM_F32 = 1
 TMM_F64X = 2
 TMM_POL_S = 1
 TMM_POL_P = 2
+TMM_POL_AVG = 4
 
 EXPORTED = ("tmm_coh_batched", "tmm_coh_batched_ex", "tmm_workspace_size", "tmm_workspace_status",
             "tmm_coh_grad", "tmm_status_string", "tmm_last_cuda_error", "tmm_version",
@@ -212,7 +213,8 @@ class DeviceProblem:
 
     @property
     def n_pol(self):
-        return bin(self.pol_mask).count("1")
+        """Output planes: one per polarisation, or one for the s/p average."""
+        return 1 if self.pol_mask & TMM_POL_AVG else bin(self.pol_mask & 3).count("1")
 
     def struct(self) -> TmmProblem:
         p = TmmProblem()
@@ -237,6 +239,9 @@ class DeviceProblem:
 
 
 def pol_mask_of(pols: str) -> int:
+    """"s", "p", "sp", or "u" (unpolarised: the mean of s and p, one plane)."""
+    if pols == "u":
+        return TMM_POL_S | TMM_POL_P | TMM_POL_AVG
     return (TMM_POL_S if "s" in pols else 0) | (TMM_POL_P if "p" in pols else 0)
 
 

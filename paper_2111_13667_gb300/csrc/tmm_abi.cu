@@ -59,7 +59,8 @@ tmm_status validate_problem(const tmm_problem *p)
 {
     if (!p) return TMM_ERR_INVALID_ARG;
     if (p->S < 0 || p->L_max < 0 || p->n_lambda < 0 || p->n_theta < 0) return TMM_ERR_INVALID_ARG;
-    if (p->pol_mask == 0 || (p->pol_mask & ~3u)) return TMM_ERR_INVALID_ARG;
+    if (p->pol_mask == 0 || p->pol_mask > 7u) return TMM_ERR_INVALID_ARG;
+    if ((p->pol_mask & TMM_POL_AVG) && (p->pol_mask & 3u) != 3u) return TMM_ERR_INVALID_ARG;
     if (p->prec != TMM_F64 && p->prec != TMM_F32 && p->prec != TMM_F64X) return TMM_ERR_INVALID_ARG;
     if (p->n_direct_per_lambda != 0 && p->n_direct_per_lambda != 1) return TMM_ERR_INVALID_ARG;
     // an empty batch reads no array, so its pointers are not checked
@@ -133,7 +134,7 @@ tmm_status tmm_coh_grad(const tmm_problem *p, const void *R_target, void *merit,
     if (p->S == 0) return TMM_OK;
     if (p->n_lambda == 0 || p->n_theta == 0) return TMM_ERR_INVALID_ARG;
     if (!R_target || !merit || (p->L_max > 0 && !dm_dd)) return TMM_ERR_INVALID_ARG;
-    if (p->prec == TMM_F64X) return TMM_ERR_UNSUPPORTED;
+    if (p->prec == TMM_F64X || (p->pol_mask & TMM_POL_AVG)) return TMM_ERR_UNSUPPORTED;
     return launch_grad(p, R_target, merit, dm_dd, dm_dn, workspace, workspace_bytes,
                        static_cast<cudaStream_t>(stream));
 }

@@ -206,12 +206,15 @@ __device__ __forceinline__ void run_item(const tmm_problem &p, int s, int lt, in
         const long long plane = (long long)p.S * p.n_theta * p.n_lambda;
         const long long o = ((long long)s * p.n_theta + a) * p.n_lambda + l;
         int pi = 0;
-        if (POL & 1) {
+        if (POL & 4) {  // unpolarised: the mean of s and p in one plane
+            Rout[o] = R(0.5) * (out[0] + out[2]);
+            if (WITH_T) Tout[o] = R(0.5) * (out[1] + out[3]);
+        } else if (POL & 1) {
             Rout[o] = out[0];
             if (WITH_T) Tout[o] = out[1];
             ++pi;
         }
-        if (POL & 2) {
+        if ((POL & 2) && !(POL & 4)) {
             Rout[pi * plane + o] = out[2];
             if (WITH_T) Tout[pi * plane + o] = out[3];
         }
@@ -446,6 +449,7 @@ static tmm_status launch_prec(const tmm_problem *p, const tmm_launch_cfg *cfg, c
     case 1: return wt ? launch_typed<R, 1, true>(p, cfg, t, ws, Ro, To, st) : launch_typed<R, 1, false>(p, cfg, t, ws, Ro, To, st);
     case 2: return wt ? launch_typed<R, 2, true>(p, cfg, t, ws, Ro, To, st) : launch_typed<R, 2, false>(p, cfg, t, ws, Ro, To, st);
     case 3: return wt ? launch_typed<R, 3, true>(p, cfg, t, ws, Ro, To, st) : launch_typed<R, 3, false>(p, cfg, t, ws, Ro, To, st);
+    case 7: return wt ? launch_typed<R, 7, true>(p, cfg, t, ws, Ro, To, st) : launch_typed<R, 7, false>(p, cfg, t, ws, Ro, To, st);
     default: return TMM_ERR_INVALID_ARG;
     }
 }

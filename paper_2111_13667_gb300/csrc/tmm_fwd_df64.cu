@@ -323,12 +323,15 @@ __global__ void __launch_bounds__(kDfMaxThreads) tmm_fwd_df64_kernel(const tmm_p
         const long long plane = (long long)p.S * p.n_theta * p.n_lambda;
         const long long o = ((long long)s * p.n_theta + a) * p.n_lambda + l;
         int pi = 0;
-        if (POL & 1) {
+        if (POL & 4) {  // unpolarised: the mean of s and p in one plane
+            Rout[o] = 0.5 * (out[0] + out[2]);
+            if (WITH_T) Tout[o] = 0.5 * (out[1] + out[3]);
+        } else if (POL & 1) {
             Rout[o] = out[0];
             if (WITH_T) Tout[o] = out[1];
             ++pi;
         }
-        if (POL & 2) {
+        if ((POL & 2) && !(POL & 4)) {
             Rout[pi * plane + o] = out[2];
             if (WITH_T) Tout[pi * plane + o] = out[3];
         }
@@ -413,6 +416,8 @@ tmm_status launch_forward_df64(const tmm_problem *p, const tmm_launch_cfg *cfg, 
                       : launch_df_typed<2, false>(p, TL, TT, n_lt, n_tt, n_items, smem, Ro, To, st);
     case 3: return wt ? launch_df_typed<3, true>(p, TL, TT, n_lt, n_tt, n_items, smem, Ro, To, st)
                       : launch_df_typed<3, false>(p, TL, TT, n_lt, n_tt, n_items, smem, Ro, To, st);
+    case 7: return wt ? launch_df_typed<7, true>(p, TL, TT, n_lt, n_tt, n_items, smem, Ro, To, st)
+                      : launch_df_typed<7, false>(p, TL, TT, n_lt, n_tt, n_items, smem, Ro, To, st);
     default: return TMM_ERR_INVALID_ARG;
     }
 }

@@ -79,7 +79,8 @@ def _problem(**kw):
 
 
 @pytest.mark.parametrize("bad", [
-    dict(S=-1), dict(L_max=-2), dict(n_lambda=-1), dict(pol_mask=0), dict(pol_mask=4), dict(prec=7),
+    dict(S=-1), dict(L_max=-2), dict(n_lambda=-1), dict(pol_mask=0), dict(pol_mask=4), dict(pol_mask=5),
+    dict(pol_mask=6), dict(pol_mask=8), dict(prec=7),
     dict(mat_table=0x5000),                       # both index sources
     dict(n_direct=None),                          # neither index source
     dict(n_direct_per_lambda=2),
@@ -107,6 +108,31 @@ def test_host_rejects_missing_outputs_and_bad_cfg(lib):
                                   None, None) == abi.TMM_ERR_INVALID_ARG
     assert lib.tmm_coh_grad(ctypes.byref(p), None, None, None, None, None, 0, None) == abi.TMM_ERR_INVALID_ARG
     assert lib.tmm_workspace_status(None, None) == abi.TMM_ERR_INVALID_ARG
+
+
+def test_optimiser_and_average_mode_argument_checks(lib):
+    from paper_2111_13667_gb300 import abi
+    fake = ctypes.c_void_p(0x7000)
+    p = _problem()
+    bad = [abi.adam_cfg(0.0), abi.adam_cfg(1.0, beta1=1.0), abi.adam_cfg(1.0, beta2=-0.1),
+           abi.adam_cfg(1.0, eps=0.0), abi.adam_cfg(1.0, d_min=2.0, d_max=1.0), abi.adam_cfg(1.0, step0=-1)]
+    for cfg in bad:
+        assert lib.tmm_optimize_adam(ctypes.byref(p), fake, ctypes.byref(cfg), 1, None, fake, 1 << 20,
+                                     None) == abi.TMM_ERR_INVALID_ARG
+    cfg = abi.adam_cfg(1.0)
+    assert lib.tmm_optimize_adam(ctypes.byref(p), fake, None, 1, None, fake, 1 << 20, None) == abi.TMM_ERR_INVALID_ARG
+    assert lib.tmm_optimize_adam(ctypes.byref(p), fake, ctypes.byref(cfg), -1, None, fake, 1 << 20,
+                                 None) == abi.TMM_ERR_INVALID_ARG
+    px = _problem(prec=abi.TMM_F64X)
+    assert lib.tmm_optimize_adam(ctypes.byref(px), fake, ctypes.byref(cfg), 1, None, fake, 1 << 20,
+                                 None) == abi.TMM_ERR_UNSUPPORTED
+    # the s/p average (pol_mask 7) is a forward output mode; merit and gradients refuse it
+    pa = _problem(pol_mask=7)
+    assert lib.tmm_coh_grad(ctypes.byref(pa), fake, fake, fake, None, None, 0, None) == abi.TMM_ERR_UNSUPPORTED
+    assert lib.tmm_optimize_adam(ctypes.byref(pa), fake, ctypes.byref(cfg), 1, None, fake, 1 << 20,
+                                 None) == abi.TMM_ERR_UNSUPPORTED
+    n = ctypes.c_size_t(0)
+    assert lib.tmm_workspace_size(ctypes.byref(pa), None, ctypes.byref(n)) == abi.TMM_OK
 
 
 def test_empty_problem_is_a_noop(lib):

@@ -78,6 +78,24 @@ def test_single_polarisation_and_R_only(prec, pols):
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32", "f64x"])
+def test_unpolarised_average_mode(prec):
+    # pol_mask 7: one plane of (R_s + R_p) / 2 and (T_s + T_p) / 2, as the paper
+    # averages s and p for unpolarised light
+    w = W.dispersive(seed=15, S=11, L=9, n_lambda=70, n_theta=9)
+    Ro, To = oracle_RT(w)
+    R, T = gpu_RT(w, prec, pols="u")
+    assert R.shape == (1,) + Ro.shape[1:]
+    assert_close(R[0], 0.5 * (Ro[0] + Ro[1]), TOL[prec], "R unpolarised")
+    assert_close(T[0], 0.5 * (To[0] + To[1]), TOL[prec], "T unpolarised")
+    # the same as averaging the two planes of the s+p launch, to rounding of a
+    # separately compiled kernel
+    Rsp, Tsp = gpu_RT(w, prec)
+    same = 1e-12 if prec != "f32" else 2e-6
+    assert_close(R[0], 0.5 * (Rsp[0] + Rsp[1]), same, "R vs s+p launch")
+    assert_close(T[0], 0.5 * (Tsp[0] + Tsp[1]), same, "T vs s+p launch")
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32", "f64x"])
 def test_total_internal_reflection_and_grazing(prec):
     # injection index 2 into air, interior indices up to 4.6, theta up to
     # exactly 90 deg (the paper's reflectivity-map shape)
