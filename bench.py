@@ -319,6 +319,15 @@ def bench_ragged(args, torch, abi, W, flush, world, max_over_ranks):
     status = run.status()
     ms_g = max_over_ranks(sum(tg) / len(tg))
     del run
+    # the environment reward -sum |R_target - R| of every stack on the same
+    # launch configuration, no R, T written (band-stop target, s and p)
+    Rt = torch.as_tensor(W.band_stop_target(w.lam, 2, w.n_theta), device=prob.d.device,
+                         dtype=prob.real_dtype).contiguous()
+    reward = torch.empty(w.S, dtype=prob.real_dtype, device=prob.d.device)
+    rws = abi.alloc_workspace(abi.tmm_reward_workspace_size(prob, cfg), device=prob.d.device)
+    tr = time_steps(lambda: abi.tmm_coh_reward(prob, Rt, reward, cfg=cfg, workspace=rws), steps, 3, torch, flush)
+    ms_r = max_over_ranks(sum(tr) / len(tr))
+    del rws
     padded = abi.DeviceProblem(prob.prec, prob.pol_mask, prob.theta, prob.lam, prob.d, table=prob.table,
                                mat_idx=prob.mat_idx)
     R = padded.empty_out()
@@ -333,6 +342,8 @@ def bench_ragged(args, torch, abi, W, flush, world, max_over_ranks):
                                  "tile_lambda": cfg.tile_lambda, "tile_theta": cfg.tile_theta,
                                  "persistent": cfg.persistent, "status": status},
             "padded_L120": {"value": evals / (ms_p * 1e-3), "ms_per_step": ms_p},
+            "reward": {"value": evals / (ms_r * 1e-3), "ms_per_step": ms_r, "stacks_per_s": w.S * world / (ms_r * 1e-3),
+                       "what": "-sum |R_target - R| per stack, persistent launch, no R/T output"},
             "speedup_vs_padded": ms_p / ms_g, "autotune_s": tune_s, "candidates": len(report),
             "layer_steps_ratio": w.layer_steps() / (w.evals * (w.L_max + 1)), "steps": steps}
 

@@ -186,6 +186,26 @@ TMM_API tmm_status tmm_coh_grad(const tmm_problem *p, const void *R_target, void
                         void *stream);
 
 /*
+ * Batched reward of the paper's reinforcement-learning environment (Sec. 5):
+ *   reward[s] = - sum over (plane, theta, lambda) of |R_target - R|
+ * for every stack, with the planes of pol_mask (s, p, or their mean for
+ * TMM_POL_AVG).  The forward kernels run in a reduction mode: no R or T is
+ * written; each (stack, tile) work item leaves its partial sum in the
+ * workspace and a second pass adds them in a fixed order (deterministic).
+ * Ragged stacks (L_per_stack) and the persistent longest-first launch work
+ * as for tmm_coh_batched_ex (cfg->max_items_per_block must be 0 here).
+ *   R_target   device [P][n_theta][n_lambda]
+ *   reward     device [S], the real type of p->prec (F32 or F64; F64X:
+ *              TMM_ERR_UNSUPPORTED)
+ *   workspace  device, >= tmm_reward_workspace_size(p, cfg) bytes, 256-byte
+ *              aligned, caller-owned scratch
+ * Asynchronous on `stream`.
+ */
+TMM_API tmm_status tmm_reward_workspace_size(const tmm_problem *p, const tmm_launch_cfg *cfg, size_t *bytes);
+TMM_API tmm_status tmm_coh_reward(const tmm_problem *p, const tmm_launch_cfg *cfg, const void *R_target,
+                                  void *reward, void *workspace, size_t workspace_bytes, void *stream);
+
+/*
  * Merit-driven thickness optimisation: the use case of the paper's Fig. 1c
  * (a merit of R over wavelength and angle minimised over the thicknesses with
  * the gradients of Sec. 4).  The paper fixes no optimiser; this runs Adam

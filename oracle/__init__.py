@@ -189,6 +189,17 @@ def merit(pols, n, d, theta, lam, R_target, L_per_stack=None, nthreads=None, lib
     return np.mean(e * e, axis=(0, 2, 3))
 
 
+def reward(pols, n, d, theta, lam, R_target, L_per_stack=None, average=False, nthreads=None, lib=None):
+    """Reward of the paper's RL environment (Sec. 5) for every stack:
+    -sum over (plane, theta, lambda) of |R_target - R|.  The planes are the
+    polarisations in ``pols`` (s before p), or their mean with ``average``;
+    ``R_target`` is [planes][N_theta][N_lambda]."""
+    R, _ = coh_tmm_pols(pols, n, d, theta, lam, L_per_stack=L_per_stack, nthreads=nthreads, lib=lib)
+    if average:
+        R = R.mean(axis=0, keepdims=True)
+    return -np.sum(np.abs(np.asarray(R_target)[:, None, :, :] - R), axis=(0, 2, 3))
+
+
 def gather_index(table, mat_idx):
     """Index assembly: n[s, j, lambda] = table[mat_idx[s, j], lambda] (plain indexing)."""
     return np.asarray(table, dtype=np.complex128)[np.asarray(mat_idx)]

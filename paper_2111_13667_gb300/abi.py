@@ -35,7 +35,8 @@ TMM_POL_AVG = 4
 EXPORTED = ("tmm_coh_batched", "tmm_coh_batched_ex", "tmm_workspace_size", "tmm_workspace_status",
             "tmm_coh_grad", "tmm_status_string", "tmm_last_cuda_error", "tmm_version",
             "tmm_probe_fma_rate", "tmm_gemm_bf16", "tmm_gemm_bf16_t", "tmm_coh_batched_noalloc",
-            "tmm_optimize_workspace_size", "tmm_optimize_adam", "tmm_surrogate_create", "tmm_surrogate_destroy", "tmm_surrogate_outputs", "tmm_surrogate_parameters",
+            "tmm_optimize_workspace_size", "tmm_optimize_adam", "tmm_reward_workspace_size", "tmm_coh_reward",
+            "tmm_surrogate_create", "tmm_surrogate_destroy", "tmm_surrogate_outputs", "tmm_surrogate_parameters",
             "tmm_surrogate_generate", "tmm_surrogate_train_step", "tmm_surrogate_infer", "tmm_surrogate_layer",
             "tmm_surrogate_status", "tmm_surrogate_save", "tmm_surrogate_load")
 
@@ -125,6 +126,8 @@ def load(path: Optional[str] = None):
                                         vp, vp, vp, ctypes.c_int32, vp]
         lib.tmm_coh_batched_noalloc.argtypes = [P, C, vp, vp, vp]
         lib.tmm_optimize_workspace_size.argtypes = [P, ctypes.POINTER(sz)]
+        lib.tmm_reward_workspace_size.argtypes = [P, C, ctypes.POINTER(sz)]
+        lib.tmm_coh_reward.argtypes = [P, C, vp, vp, vp, sz, vp]
         lib.tmm_optimize_adam.argtypes = [P, vp, ctypes.POINTER(TmmAdamCfg), ctypes.c_int32, vp, vp, sz, vp]
         i32, f32 = ctypes.c_int32, ctypes.c_float
         lib.tmm_surrogate_create.argtypes = [ctypes.POINTER(TmmSurrogateDesc), ctypes.POINTER(vp)]
@@ -148,7 +151,7 @@ def load(path: Optional[str] = None):
         for name in ("tmm_coh_batched", "tmm_coh_batched_ex", "tmm_workspace_size",
                      "tmm_workspace_status", "tmm_coh_grad", "tmm_probe_fma_rate", "tmm_gemm_bf16",
                      "tmm_gemm_bf16_t", "tmm_coh_batched_noalloc", "tmm_optimize_workspace_size",
-                     "tmm_optimize_adam"):
+                     "tmm_optimize_adam", "tmm_reward_workspace_size", "tmm_coh_reward"):
             getattr(lib, name).restype = ctypes.c_int
         if path is None:
             _lib = lib
@@ -336,6 +339,28 @@ def tmm_gemm_bf16_t(A: torch.Tensor, B: torch.Tensor, bias: Optional[torch.Tenso
     N = B.shape[0]
     _check("tmm_gemm_bf16_t", load().tmm_gemm_bf16_t(_ptr(A), _ptr(B), _ptr(bias), M, N, K, epilogue, _ptr(out),
                                                      _ptr(aux), _ptr(outT), int(outT.stride(0)), _stream(stream)))
+
+
+def tmm_reward_workspace_size(prob: DeviceProblem, cfg: Optional[TmmLaunchCfg] = None) -> int:
+    s = prob.struct()
+    n = ctypes.c_size_t(0)
+    _check("tmm_reward_workspace_size", load().tmm_reward_workspace_size(ctypes.byref(s),
+                                                                         ctypes.byref(cfg) if cfg else None,
+                                                                         ctypes.byref(n)))
+    return n.value
+
+
+def tmm_coh_reward(prob: DeviceProblem, R_target: torch.Tensor, reward: torch.Tensor,
+                   cfg: Optional[TmmLaunchCfg] = None, workspace: Optional[torch.Tensor] = None, stream=None):
+    """reward[s] = -sum |R_target - R| over the output planes, theta, lambda."""
+    if workspace is None:
+        workspace = alloc_workspace(tmm_reward_workspace_size(prob, cfg), device=prob.d.device)
+    nbytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
+    s = prob.struct()
+    _check("tmm_coh_reward", load().tmm_coh_reward(ctypes.byref(s), ctypes.byref(cfg) if cfg else None,
+                                                   _ptr(R_target), _ptr(reward), _ptr(workspace), nbytes,
+                                                   _stream(stream)))
+    return workspace
 
 
 def adam_cfg(lr, beta1=0.9, beta2=0.999, eps=1e-8, d_min=0.0, d_max=1e30, step0=0) -> TmmAdamCfg:

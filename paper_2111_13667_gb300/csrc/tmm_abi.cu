@@ -139,6 +139,38 @@ tmm_status tmm_coh_grad(const tmm_problem *p, const void *R_target, void *merit,
                        static_cast<cudaStream_t>(stream));
 }
 
+tmm_status tmm_reward_workspace_size(const tmm_problem *p, const tmm_launch_cfg *cfg, size_t *bytes)
+{
+    if (!bytes) return TMM_ERR_INVALID_ARG;
+    tmm_status s = validate_problem(p);
+    if (s != TMM_OK) return s;
+    if (p->prec == TMM_F64X) return TMM_ERR_UNSUPPORTED;
+    if (p->S == 0 || p->n_lambda == 0 || p->n_theta == 0) {
+        *bytes = 0;
+        return TMM_OK;
+    }
+    Tile t;
+    size_t part = 0;
+    return reward_layout(p, cfg, &t, &part, bytes);
+}
+
+tmm_status tmm_coh_reward(const tmm_problem *p, const tmm_launch_cfg *cfg, const void *R_target, void *reward,
+                          void *workspace, size_t workspace_bytes, void *stream)
+{
+    tmm_status s = validate_problem(p);
+    if (s != TMM_OK) return s;
+    if (p->prec == TMM_F64X) return TMM_ERR_UNSUPPORTED;
+    if (cfg && (cfg->persistent < 0 || cfg->persistent > 1 || cfg->max_items_per_block != 0))
+        return TMM_ERR_INVALID_ARG;
+    if (p->S == 0) return TMM_OK;
+    if (!R_target || !reward) return TMM_ERR_INVALID_ARG;
+    if (p->n_lambda == 0 || p->n_theta == 0) {  // an empty sum
+        cudaError_t e = cudaMemsetAsync(reward, 0, (size_t)p->S * real_size(p->prec), static_cast<cudaStream_t>(stream));
+        return e == cudaSuccess ? TMM_OK : cuda_fail(e);
+    }
+    return launch_reward(p, cfg, R_target, reward, workspace, workspace_bytes, static_cast<cudaStream_t>(stream));
+}
+
 const char *tmm_status_string(int status)
 {
     switch (status) {

@@ -176,11 +176,21 @@ __device__ __forceinline__ void eval_point(const StageA<R> *__restrict__ sa, con
     }
 }
 
+// Reduction mode (tmm_coh_reward): with Rt set, a work item writes no R, T
+// but the sum over its points and output planes of |R_target - R| into
+// partial[s * n_tiles + tile] (fixed-order block reduction).
+template <typename R> struct Reduce {
+    const R *Rt;  // [P][n_theta][n_lambda] or null (plain R, T output)
+    R *partial;   // [S][n_tiles]
+    int n_tiles;
+};
+
 // Stage one work item and evaluate it.  Every thread of the block calls this;
-// it contains one barrier.
-template <typename R, int POL, bool WITH_T>
-__device__ __forceinline__ void run_item(const tmm_problem &p, int s, int lt, int tt, int TL, int TT,
-                                         unsigned char *smem, R *__restrict__ Rout, R *__restrict__ Tout)
+// it contains one barrier (more in reduction mode).
+template <typename R, int POL, bool WITH_T, bool RED>
+__device__ __forceinline__ void run_item(const tmm_problem &p, int s, int lt, int tt, int n_tt, int TL, int TT,
+                                         unsigned char *smem, R *__restrict__ Rout, R *__restrict__ Tout,
+                                         const Reduce<R> &red)
 {
     StageA<R> *sa = reinterpret_cast<StageA<R> *>(smem);
     StageB<R> *sb = reinterpret_cast<StageB<R> *>(sa + (size_t)(p.L_max + 2) * TL);
@@ -194,6 +204,7 @@ __device__ __forceinline__ void run_item(const tmm_problem &p, int s, int lt, in
     __syncthreads();
 
     const int tl = threadIdx.x, l = l0 + tl, a = t0 + threadIdx.y;
+    R contrib = R(0);
     if (l < p.n_lambda && a < p.n_theta) {
         R out[4];
         if (L >= 0) {
@@ -203,44 +214,70 @@ __device__ __forceinline__ void run_item(const tmm_problem &p, int s, int lt, in
         } else {
             out[0] = out[1] = out[2] = out[3] = nan_w<R>();
         }
-        const long long plane = (long long)p.S * p.n_theta * p.n_lambda;
-        const long long o = ((long long)s * p.n_theta + a) * p.n_lambda + l;
-        int pi = 0;
-        if (POL & 4) {  // unpolarised: the mean of s and p in one plane
-            Rout[o] = R(0.5) * (out[0] + out[2]);
-            if (WITH_T) Tout[o] = R(0.5) * (out[1] + out[3]);
-        } else if (POL & 1) {
-            Rout[o] = out[0];
-            if (WITH_T) Tout[o] = out[1];
-            ++pi;
+        if (RED) {
+            const long long tplane = (long long)p.n_theta * p.n_lambda, ot = (long long)a * p.n_lambda + l;
+            if (POL & 4) {
+                contrib = fabs(red.Rt[ot] - R(0.5) * (out[0] + out[2]));
+            } else {
+                int pi = 0;
+                if (POL & 1) contrib += fabs(red.Rt[ot] - out[0]), ++pi;
+                if (POL & 2) contrib += fabs(red.Rt[pi * tplane + ot] - out[2]);
+            }
+        } else {
+            const long long plane = (long long)p.S * p.n_theta * p.n_lambda;
+            const long long o = ((long long)s * p.n_theta + a) * p.n_lambda + l;
+            int pi = 0;
+            if (POL & 4) {  // unpolarised: the mean of s and p in one plane
+                Rout[o] = R(0.5) * (out[0] + out[2]);
+                if (WITH_T) Tout[o] = R(0.5) * (out[1] + out[3]);
+            } else if (POL & 1) {
+                Rout[o] = out[0];
+                if (WITH_T) Tout[o] = out[1];
+                ++pi;
+            }
+            if ((POL & 2) && !(POL & 4)) {
+                Rout[pi * plane + o] = out[2];
+                if (WITH_T) Tout[pi * plane + o] = out[3];
+            }
         }
-        if ((POL & 2) && !(POL & 4)) {
-            Rout[pi * plane + o] = out[2];
-            if (WITH_T) Tout[pi * plane + o] = out[3];
+    }
+    if (RED) {
+        // fixed-order tree sum over the block (the stage is no longer read)
+        __syncthreads();
+        R *buf = reinterpret_cast<R *>(smem);
+        buf[tid] = contrib;
+        __syncthreads();
+        int half = 1;
+        while (half < nthr) half <<= 1;
+        for (half >>= 1; half > 0; half >>= 1) {
+            if (tid < half && tid + half < nthr) buf[tid] += buf[tid + half];
+            __syncthreads();
         }
+        if (tid == 0) red.partial[(long long)s * red.n_tiles + lt * n_tt + tt] = buf[0];
     }
     __syncthreads();
 }
 
-template <typename R, int POL, bool WITH_T>
+template <typename R, int POL, bool WITH_T, bool RED>
 __global__ void __launch_bounds__(kMaxThreads) tmm_fwd_kernel(const tmm_problem p, int TL, int TT, int n_lt, int n_tt,
-                                                       R *__restrict__ Rout, R *__restrict__ Tout)
+                                                       R *__restrict__ Rout, R *__restrict__ Tout, const Reduce<R> red)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const long long item = blockIdx.x;
     const int per_stack = n_lt * n_tt;
     const int s = (int)(item / per_stack);
     const int r = (int)(item - (long long)s * per_stack);
-    run_item<R, POL, WITH_T>(p, s, r / n_tt, r % n_tt, TL, TT, smem, Rout, Tout);
+    run_item<R, POL, WITH_T, RED>(p, s, r / n_tt, r % n_tt, n_tt, TL, TT, smem, Rout, Tout, red);
 }
 
 // Persistent variant: blocks pull work items from `counter`; item k belongs to
 // stack order[k / per_stack] (longest stacks first), tile k % per_stack.
-template <typename R, int POL, bool WITH_T>
+template <typename R, int POL, bool WITH_T, bool RED>
 __global__ void __launch_bounds__(kMaxThreads) tmm_fwd_persistent(const tmm_problem p, int TL, int TT, int n_lt, int n_tt,
                                                            const int *__restrict__ order, unsigned int *counter,
                                                            int *err, unsigned int n_items, int max_items,
-                                                           R *__restrict__ Rout, R *__restrict__ Tout)
+                                                           R *__restrict__ Rout, R *__restrict__ Tout,
+                                                           const Reduce<R> red)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ unsigned int item_sh;
@@ -258,7 +295,7 @@ __global__ void __launch_bounds__(kMaxThreads) tmm_fwd_persistent(const tmm_prob
         }
         const int k = (int)(item / per_stack);
         const int r = (int)(item - (unsigned int)k * per_stack);
-        run_item<R, POL, WITH_T>(p, order[k], r / n_tt, r % n_tt, TL, TT, smem, Rout, Tout);
+        run_item<R, POL, WITH_T, RED>(p, order[k], r / n_tt, r % n_tt, n_tt, TL, TT, smem, Rout, Tout, red);
     }
 }
 
@@ -385,22 +422,22 @@ static tmm_status prepare_kernel(Kernel k, int threads, size_t smem, bool need_o
     return TMM_OK;
 }
 
-template <typename R, int POL, bool WITH_T>
+template <typename R, int POL, bool WITH_T, bool RED>
 static tmm_status launch_typed(const tmm_problem *p, const tmm_launch_cfg *cfg, const Tile &t, void *ws,
-                               R *Rout, R *Tout, cudaStream_t st)
+                               R *Rout, R *Tout, const Reduce<R> &red, cudaStream_t st)
 {
     const dim3 block(t.TL, t.TT);
     const bool persistent = cfg && cfg->persistent;
     if (!persistent) {
-        auto k = tmm_fwd_kernel<R, POL, WITH_T>;
+        auto k = tmm_fwd_kernel<R, POL, WITH_T, RED>;
         tmm_status s = prepare_kernel(k, t.TL * t.TT, t.smem, false, nullptr);
         if (s != TMM_OK) return s;
         if (t.n_items > 0x7fffffffLL) return TMM_ERR_UNSUPPORTED;
         if (t.n_items == 0) return TMM_OK;
-        k<<<(unsigned)t.n_items, block, t.smem, st>>>(*p, t.TL, t.TT, t.n_lt, t.n_tt, Rout, Tout);
+        k<<<(unsigned)t.n_items, block, t.smem, st>>>(*p, t.TL, t.TT, t.n_lt, t.n_tt, Rout, Tout, red);
         return check_launch();
     }
-    auto k = tmm_fwd_persistent<R, POL, WITH_T>;
+    auto k = tmm_fwd_persistent<R, POL, WITH_T, RED>;
     int occ = 0;
     tmm_status s = prepare_kernel(k, t.TL * t.TT, t.smem, true, &occ);
     if (s != TMM_OK) return s;
@@ -434,22 +471,31 @@ static tmm_status launch_typed(const tmm_problem *p, const tmm_launch_cfg *cfg, 
     k<<<(unsigned)grid, block, t.smem, st>>>(*p, t.TL, t.TT, t.n_lt, t.n_tt, order,
                                              reinterpret_cast<unsigned int *>(base + w.counter),
                                              reinterpret_cast<int *>(base + w.err), (unsigned)t.n_items,
-                                             cfg->max_items_per_block, Rout, Tout);
+                                             cfg->max_items_per_block, Rout, Tout, red);
     return check_launch();
 }
 
 template <typename R>
 static tmm_status launch_prec(const tmm_problem *p, const tmm_launch_cfg *cfg, const Tile &t, void *ws, void *R_,
-                              void *T_, cudaStream_t st)
+                              void *T_, const Reduce<R> &red, cudaStream_t st)
 {
     R *Ro = static_cast<R *>(R_);
     R *To = static_cast<R *>(T_);
+    if (red.Rt) {  // reduction mode: no R, T output
+        switch (p->pol_mask) {
+        case 1: return launch_typed<R, 1, false, true>(p, cfg, t, ws, Ro, To, red, st);
+        case 2: return launch_typed<R, 2, false, true>(p, cfg, t, ws, Ro, To, red, st);
+        case 3: return launch_typed<R, 3, false, true>(p, cfg, t, ws, Ro, To, red, st);
+        case 7: return launch_typed<R, 7, false, true>(p, cfg, t, ws, Ro, To, red, st);
+        default: return TMM_ERR_INVALID_ARG;
+        }
+    }
     const bool wt = To != nullptr;
     switch (p->pol_mask) {
-    case 1: return wt ? launch_typed<R, 1, true>(p, cfg, t, ws, Ro, To, st) : launch_typed<R, 1, false>(p, cfg, t, ws, Ro, To, st);
-    case 2: return wt ? launch_typed<R, 2, true>(p, cfg, t, ws, Ro, To, st) : launch_typed<R, 2, false>(p, cfg, t, ws, Ro, To, st);
-    case 3: return wt ? launch_typed<R, 3, true>(p, cfg, t, ws, Ro, To, st) : launch_typed<R, 3, false>(p, cfg, t, ws, Ro, To, st);
-    case 7: return wt ? launch_typed<R, 7, true>(p, cfg, t, ws, Ro, To, st) : launch_typed<R, 7, false>(p, cfg, t, ws, Ro, To, st);
+    case 1: return wt ? launch_typed<R, 1, true, false>(p, cfg, t, ws, Ro, To, red, st) : launch_typed<R, 1, false, false>(p, cfg, t, ws, Ro, To, red, st);
+    case 2: return wt ? launch_typed<R, 2, true, false>(p, cfg, t, ws, Ro, To, red, st) : launch_typed<R, 2, false, false>(p, cfg, t, ws, Ro, To, red, st);
+    case 3: return wt ? launch_typed<R, 3, true, false>(p, cfg, t, ws, Ro, To, red, st) : launch_typed<R, 3, false, false>(p, cfg, t, ws, Ro, To, red, st);
+    case 7: return wt ? launch_typed<R, 7, true, false>(p, cfg, t, ws, Ro, To, red, st) : launch_typed<R, 7, false, false>(p, cfg, t, ws, Ro, To, red, st);
     default: return TMM_ERR_INVALID_ARG;
     }
 }
@@ -466,8 +512,63 @@ tmm_status launch_forward(const tmm_problem *p, const tmm_launch_cfg *cfg, void 
         if (ws_bytes < persistent_ws_layout(p).total) return TMM_ERR_NOMEM;
         if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return TMM_ERR_INVALID_ARG;
     }
-    return p->prec == TMM_F64 ? launch_prec<double>(p, cfg, t, ws, R, T, st)
-                              : launch_prec<float>(p, cfg, t, ws, R, T, st);
+    return p->prec == TMM_F64 ? launch_prec<double>(p, cfg, t, ws, R, T, Reduce<double>{nullptr, nullptr, 0}, st)
+                              : launch_prec<float>(p, cfg, t, ws, R, T, Reduce<float>{nullptr, nullptr, 0}, st);
+}
+
+// ---------------------------------------------------------------- reward
+// reward[s] = -sum_k partial[s][k], k in tile order (deterministic).
+template <typename R>
+__global__ void reward_finalize(int S, int n_tiles, const R *__restrict__ partial, R *__restrict__ reward)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    R acc = R(0);
+    for (int k = 0; k < n_tiles; ++k) acc += partial[(long long)s * n_tiles + k];
+    reward[s] = -acc;
+}
+
+tmm_status reward_layout(const tmm_problem *p, const tmm_launch_cfg *cfg, Tile *t, size_t *partial_bytes,
+                         size_t *total)
+{
+    tmm_status s = choose_tile(p, cfg, t);
+    if (s != TMM_OK) return s;
+    // the block's tree sum reuses the stage memory: one real per thread
+    t->smem = std::max(t->smem, (size_t)t->TL * t->TT * real_size(p->prec));
+    DeviceInfo di;
+    s = device_info(&di);
+    if (s != TMM_OK) return s;
+    if (t->smem > (size_t)di.max_smem_optin) return TMM_ERR_UNSUPPORTED;
+    *partial_bytes = align_up((size_t)p->S * t->n_lt * t->n_tt * real_size(p->prec), 256);
+    *total = *partial_bytes + ((cfg && cfg->persistent) ? persistent_ws_layout(p).total : 0);
+    return TMM_OK;
+}
+
+tmm_status launch_reward(const tmm_problem *p, const tmm_launch_cfg *cfg, const void *R_target, void *reward,
+                         void *ws, size_t ws_bytes, cudaStream_t st)
+{
+    Tile t;
+    size_t part = 0, total = 0;
+    tmm_status s = reward_layout(p, cfg, &t, &part, &total);
+    if (s != TMM_OK) return s;
+    if (!ws || ws_bytes < total) return TMM_ERR_NOMEM;
+    if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return TMM_ERR_INVALID_ARG;
+    unsigned char *base = static_cast<unsigned char *>(ws);
+    const int n_tiles = t.n_lt * t.n_tt;
+    if (p->prec == TMM_F64) {
+        s = launch_prec<double>(p, cfg, t, base + part, nullptr, nullptr,
+                                Reduce<double>{static_cast<const double *>(R_target), reinterpret_cast<double *>(base), n_tiles}, st);
+        if (s != TMM_OK) return s;
+        reward_finalize<double><<<(p->S + 255) / 256, 256, 0, st>>>(p->S, n_tiles, reinterpret_cast<const double *>(base),
+                                                                   static_cast<double *>(reward));
+    } else {
+        s = launch_prec<float>(p, cfg, t, base + part, nullptr, nullptr,
+                               Reduce<float>{static_cast<const float *>(R_target), reinterpret_cast<float *>(base), n_tiles}, st);
+        if (s != TMM_OK) return s;
+        reward_finalize<float><<<(p->S + 255) / 256, 256, 0, st>>>(p->S, n_tiles, reinterpret_cast<const float *>(base),
+                                                                  static_cast<float *>(reward));
+    }
+    return check_launch();
 }
 
 }  // namespace tmm

@@ -41,6 +41,11 @@ PersistentWs persistent_ws_layout(const tmm_problem *p);
 
 tmm_status launch_forward(const tmm_problem *p, const tmm_launch_cfg *cfg, void *ws, size_t ws_bytes,
                           void *R, void *T, cudaStream_t st);
+// Per-stack reward -sum |R_target - R| (forward kernels in reduction mode).
+tmm_status reward_layout(const tmm_problem *p, const tmm_launch_cfg *cfg, Tile *t, size_t *partial_bytes,
+                         size_t *total);
+tmm_status launch_reward(const tmm_problem *p, const tmm_launch_cfg *cfg, const void *R_target, void *reward,
+                         void *ws, size_t ws_bytes, cudaStream_t st);
 tmm_status launch_forward_df64(const tmm_problem *p, const tmm_launch_cfg *cfg, void *R, void *T, cudaStream_t st);
 
 // Adjoint / merit.

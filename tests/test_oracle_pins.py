@@ -341,3 +341,25 @@ def test_rejects_bad_arguments():
         oracle.coh_tmm("s", n, np.zeros((1, 2)), [0.0], [500.0])
     with pytest.raises(ValueError):
         oracle.coh_tmm("s", n, d, [0.0], [500.0], L_per_stack=np.array([5], dtype=np.int32))
+
+
+def test_reward_closed_forms():
+    # air | glass at normal incidence: R = ((1 - 1.5) / 2.5)^2 = 0.04 at every
+    # lambda, so against a zero target the reward is -0.04 per (plane, lambda)
+    lam = np.linspace(400.0, 800.0, 7)
+    n = np.repeat(np.array([[1.0, 1.5]], dtype=np.complex128)[:, :, None], 7, axis=2)
+    th = np.array([0.0])
+    r = oracle.reward("sp", n, np.zeros((1, 0)), th, lam, np.zeros((2, 1, 7)))
+    assert abs(r[0] + 2 * 7 * 0.04) < 1e-14
+    r = oracle.reward("sp", n, np.zeros((1, 0)), th, lam, np.zeros((1, 1, 7)), average=True)
+    assert abs(r[0] + 7 * 0.04) < 1e-14
+    # a target of 1 (a perfect mirror wanted): -sum (1 - R)
+    r = oracle.reward("s", n, np.zeros((1, 0)), th, lam, np.ones((1, 1, 7)))
+    assert abs(r[0] + 7 * 0.96) < 1e-13
+    # the target equal to the stack's own R gives zero, any other target less
+    rng = np.random.default_rng(3)
+    nd = np.repeat(np.array([[1.0, 2.1, 1.4, 1.52]], dtype=np.complex128)[:, :, None], 7, axis=2)
+    d = np.array([[120.0, 80.0]])
+    R, _ = oracle.coh_tmm_pols("sp", nd, d, np.deg2rad([0.0, 40.0]), lam)
+    assert abs(oracle.reward("sp", nd, d, np.deg2rad([0.0, 40.0]), lam, R[:, 0])[0]) < 1e-15
+    assert oracle.reward("sp", nd, d, np.deg2rad([0.0, 40.0]), lam, rng.uniform(0, 1, R[:, 0].shape))[0] < 0
