@@ -16,9 +16,11 @@ Two independent formulations live here:
   form of the same thin-film problem, written independently in numpy; it is
   used only to pin the first formulation on random stacks.
 
-Beside them: ``mlp.py`` (the surrogate network's reference forward/backward)
-and ``optimize.py`` (many-start Adam over the thicknesses on top of
-``merit_grad``, the merit-driven optimisation of the paper's Fig. 1c).
+Beside them: ``mlp.py`` (the surrogate network's reference forward/backward),
+``optimize.py`` (many-start Adam over the thicknesses on top of
+``merit_grad``, the merit-driven optimisation of the paper's Fig. 1c) and
+``incoherent.py`` (thick incoherent layers combined by intensities between
+coherent blocks evaluated with ``coh_tmm``).
 """
 from __future__ import annotations
 
