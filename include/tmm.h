@@ -186,6 +186,25 @@ TMM_API tmm_status tmm_coh_grad(const tmm_problem *p, const void *R_target, void
                         void *stream);
 
 /*
+ * Stacks with incoherent (thick) layers.  The paper treats coherent stacks
+ * only; this extends tmm_coh_batched in the usual way: media 0 and L_s+1 and
+ * every finite layer flagged in `incoherent` are incoherent; the coherent
+ * blocks between consecutive incoherent media are evaluated as amplitude
+ * products (Eqs. 1-6) and combined through the incoherent layers by
+ * intensities (each block's R and T for light from either side).
+ *   incoherent  device uint8 [S][L_max], nonzero = incoherent layer; NULL =
+ *               none (the coherent result)
+ *   R, T        as tmm_coh_batched (T may be NULL); pol_mask 1, 2, 3 or 7
+ * Incoherent layers must be non-absorbing: a point whose wavelength gives an
+ * incoherent layer a complex index gets NaN.  The first incoherent layer in
+ * which the wave is evanescent (n_j <= n_0 sin theta) ends the stack: it is
+ * the exit medium for R and T = 0.  prec TMM_F64 or TMM_F32 (TMM_F64X:
+ * TMM_ERR_UNSUPPORTED).  Asynchronous on `stream`.
+ */
+TMM_API tmm_status tmm_inc_batched(const tmm_problem *p, const uint8_t *incoherent, void *R, void *T,
+                                   void *stream);
+
+/*
  * Batched reward of the paper's reinforcement-learning environment (Sec. 5):
  *   reward[s] = - sum over (plane, theta, lambda) of |R_target - R|
  * for every stack, with the planes of pol_mask (s, p, or their mean for

@@ -1,0 +1,104 @@
+"""GPU parity of stacks with incoherent layers (tmm_inc_batched) against the
+oracle's intensity combination of coherent blocks (``oracle/incoherent.py``).
+
+Tolerances as for the coherent path: FP64 within 1e-10, FP32 within 1e-4
+absolute in R and T."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import incoherent as inc
+from paper_2111_13667_gb300 import abi
+from paper_2111_13667_gb300 import workloads as W
+from tests.helpers import oracle_RT
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-10, "f32": 1e-4}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    abi.load()
+
+
+def random_inc_workload(seed, S=5, L=6, n_lambda=17, n_theta=5, L_per_stack=None):
+    """Coherent layers may absorb; flagged (incoherent) layers are real and thick."""
+    rng = np.random.default_rng(seed)
+    lam = np.linspace(450.0, 750.0, n_lambda)
+    flags = (rng.uniform(size=(S, L)) < 0.35).astype(np.uint8)
+    n = np.empty((S, L + 2, n_lambda), dtype=np.complex128)
+    n[:, 0] = 1.0
+    re = rng.uniform(1.3, 2.4, (S, L))
+    im = rng.uniform(0.0, 0.08, (S, L)) * (flags == 0)
+    n[:, 1:L + 1] = (re + 1j * im)[:, :, None] * (1.0 + 0.02 * (lam[None, None, :] - 600.0) / 300.0)
+    n[:, L + 1] = 1.52
+    d = np.where(flags == 1, rng.uniform(2e4, 5e5, (S, L)), rng.uniform(20.0, 250.0, (S, L)))
+    if L_per_stack is not None:
+        for s in range(S):
+            n[s, L_per_stack[s] + 1:] = 1.52
+            d[s, L_per_stack[s]:] = 0.0
+            flags[s, L_per_stack[s]:] = 0
+    w = W.Workload("inc", theta=np.deg2rad(np.linspace(0, 80, n_theta)), lam=lam, d=d, n_direct=n,
+                   L_per_stack=L_per_stack)
+    return w, flags
+
+
+def gpu_inc(w, flags, prec, pols=None):
+    prob = abi.to_device(w, prec, pols=pols)
+    R, T = prob.empty_out(), prob.empty_out()
+    fl = None if flags is None else torch.as_tensor(flags, dtype=torch.uint8, device="cuda").contiguous()
+    abi.tmm_inc_batched(prob, fl, R, T)
+    torch.cuda.synchronize()
+    return R.double().cpu().numpy(), T.double().cpu().numpy()
+
+
+def oracle_inc(w, flags):
+    out = [inc.inc_tmm(pol, w.n_direct, w.d, flags, w.theta, w.lam, L_per_stack=w.L_per_stack) for pol in "sp"]
+    return np.stack([o[0] for o in out]), np.stack([o[1] for o in out])
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_incoherent_layers_match_oracle(prec):
+    w, flags = random_inc_workload(41)
+    assert flags.sum() >= 4
+    Ro, To = oracle_inc(w, flags)
+    R, T = gpu_inc(w, flags, prec)
+    assert np.max(np.abs(R - Ro)) <= TOL[prec] and np.max(np.abs(T - To)) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_ragged_stacks_and_unpolarised_mode(prec):
+    Ls = np.array([6, 3, 1, 5, 4], dtype=np.int32)
+    w, flags = random_inc_workload(42, L_per_stack=Ls)
+    Ro, To = oracle_inc(w, flags)
+    R, T = gpu_inc(w, flags, prec)
+    assert np.max(np.abs(R - Ro)) <= TOL[prec] and np.max(np.abs(T - To)) <= TOL[prec]
+    Ru, Tu = gpu_inc(w, flags, prec, pols="u")
+    assert np.max(np.abs(Ru[0] - 0.5 * (Ro[0] + Ro[1]))) <= TOL[prec]
+    assert np.max(np.abs(Tu[0] - 0.5 * (To[0] + To[1]))) <= TOL[prec]
+
+
+def test_no_flags_is_the_coherent_result():
+    w, _ = random_inc_workload(43)
+    Ro, To = oracle_RT(w)
+    R, T = gpu_inc(w, None, "f64")
+    assert np.max(np.abs(R - Ro)) <= 1e-10 and np.max(np.abs(T - To)) <= 1e-10
+
+
+def test_evanescent_cut_and_absorbing_incoherent_layer():
+    lam = np.array([600.0, 650.0])
+    th = np.deg2rad([0.0, 70.0])
+    nd = np.array([[1.8, 2.2, 1.5, 2.0, 1.0],        # at 70 deg the 1.5 slab is evanescent
+                   [1.0, 2.0, 1.5 + 0.01j, 1.7, 1.0]], dtype=np.complex128)  # absorbing incoherent
+    d = np.array([[110.0, 1e6, 90.0], [100.0, 1e5, 80.0]])
+    flags = np.array([[0, 1, 0], [0, 1, 0]], dtype=np.uint8)
+    w = W.Workload("cut", theta=th, lam=lam, d=d, n_direct=nd)
+    Ro, To = oracle_inc(W.Workload("cut", theta=th, lam=lam, d=d[:1], n_direct=np.repeat(nd[:1, :, None], 2, 2)),
+                        flags[:1])
+    R, T = gpu_inc(w, flags, "f64")
+    assert np.max(np.abs(R[:, 0] - Ro[:, 0])) <= 1e-10 and np.max(np.abs(T[:, 0] - To[:, 0])) <= 1e-10
+    assert np.all(T[:, 0, 1, :] == 0.0)
+    assert np.isnan(R[:, 1]).all() and np.isnan(T[:, 1]).all()
