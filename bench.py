@@ -269,6 +269,8 @@ def gpu_arm(args):
             out["adjoint"] = bench_adjoint(args, torch, abi, W, flush, world, max_over_ranks)
         if "optimize" in sections:
             out["optimize"] = bench_optimize(args, torch, abi, W, flush, world, max_over_ranks)
+        if "incoherent" in sections:
+            out["incoherent"] = bench_incoherent(args, torch, abi, W, flush, world, max_over_ranks)
         if "paper" in sections:
             out["paper_shapes"] = bench_paper_shapes(args, torch, abi, W, flush)
         if "surrogate" in sections and not args.skip_surrogate:
@@ -288,7 +290,7 @@ def gpu_arm(args):
         "roofline": head["roofline"], "clocks": head.get("clocks"), "e2e": head.get("e2e"),
         "gpu_launches": args.steps,
     }
-    for k in ("f64", "f64x", "ragged", "adjoint", "optimize", "paper_shapes", "surrogate"):
+    for k in ("f64", "f64x", "ragged", "adjoint", "optimize", "incoherent", "paper_shapes", "surrogate"):
         if k in out:
             line[k] = out[k]
     line["cpu_baseline"] = cpu_baseline(w, args) if (rank == 0 and world == 1 and not args.skip_cpu) else None
@@ -399,6 +401,30 @@ def bench_optimize(args, torch, abi, W, flush, world, max_over_ranks):
             "stack_steps_per_s": w.S * world * 1e3 / ms, "evals_per_s": w.evals * world / (ms * 1e-3),
             "merit_mean_step0": float(h[0].mean()), "merit_mean_step99": float(h[-1].mean()),
             "merit_best_step99": float(h[-1].min()), "steps_timed": 3 * n_steps}
+
+
+def bench_incoherent(args, torch, abi, W, flush, world, max_over_ranks):
+    """Coatings on a 1 mm incoherent glass plate (16384 stacks x 23 coherent
+    layers + the plate, 512 lambda x 32 theta, s+p, R and T): the incoherent
+    kernel vs the coherent kernel on the same stacks (which would show the
+    plate's fringes)."""
+    w = W.coated_substrate()
+    res = {"workload": w.name, "unit": "evals/s"}
+    for prec in ("f32", "f64"):
+        if prec == "f64" and args.skip_f64:
+            continue
+        prob = abi.to_device(w, prec)
+        flags = torch.as_tensor(w.meta["incoherent"], device=prob.d.device)
+        R, T = prob.empty_out(), prob.empty_out()
+        steps = max(3, args.steps // 2) if prec == "f32" else 2
+        ti = time_steps(lambda: abi.tmm_inc_batched(prob, flags, R, T), steps, 3, torch, flush)
+        tc = time_steps(lambda: abi.tmm_coh_batched(prob, R, T), steps, 3, torch, flush)
+        ms_i, ms_c = max_over_ranks(sum(ti) / len(ti)), max_over_ranks(sum(tc) / len(tc))
+        res[prec] = {"value": w.evals * world / (ms_i * 1e-3), "ms_per_step": ms_i,
+                     "coherent_same_stacks_ms": ms_c, "steps": steps}
+        del R, T, prob
+        torch.cuda.empty_cache()
+    return res
 
 
 def bench_surrogate(args, torch, abi, W, flush, world, max_over_ranks):
@@ -588,8 +614,9 @@ def main():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-extras", action="store_true", help="headline only (no ragged / adjoint lines)")
     ap.add_argument("--skip-surrogate", action="store_true")
-    ap.add_argument("--sections", default="ragged,adjoint,optimize,paper,surrogate",
-                    help="extra sections after the headline (comma list of ragged, adjoint, optimize, paper, surrogate)")
+    ap.add_argument("--sections", default="ragged,adjoint,optimize,incoherent,paper,surrogate",
+                    help="extra sections after the headline (comma list of ragged, adjoint, optimize, incoherent, paper, "
+                         "surrogate)")
     ap.add_argument("--sur-train", type=int, default=2_000_000, help="training spectra (GPU-generated)")
     ap.add_argument("--sur-steps", type=int, default=2000, help="training steps of 8192 spectra")
     ap.add_argument("--stacks", type=int, default=0, help="shrink the workload (profiling runs only)")

@@ -207,6 +207,27 @@ def ragged(seed=3, S=131072, L_max=120, n_lambda=256, n_theta=16):
                     L_per_stack=Ls)
 
 
+def coated_substrate(seed=5, S=16384, L=24, n_lambda=512, n_theta=32):
+    """Coatings on a thick glass plate in air: layers 1..L-1 as the dispersive
+    workload (8 Cauchy materials, d ~ U[5, 400] nm), layer L a 1 mm plate of
+    the substrate index 1.52 flagged incoherent, air behind it.  Returns the
+    workload with ``meta["incoherent"]`` = uint8 [S][L] flags."""
+    rng = np.random.default_rng(seed)
+    lam = np.linspace(300.0, 1200.0, n_lambda)
+    table = cauchy_table(rng, lam)
+    mat = _mat_rows(rng, S, L)
+    mat[:, L] = N_MATERIALS + 1       # the plate: substrate index
+    mat[:, L + 1] = N_MATERIALS       # air behind it (the ambient row)
+    d = rng.uniform(5.0, 400.0, (S, L))
+    d[:, L - 1] = 1.0e6
+    flags = np.zeros((S, L), dtype=np.uint8)
+    flags[:, L - 1] = 1
+    return Workload(f"coated substrate ({S} stacks x {L - 1} coherent layers on a 1 mm incoherent plate, "
+                    f"{n_lambda} lambda x {n_theta} theta)",
+                    theta=deg(np.linspace(0, 85, n_theta)), lam=lam, d=d, table=table, mat_idx=mat,
+                    meta={"incoherent": flags})
+
+
 SURROGATE_L = 20
 SURROGATE_D_RANGE = (20.0, 250.0)
 
@@ -280,4 +301,5 @@ WORKLOADS = {
     "speedup_x1": speedup_x1,
     "dataset_x2": dataset_x2,
     "map_x3": map_x3,
+    "coated_substrate": coated_substrate,
 }

@@ -10,7 +10,7 @@ import torch
 from oracle import incoherent as inc
 from paper_2111_13667_gb300 import abi
 from paper_2111_13667_gb300 import workloads as W
-from tests.helpers import oracle_RT
+from tests.helpers import oracle_RT, oracle_index
 
 pytestmark = pytest.mark.gpu
 
@@ -102,3 +102,15 @@ def test_evanescent_cut_and_absorbing_incoherent_layer():
     assert np.max(np.abs(R[:, 0] - Ro[:, 0])) <= 1e-10 and np.max(np.abs(T[:, 0] - To[:, 0])) <= 1e-10
     assert np.all(T[:, 0, 1, :] == 0.0)
     assert np.isnan(R[:, 1]).all() and np.isnan(T[:, 1]).all()
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_coated_substrate_workload_sample(prec):
+    # the benchmark's workload (gathered material table, 1 mm incoherent plate)
+    w = W.coated_substrate(S=4, n_lambda=23, n_theta=6)
+    flags = w.meta["incoherent"]
+    n = oracle_index(w)
+    Ro = np.stack([inc.inc_tmm(pol, n, w.d, flags, w.theta, w.lam)[0] for pol in "sp"])
+    To = np.stack([inc.inc_tmm(pol, n, w.d, flags, w.theta, w.lam)[1] for pol in "sp"])
+    R, T = gpu_inc(w, flags, prec)
+    assert np.max(np.abs(R - Ro)) <= TOL[prec] and np.max(np.abs(T - To)) <= TOL[prec]
