@@ -20,7 +20,8 @@ Beside them: ``mlp.py`` (the surrogate network's reference forward/backward),
 ``optimize.py`` (many-start Adam over the thicknesses on top of
 ``merit_grad``, the merit-driven optimisation of the paper's Fig. 1c) and
 ``incoherent.py`` (thick incoherent layers combined by intensities between
-coherent blocks evaluated with ``coh_tmm``).
+coherent blocks evaluated with ``coh_tmm``) and ``absorption.py`` (absorbed
+fraction per layer from the field amplitudes of right partial products).
 """
 from __future__ import annotations
 
