@@ -205,6 +205,21 @@ TMM_API tmm_status tmm_inc_batched(const tmm_problem *p, const uint8_t *incohere
                                    void *stream);
 
 /*
+ * Absorbed fraction of the incident power in every layer, from the partial
+ * products of Eq. 4 (the paper notes partial coefficients come from
+ * multiplying only part of the chain): A_j = F_j - F_{j+1}, F_j the Poynting
+ * flux at the left boundary of layer j normalised by the incident flux
+ * (F_1 = 1 - R, F_{L+1} = T, so R + T + sum_j A_j = 1).
+ *   A     device [P][S][L_max][n_theta][n_lambda]; entries j >= L_s are 0;
+ *         with TMM_POL_AVG one plane holding (A_s + A_p) / 2
+ *   R, T  device [P][S][n_theta][n_lambda] from the same sweep, or NULL (T
+ *         may be NULL alone)
+ * Limits: L_max <= 127 (else TMM_ERR_UNSUPPORTED); prec TMM_F64 or TMM_F32.
+ * Exact grazing incidence gives A = 0, R = 1, T = 0.  Asynchronous on `stream`.
+ */
+TMM_API tmm_status tmm_absorption_batched(const tmm_problem *p, void *A, void *R, void *T, void *stream);
+
+/*
  * Batched reward of the paper's reinforcement-learning environment (Sec. 5):
  *   reward[s] = - sum over (plane, theta, lambda) of |R_target - R|
  * for every stack, with the planes of pol_mask (s, p, or their mean for

@@ -14,7 +14,8 @@ The amplitudes come from the boundary conditions written as 2x2 matrices
 (continuity of E_y and q E-difference for s; of H_y and (q / n^2) H-difference
 for p), multiplied in full (complex128), the incident amplitude set to 1.
 The integral of |a e^{i kappa z} + b e^{-i kappa z}|^2 (and of the difference)
-is taken in closed form.  Layers past L_s give 0; the clamp of Im delta
+is taken in closed form, the backward term with its amplitude at the layer's
+right boundary (no growing exponential).  Layers past L_s give 0; the clamp of Im delta
 (reading C6) applies to the propagation matrices as in the other oracles.
 """
 from __future__ import annotations
@@ -41,10 +42,12 @@ def _int_exp(c, d):
     return np.where(small, d * (1 + c * d / 2), np.expm1(safe * d) / safe)
 
 
-def _int_mod2(a, b, kappa, d, sign):
-    """integral_0^d |a e^{i kappa z} + sign b e^{-i kappa z}|^2 dz."""
-    return (np.abs(a) ** 2 * _int_exp(-2 * kappa.imag, d).real
-            + np.abs(b) ** 2 * _int_exp(2 * kappa.imag, d).real
+def _int_mod2(a, b, b_right, kappa, d, sign):
+    """integral_0^d |a e^{i kappa z} + sign b e^{-i kappa z}|^2 dz, where the
+    backward wave's own term is written with its amplitude at z = d,
+    b_right = b e^{-i kappa d}, so that every exponential decays."""
+    decay = _int_exp(-2 * kappa.imag, d).real
+    return ((np.abs(a) ** 2 + np.abs(b_right) ** 2) * decay
             + 2 * sign * (a * np.conj(b) * _int_exp(2j * kappa.real, d)).real)
 
 
@@ -79,12 +82,15 @@ def absorption(pol, n, d, theta, lam, L_per_stack=None):
                 delta = delta.real + 1j * np.minimum(delta.imag, IM_DELTA_MAX)
                 z = np.zeros_like(delta)
                 return np.array([[np.exp(-1j * delta), z], [z, np.exp(1j * delta)]])
-            # right partial products: Pr[j] maps v_left(L+1) to v_left(j)
+            # right partial products: Pr[j] maps v_left(L+1) to v_left(j), Pq[j]
+            # to the amplitudes at the right boundary of layer j
             eye = np.array([[np.ones(Nl), np.zeros(Nl)], [np.zeros(Nl), np.ones(Nl)]], dtype=np.complex128)
             Pr = [None] * (L + 2)
+            Pq = [None] * (L + 2)
             Pr[L + 1] = eye
             for j in range(L, 0, -1):
-                Pr[j] = np.einsum("ikl,kjl->ijl", phase(j), np.einsum("ikl,kjl->ijl", interface(j), Pr[j + 1]))
+                Pq[j] = np.einsum("ikl,kjl->ijl", interface(j), Pr[j + 1])
+                Pr[j] = np.einsum("ikl,kjl->ijl", phase(j), Pq[j])
             M = np.einsum("ikl,kjl->ijl", interface(0), Pr[1])
             t = 1.0 / M[0, 0]
             r = M[1, 0] * t
@@ -94,14 +100,15 @@ def absorption(pol, n, d, theta, lam, L_per_stack=None):
             k0 = 2 * np.pi / lam
             for j in range(1, L + 1):
                 v = Pr[j][:, 0] * t   # amplitudes at the left boundary of layer j
+                b_right = Pq[j][1, 0] * t
                 kappa = k0 * q[j]
                 dj = d[s, j - 1]
                 im_eps = (med[j] ** 2).imag
                 if pol == "s":
-                    e2 = _int_mod2(v[0], v[1], kappa, dj, +1)
+                    e2 = _int_mod2(v[0], v[1], b_right, kappa, dj, +1)
                 else:
                     n4 = np.abs(med[j]) ** 4
-                    e2 = (np.abs(q[j]) ** 2 * _int_mod2(v[0], v[1], kappa, dj, -1)
-                          + beta ** 2 * _int_mod2(v[0], v[1], kappa, dj, +1)) / n4
+                    e2 = (np.abs(q[j]) ** 2 * _int_mod2(v[0], v[1], b_right, kappa, dj, -1)
+                          + beta ** 2 * _int_mod2(v[0], v[1], b_right, kappa, dj, +1)) / n4
                 A[s, j - 1, it] = k0 * im_eps * e2 / p_in
     return A, R, T

@@ -36,7 +36,7 @@ EXPORTED = ("tmm_coh_batched", "tmm_coh_batched_ex", "tmm_workspace_size", "tmm_
             "tmm_coh_grad", "tmm_status_string", "tmm_last_cuda_error", "tmm_version",
             "tmm_probe_fma_rate", "tmm_gemm_bf16", "tmm_gemm_bf16_t", "tmm_coh_batched_noalloc",
             "tmm_optimize_workspace_size", "tmm_optimize_adam", "tmm_reward_workspace_size", "tmm_coh_reward",
-            "tmm_inc_batched", "tmm_surrogate_create", "tmm_surrogate_destroy", "tmm_surrogate_outputs", "tmm_surrogate_parameters",
+            "tmm_inc_batched", "tmm_absorption_batched", "tmm_surrogate_create", "tmm_surrogate_destroy", "tmm_surrogate_outputs", "tmm_surrogate_parameters",
             "tmm_surrogate_generate", "tmm_surrogate_train_step", "tmm_surrogate_infer", "tmm_surrogate_layer",
             "tmm_surrogate_status", "tmm_surrogate_save", "tmm_surrogate_load")
 
@@ -129,6 +129,7 @@ def load(path: Optional[str] = None):
         lib.tmm_reward_workspace_size.argtypes = [P, C, ctypes.POINTER(sz)]
         lib.tmm_coh_reward.argtypes = [P, C, vp, vp, vp, sz, vp]
         lib.tmm_inc_batched.argtypes = [P, vp, vp, vp, vp]
+        lib.tmm_absorption_batched.argtypes = [P, vp, vp, vp, vp]
         lib.tmm_optimize_adam.argtypes = [P, vp, ctypes.POINTER(TmmAdamCfg), ctypes.c_int32, vp, vp, sz, vp]
         i32, f32 = ctypes.c_int32, ctypes.c_float
         lib.tmm_surrogate_create.argtypes = [ctypes.POINTER(TmmSurrogateDesc), ctypes.POINTER(vp)]
@@ -152,7 +153,8 @@ def load(path: Optional[str] = None):
         for name in ("tmm_coh_batched", "tmm_coh_batched_ex", "tmm_workspace_size",
                      "tmm_workspace_status", "tmm_coh_grad", "tmm_probe_fma_rate", "tmm_gemm_bf16",
                      "tmm_gemm_bf16_t", "tmm_coh_batched_noalloc", "tmm_optimize_workspace_size",
-                     "tmm_optimize_adam", "tmm_reward_workspace_size", "tmm_coh_reward", "tmm_inc_batched"):
+                     "tmm_optimize_adam", "tmm_reward_workspace_size", "tmm_coh_reward", "tmm_inc_batched",
+                     "tmm_absorption_batched"):
             getattr(lib, name).restype = ctypes.c_int
         if path is None:
             _lib = lib
@@ -369,6 +371,13 @@ def tmm_inc_batched(prob: DeviceProblem, incoherent: Optional[torch.Tensor], R: 
     """R, T with incoherent layers; ``incoherent`` uint8 [S][L_max] on the device or None."""
     _check("tmm_inc_batched", load().tmm_inc_batched(ctypes.byref(prob.struct()), _ptr(incoherent), _ptr(R),
                                                      _ptr(T), _stream(stream)))
+
+
+def tmm_absorption_batched(prob: DeviceProblem, A: torch.Tensor, R: Optional[torch.Tensor] = None,
+                           T: Optional[torch.Tensor] = None, stream=None):
+    """A [P][S][L_max][N_theta][N_lambda] (and R, T) from the partial products."""
+    _check("tmm_absorption_batched", load().tmm_absorption_batched(ctypes.byref(prob.struct()), _ptr(A), _ptr(R),
+                                                                   _ptr(T), _stream(stream)))
 
 
 def adam_cfg(lr, beta1=0.9, beta2=0.999, eps=1e-8, d_min=0.0, d_max=1e30, step0=0) -> TmmAdamCfg:

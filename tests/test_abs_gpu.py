@@ -1,0 +1,89 @@
+"""GPU parity of the per-layer absorption (tmm_absorption_batched, flux
+differences at layer boundaries) against the oracle's integrals of the
+absorption density (``oracle/absorption.py``), a different formulation.
+
+Tolerances: FP64 within 1e-10 absolute, FP32 within 1e-4, element by
+element in A, R and T; energy balance R + T + sum A = 1 to the same."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import absorption as ab
+from paper_2111_13667_gb300 import abi
+from paper_2111_13667_gb300 import workloads as W
+from tests.helpers import oracle_index
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-10, "f32": 1e-4}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    abi.load()
+
+
+def gpu_abs(w, prec, pols=None):
+    prob = abi.to_device(w, prec, pols=pols)
+    P = prob.n_pol
+    A = torch.empty(P, w.S, w.L_max, w.n_theta, w.n_lambda, dtype=prob.real_dtype, device="cuda")
+    R, T = prob.empty_out(), prob.empty_out()
+    abi.tmm_absorption_batched(prob, A, R, T)
+    torch.cuda.synchronize()
+    return A.double().cpu().numpy(), R.double().cpu().numpy(), T.double().cpu().numpy()
+
+
+def oracle_abs(w):
+    n = oracle_index(w)
+    out = [ab.absorption(pol, n, w.d, w.theta, w.lam, L_per_stack=w.L_per_stack) for pol in "sp"]
+    return tuple(np.stack([o[i] for o in out]) for i in range(3))
+
+
+def lossy_workload(seed, S=6, L=7, n_lambda=19, n_theta=5):
+    rng = np.random.default_rng(seed)
+    lam = np.linspace(420.0, 780.0, n_lambda)
+    n = np.empty((S, L + 2, n_lambda), dtype=np.complex128)
+    n[:, 0] = 1.0
+    n[:, 1:L + 1] = (rng.uniform(1.3, 2.6, (S, L)) + 1j * rng.uniform(0.0, 0.4, (S, L)))[:, :, None] \
+        * (1.0 + 0.03 * (lam - 600.0) / 180.0)
+    n[:, L + 1] = 1.52 + 0.02j
+    d = rng.uniform(15.0, 250.0, (S, L))
+    return W.Workload("lossy", theta=np.deg2rad(np.linspace(0, 80, n_theta)), lam=lam, d=d, n_direct=n)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_absorption_matches_oracle(prec):
+    w = lossy_workload(51)
+    Ao, Ro, To = oracle_abs(w)
+    A, R, T = gpu_abs(w, prec)
+    assert np.max(np.abs(A - Ao)) <= TOL[prec], np.max(np.abs(A - Ao))
+    assert np.max(np.abs(R - Ro)) <= TOL[prec] and np.max(np.abs(T - To)) <= TOL[prec]
+    assert np.max(np.abs(R + T + A.sum(axis=2) - 1.0)) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_dispersive_table_ragged_and_unpolarised(prec):
+    w = W.ragged(seed=52, S=23, L_max=12, n_lambda=21, n_theta=4)
+    Ao, Ro, To = oracle_abs(w)
+    A, R, T = gpu_abs(w, prec)
+    assert np.max(np.abs(A - Ao)) <= TOL[prec] and np.max(np.abs(T - To)) <= TOL[prec]
+    for s in range(w.S):
+        assert np.all(A[:, s, w.L_per_stack[s]:] == 0.0)
+    Au, _, _ = gpu_abs(w, prec, pols="u")
+    assert np.max(np.abs(Au[0] - 0.5 * (Ao[0] + Ao[1]))) <= TOL[prec]
+
+
+def test_thick_absorbers_and_grazing():
+    # opaque layers (the Im delta clamp) keep the balance; exact grazing gives A = 0
+    lam = np.array([500.0, 700.0])
+    th = np.deg2rad([0.0, 45.0, 90.0])
+    nd = np.array([[1.0, 2.0 + 1.0j, 1.6, 0.2 + 3.5j, 1.52]], dtype=np.complex128)
+    w = W.Workload("opaque", theta=th, lam=lam, d=np.array([[40.0, 100.0, 2e4]]), n_direct=nd)
+    A, R, T = gpu_abs(w, "f64")
+    assert np.max(np.abs(R + T + A.sum(axis=2) - 1.0)) <= 1e-10
+    assert np.all(A[:, :, :, 2, :] == 0.0) and np.all(R[:, :, 2, :] == 1.0)
+    wl = W.Workload("opaque", theta=th[:2], lam=lam, d=w.d, n_direct=np.repeat(nd[:, :, None], 2, 2))
+    Ao, Ro, _ = oracle_abs(wl)
+    assert np.max(np.abs(A[:, :, :, :2] - Ao)) <= 1e-10
