@@ -271,6 +271,8 @@ def gpu_arm(args):
             out["optimize"] = bench_optimize(args, torch, abi, W, flush, world, max_over_ranks)
         if "incoherent" in sections:
             out["incoherent"] = bench_incoherent(args, torch, abi, W, flush, world, max_over_ranks)
+        if "absorption" in sections:
+            out["absorption"] = bench_absorption(args, torch, abi, W, flush, world, max_over_ranks)
         if "paper" in sections:
             out["paper_shapes"] = bench_paper_shapes(args, torch, abi, W, flush)
         if "surrogate" in sections and not args.skip_surrogate:
@@ -290,7 +292,8 @@ def gpu_arm(args):
         "roofline": head["roofline"], "clocks": head.get("clocks"), "e2e": head.get("e2e"),
         "gpu_launches": args.steps,
     }
-    for k in ("f64", "f64x", "ragged", "adjoint", "optimize", "incoherent", "paper_shapes", "surrogate"):
+    for k in ("f64", "f64x", "ragged", "adjoint", "optimize", "incoherent", "absorption", "paper_shapes",
+              "surrogate"):
         if k in out:
             line[k] = out[k]
     line["cpu_baseline"] = cpu_baseline(w, args) if (rank == 0 and world == 1 and not args.skip_cpu) else None
@@ -423,6 +426,33 @@ def bench_incoherent(args, torch, abi, W, flush, world, max_over_ranks):
         res[prec] = {"value": w.evals * world / (ms_i * 1e-3), "ms_per_step": ms_i,
                      "coherent_same_stacks_ms": ms_c, "steps": steps}
         del R, T, prob
+        torch.cuda.empty_cache()
+    return res
+
+
+def bench_absorption(args, torch, abi, W, flush, world, max_over_ranks):
+    """Absorbed fraction in every layer (the adjoint workload: 4096 stacks x
+    40 absorbing layers, 512 lambda x 16 theta, s+p) with R and T from the
+    same sweep, vs the plain forward on the same stacks."""
+    w = W.adjoint()
+    res = {"workload": w.name, "unit": "evals/s (A for every layer, R, T)"}
+    for prec in ("f32", "f64"):
+        if prec == "f64" and args.skip_f64:
+            continue
+        prob = abi.to_device(w, prec)
+        A = torch.empty(prob.n_pol, w.S, w.L_max, w.n_theta, w.n_lambda, dtype=prob.real_dtype,
+                        device=prob.d.device)
+        R, T = prob.empty_out(), prob.empty_out()
+        steps = max(3, args.steps // 2) if prec == "f32" else 2
+        ta = time_steps(lambda: abi.tmm_absorption_batched(prob, A, R, T), steps, 3, torch, flush)
+        tf = time_steps(lambda: abi.tmm_coh_batched(prob, R, T), steps, 3, torch, flush)
+        abi.tmm_absorption_batched(prob, A, R, T)
+        torch.cuda.synchronize()
+        bal = float((R + T + A.sum(dim=2) - 1.0).abs().max())
+        ms_a, ms_f = max_over_ranks(sum(ta) / len(ta)), max_over_ranks(sum(tf) / len(tf))
+        res[prec] = {"value": w.evals * world / (ms_a * 1e-3), "ms_per_step": ms_a, "forward_same_stacks_ms": ms_f,
+                     "A_bytes": A.numel() * A.element_size(), "max_energy_balance_error": bal, "steps": steps}
+        del A, R, T, prob
         torch.cuda.empty_cache()
     return res
 
@@ -614,9 +644,9 @@ def main():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-extras", action="store_true", help="headline only (no ragged / adjoint lines)")
     ap.add_argument("--skip-surrogate", action="store_true")
-    ap.add_argument("--sections", default="ragged,adjoint,optimize,incoherent,paper,surrogate",
-                    help="extra sections after the headline (comma list of ragged, adjoint, optimize, incoherent, paper, "
-                         "surrogate)")
+    ap.add_argument("--sections", default="ragged,adjoint,optimize,incoherent,absorption,paper,surrogate",
+                    help="extra sections after the headline (comma list of ragged, adjoint, optimize, incoherent, "
+                         "absorption, paper, surrogate)")
     ap.add_argument("--sur-train", type=int, default=2_000_000, help="training spectra (GPU-generated)")
     ap.add_argument("--sur-steps", type=int, default=2000, help="training steps of 8192 spectra")
     ap.add_argument("--stacks", type=int, default=0, help="shrink the workload (profiling runs only)")
