@@ -106,23 +106,12 @@ def test_total_internal_reflection_and_grazing(prec):
         assert np.max(np.abs(R[:, 0, -1, :] - 1.0)) <= 1e-12 and np.max(np.abs(T[:, 0, -1, :])) <= 1e-12
     else:
         assert np.all(R[:, 0, -1, :] == 1.0) and np.all(T[:, 0, -1, :] == 0.0)  # grazing reading
-    if prec != "f32":
-        # double-float keeps ~48 bits: on this map's high-Q guided-mode
-        # resonances under total internal reflection it lands at 1.0e-10
-        tol = TOL[prec] if prec == "f64" else 3e-10
-        assert_close(R, Ro, tol, "R")
-        assert_close(T, To, tol, "T")
-        return
-    # FP32: below the outcoupling critical angle (30 deg) the 1e-4 bar holds.
-    # Under total internal reflection these high-index layers form leaky
-    # guided modes whose resonances amplify FP32 rounding in R (which must be
-    # exactly 1 there); the measured loss is below 2e-3 and the FP64 path
-    # covers this regime at 1e-10.
-    below = np.sin(w.theta) * 2.0 < 1.0
-    assert_close(R[:, :, below], Ro[:, :, below], TOL[prec], "R below critical angle")
-    assert_close(T[:, :, below], To[:, :, below], TOL[prec], "T below critical angle")
-    assert_close(R, Ro, 2e-3, "R total internal reflection")
+    # every precision meets its standard tolerance on the whole map, total
+    # internal reflection with its high-Q guided modes included
+    assert_close(R, Ro, TOL[prec], "R")
     assert_close(T, To, TOL[prec], "T")
+    below = np.sin(w.theta) * 2.0 < 1.0
+    assert (~below).sum() > 100  # the map reaches far into total internal reflection
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32", "f64x"])
