@@ -135,6 +135,34 @@ def test_optimiser_and_average_mode_argument_checks(lib):
     assert lib.tmm_workspace_size(ctypes.byref(pa), None, ctypes.byref(n)) == abi.TMM_OK
 
 
+def test_incoherent_absorption_reward_argument_checks(lib):
+    from paper_2111_13667_gb300 import abi
+    fake = ctypes.c_void_p(0x7000)
+    p = _problem()
+    px = _problem(prec=abi.TMM_F64X)
+    # missing outputs
+    assert lib.tmm_inc_batched(ctypes.byref(p), None, None, None, None) == abi.TMM_ERR_INVALID_ARG
+    assert lib.tmm_absorption_batched(ctypes.byref(p), None, None, None, None) == abi.TMM_ERR_INVALID_ARG
+    assert lib.tmm_absorption_batched(ctypes.byref(p), fake, None, fake, None) == abi.TMM_ERR_INVALID_ARG
+    assert lib.tmm_coh_reward(ctypes.byref(p), None, None, fake, fake, 1 << 20, None) == abi.TMM_ERR_INVALID_ARG
+    # double-float is the forward kernel's mode only
+    assert lib.tmm_inc_batched(ctypes.byref(px), None, fake, None, None) == abi.TMM_ERR_UNSUPPORTED
+    assert lib.tmm_absorption_batched(ctypes.byref(px), fake, None, None, None) == abi.TMM_ERR_UNSUPPORTED
+    assert lib.tmm_coh_reward(ctypes.byref(px), None, fake, fake, fake, 1 << 20, None) == abi.TMM_ERR_UNSUPPORTED
+    # absorption keeps per-layer records: L_max <= 127
+    big = _problem(L_max=200)
+    assert lib.tmm_absorption_batched(ctypes.byref(big), fake, None, None, None) == abi.TMM_ERR_UNSUPPORTED
+    # a reward launch has no status channel for an iteration limit
+    cfg = abi.launch_cfg(persistent=1, max_items_per_block=3)
+    assert lib.tmm_coh_reward(ctypes.byref(p), ctypes.byref(cfg), fake, fake, fake, 1 << 20,
+                              None) == abi.TMM_ERR_INVALID_ARG
+    # empty batches are no-ops
+    e = _problem(S=0)
+    assert lib.tmm_inc_batched(ctypes.byref(e), None, None, None, None) == abi.TMM_OK
+    assert lib.tmm_absorption_batched(ctypes.byref(e), None, None, None, None) == abi.TMM_OK
+    assert lib.tmm_coh_reward(ctypes.byref(e), None, None, None, None, 0, None) == abi.TMM_OK
+
+
 def test_empty_problem_is_a_noop(lib):
     from paper_2111_13667_gb300 import abi
     p = _problem(S=0)
