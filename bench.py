@@ -19,6 +19,7 @@ import json
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -57,9 +58,9 @@ def kernel_hash():
     return h.hexdigest()[:16]
 
 
-def stored_traffic(kernel_key):
-    """DRAM bytes per launch from the committed ncu summary, if it still
-    describes the current kernel source (else None)."""
+def stored_profile(kernel_key, field):
+    """A figure of the committed ncu summary (profiles/traffic.json), if it
+    still describes the current kernel source (else None)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
@@ -68,7 +69,12 @@ def stored_traffic(kernel_key):
     ent = data.get(kernel_key)
     if not ent or ent.get("source_hash") != kernel_hash():
         return None
-    return ent.get("dram_bytes_per_launch")
+    return ent.get(field)
+
+
+def stored_traffic(kernel_key):
+    """DRAM bytes per launch from the committed ncu summary (or None)."""
+    return stored_profile(kernel_key, "dram_bytes_per_launch")
 
 
 def measured_peaks():
@@ -88,7 +94,7 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"tmm_clocks_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
@@ -218,6 +224,7 @@ def gpu_arm(args):
         entry = {"value": value, "ms_per_step": ms, "steps": steps, "warmup": warmup, "wall_s": wall,
                  "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
                               "unit": "TFLOP/s", "frac": achieved / peak, "traffic": stored_traffic(key),
+                              "issue_frac": stored_profile(key, "issue_active_frac"),
                               "kernel": key,
                               "work": f"{FLOPS_PER_EVAL_INTERFACE:g} flop per eval-interface x {interfaces} "
                                       f"interfaces x {evals} evals (standard count of the vector-sweep "
