@@ -100,8 +100,16 @@ __device__ __forceinline__ void fill_stage_grad(const tmm_problem &p, int s, int
     }
 }
 
+// Resident blocks per SM the FP32 instance is compiled for: the kernel is
+// latency-bound (thread-local states, two warp sums per layer), and capping
+// registers at 64 for four 256-thread blocks per SM beats two blocks at 111
+// registers (measured 18 % faster, same results); the FP64 instance is held to
+// two blocks (128 registers).
+template <typename R> struct GradMinBlocks { static constexpr int value = 2; };
+template <> struct GradMinBlocks<float> { static constexpr int value = 4; };
+
 template <typename R, int KMAX>
-__global__ void __launch_bounds__(kGradThreads) tmm_grad_kernel(const tmm_problem p, const R *__restrict__ Rt,
+__global__ void __launch_bounds__(kGradThreads, GradMinBlocks<R>::value) tmm_grad_kernel(const tmm_problem p, const R *__restrict__ Rt,
                                                                 int TL, int TT, int n_lt, int n_tt, int G, R inv_N,
                                                                 R *__restrict__ merit, R *__restrict__ dm_dd,
                                                                 R *__restrict__ dm_dn, R *__restrict__ partial)
