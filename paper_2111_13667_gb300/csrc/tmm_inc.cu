@@ -246,8 +246,18 @@ tmm_status launch_inc_typed(const tmm_problem *p, const uint8_t *inc, int TL, in
 {
     auto k = tmm_inc_kernel<R, POL, WITH_T>;
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        // once per (instantiation, device) and size: repeated launches and graph
+        // capture stay free of attribute calls
+        static int set_bytes[64] = {};
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
         if (e != cudaSuccess) return cuda_fail(e);
+        if (dev < 0 || dev >= 64) return TMM_ERR_UNSUPPORTED;
+        if (set_bytes[dev] < (int)smem) {
+            e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return cuda_fail(e);
+            set_bytes[dev] = (int)smem;
+        }
     }
     k<<<(unsigned)items, dim3(TL, TT), smem, st>>>(*p, inc, TL, TT, n_lt, n_tt, Ro, To);
     return check_launch();
