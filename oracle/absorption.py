@@ -112,3 +112,55 @@ def absorption(pol, n, d, theta, lam, L_per_stack=None):
                           + beta ** 2 * _int_mod2(v[0], v[1], b_right, kappa, dj, +1)) / n4
                 A[s, j - 1, it] = k0 * im_eps * e2 / p_in
     return A, R, T
+
+
+def field_profile(pol, n, d, theta, lam, n_z, L_per_stack=None):
+    """|E(z) / E_inc|^2 at the depths z_k = (k + 1/2) d_j / n_z of every layer:
+    [S][L_max][n_z][N_theta][N_lambda] (0 past L_s).  E_inc is the incident
+    plane wave's field amplitude: for p, |E|^2 = (|q|^2 |a e - b e|^2 +
+    beta^2 |a e + b e|^2) / |n|^4 in units of the incident H amplitude, and
+    the incident E = H / n_0 in those units, so the ratio carries n_0^2."""
+    n = np.asarray(n, dtype=np.complex128)
+    d = np.asarray(d, dtype=np.float64)
+    theta = np.atleast_1d(np.asarray(theta, dtype=np.float64))
+    lam = np.atleast_1d(np.asarray(lam, dtype=np.float64))
+    S, Lp2, Nl = n.shape
+    L_max = Lp2 - 2
+    out = np.zeros((S, L_max, n_z, theta.size, Nl))
+    for s in range(S):
+        L = int(L_per_stack[s]) if L_per_stack is not None else L_max
+        med = n[s, :L + 2]
+        for it, th in enumerate(theta):
+            beta = med[0].real * np.sin(th)
+            q = _root(med ** 2 - beta ** 2)
+            q[0] = med[0].real * np.cos(th)
+            k = q if pol == "s" else q / med ** 2
+            def interface(j):
+                a, b = k[j], k[j + 1]
+                return np.array([[a + b, a - b], [a - b, a + b]]) / (2 * a)
+            def phase(j):
+                delta = 2 * np.pi * q[j] * d[s, j - 1] / lam
+                delta = delta.real + 1j * np.minimum(delta.imag, IM_DELTA_MAX)
+                z = np.zeros_like(delta)
+                return np.array([[np.exp(-1j * delta), z], [z, np.exp(1j * delta)]])
+            eye = np.array([[np.ones(Nl), np.zeros(Nl)], [np.zeros(Nl), np.ones(Nl)]], dtype=np.complex128)
+            Pr = [None] * (L + 2)
+            Pr[L + 1] = eye
+            for j in range(L, 0, -1):
+                Pr[j] = np.einsum("ikl,kjl->ijl", phase(j), np.einsum("ikl,kjl->ijl", interface(j), Pr[j + 1]))
+            M = np.einsum("ikl,kjl->ijl", interface(0), Pr[1])
+            t = 1.0 / M[0, 0]
+            k0 = 2 * np.pi / lam
+            for j in range(1, L + 1):
+                a, b = Pr[j][0, 0] * t, Pr[j][1, 0] * t
+                kappa = k0 * q[j]
+                for kz in range(n_z):
+                    z = (kz + 0.5) * d[s, j - 1] / n_z
+                    fw, bw = a * np.exp(1j * kappa * z), b * np.exp(-1j * kappa * z)
+                    if pol == "s":
+                        e2 = np.abs(fw + bw) ** 2
+                    else:
+                        e2 = (np.abs(q[j]) ** 2 * np.abs(fw - bw) ** 2 + beta ** 2 * np.abs(fw + bw) ** 2) \
+                            / np.abs(med[j]) ** 4 * med[0].real ** 2
+                    out[s, j - 1, kz, it] = e2
+    return out

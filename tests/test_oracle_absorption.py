@@ -72,3 +72,34 @@ def test_layers_past_L_s_are_zero():
     for s in range(3):
         assert np.all(A[s, Ls[s]:] == 0.0)
     assert np.max(np.abs(R + T + A.sum(axis=1) - 1.0)) < 1e-13
+
+
+@pytest.mark.parametrize("pol", ["s", "p"])
+def test_field_profile_integrates_to_the_absorbed_fraction(pol):
+    # k0 Im(n^2) |E / E_inc|^2 is the absorption density per incident flux
+    # (times the flux of a unit incident wave); its midpoint-rule integral over
+    # each layer converges to A_j
+    n, d, lam = lossy_stacks(5, S=2, L=4, n_lambda=3)
+    n0 = 1.3  # a denser injection medium pins the n_0^2 of the p normalisation
+    n[:, 0] = n0
+    th = np.deg2rad([0.0, 50.0])
+    A, _, _ = ab.absorption(pol, n, d, th, lam)
+    nz = 400
+    E2 = ab.field_profile(pol, n, d, th, lam, nz)
+    k0 = 2 * np.pi / lam
+    flux_inc = np.cos(th)[:, None] * n0 if pol == "s" else np.cos(th)[:, None] / n0
+    im_eps = (n[:, 1:5, :] ** 2).imag                       # [S][L][N_lambda]
+    dens = k0 * im_eps[:, :, None, None, :] * E2            # [S][L][n_z][N_theta][N_lambda]
+    if pol == "p":
+        dens = dens / n0 ** 2
+    integral = dens.mean(axis=2) * d[:, :, None, None] / flux_inc[None, None]
+    assert np.max(np.abs(integral - A)) < 2e-5
+
+
+def test_field_profile_of_a_bare_interface_region():
+    # no layer reflects: an index-matched lossless layer carries the incident
+    # wave unchanged, |E / E_inc|^2 = 1 (s) and, for p, the same
+    n = np.array([[[1.5], [1.5], [1.5]]], dtype=np.complex128)
+    for pol in "sp":
+        E2 = ab.field_profile(pol, n, np.array([[300.0]]), np.deg2rad([30.0]), np.array([600.0]), 5)
+        assert np.max(np.abs(E2 - 1.0)) < 1e-14
