@@ -220,6 +220,20 @@ TMM_API tmm_status tmm_inc_batched(const tmm_problem *p, const uint8_t *incohere
 TMM_API tmm_status tmm_absorption_batched(const tmm_problem *p, void *A, void *R, void *T, void *stream);
 
 /*
+ * Field intensity inside every layer: |E(z) / E_inc|^2 at the depths
+ * z_k = (k + 1/2) d_j / n_z, k = 0 .. n_z - 1, of every layer j, from the same
+ * partial products (E_inc: the incident plane wave's field amplitude; for p
+ * both the tangential and the normal field component count).
+ * k0 Im(n_j^2) |E|^2 |E_inc|^2 is the absorption density whose integral over
+ * layer j is tmm_absorption_batched's A_j times the incident flux.
+ *   E    device [P][S][L_max][n_z][n_theta][n_lambda]; layers j >= L_s are 0;
+ *        with TMM_POL_AVG one plane of the mean of s and p
+ * Limits: L_max <= 127, n_z >= 1; prec TMM_F64 or TMM_F32.  Exact grazing
+ * incidence gives 0.  Asynchronous on `stream`.
+ */
+TMM_API tmm_status tmm_field_profile(const tmm_problem *p, int32_t n_z, void *E, void *stream);
+
+/*
  * Batched reward of the paper's reinforcement-learning environment (Sec. 5):
  *   reward[s] = - sum over (plane, theta, lambda) of |R_target - R|
  * for every stack, with the planes of pol_mask (s, p, or their mean for

@@ -145,18 +145,23 @@ def field_profile(pol, n, d, theta, lam, n_z, L_per_stack=None):
                 return np.array([[np.exp(-1j * delta), z], [z, np.exp(1j * delta)]])
             eye = np.array([[np.ones(Nl), np.zeros(Nl)], [np.zeros(Nl), np.ones(Nl)]], dtype=np.complex128)
             Pr = [None] * (L + 2)
+            Pq = [None] * (L + 2)
             Pr[L + 1] = eye
             for j in range(L, 0, -1):
-                Pr[j] = np.einsum("ikl,kjl->ijl", phase(j), np.einsum("ikl,kjl->ijl", interface(j), Pr[j + 1]))
+                Pq[j] = np.einsum("ikl,kjl->ijl", interface(j), Pr[j + 1])
+                Pr[j] = np.einsum("ikl,kjl->ijl", phase(j), Pq[j])
             M = np.einsum("ikl,kjl->ijl", interface(0), Pr[1])
             t = 1.0 / M[0, 0]
             k0 = 2 * np.pi / lam
             for j in range(1, L + 1):
-                a, b = Pr[j][0, 0] * t, Pr[j][1, 0] * t
+                # forward wave from the left boundary, backward wave from the
+                # right boundary: both decay away from where they are taken
+                a, b_right = Pr[j][0, 0] * t, Pq[j][1, 0] * t
                 kappa = k0 * q[j]
+                dj = d[s, j - 1]
                 for kz in range(n_z):
-                    z = (kz + 0.5) * d[s, j - 1] / n_z
-                    fw, bw = a * np.exp(1j * kappa * z), b * np.exp(-1j * kappa * z)
+                    z = (kz + 0.5) * dj / n_z
+                    fw, bw = a * np.exp(1j * kappa * z), b_right * np.exp(1j * kappa * (dj - z))
                     if pol == "s":
                         e2 = np.abs(fw + bw) ** 2
                     else:

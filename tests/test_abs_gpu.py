@@ -87,3 +87,44 @@ def test_thick_absorbers_and_grazing():
     wl = W.Workload("opaque", theta=th[:2], lam=lam, d=w.d, n_direct=np.repeat(nd[:, :, None], 2, 2))
     Ao, Ro, _ = oracle_abs(wl)
     assert np.max(np.abs(A[:, :, :, :2] - Ao)) <= 1e-10
+
+
+def gpu_field(w, prec, n_z, pols=None):
+    prob = abi.to_device(w, prec, pols=pols)
+    E = torch.empty(prob.n_pol, w.S, w.L_max, n_z, w.n_theta, w.n_lambda, dtype=prob.real_dtype, device="cuda")
+    abi.tmm_field_profile(prob, n_z, E)
+    torch.cuda.synchronize()
+    return E.double().cpu().numpy()
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_field_profile_matches_oracle(prec):
+    w = lossy_workload(53, S=4, L=5, n_lambda=11, n_theta=4)
+    n = oracle_index(w)
+    Eo = np.stack([ab.field_profile(pol, n, w.d, w.theta, w.lam, 6) for pol in "sp"])
+    E = gpu_field(w, prec, 6)
+    rel = np.max(np.abs(E - Eo) / np.maximum(1.0, np.abs(Eo)))
+    assert rel <= (1e-10 if prec == "f64" else 1e-4), rel
+
+
+def test_field_profile_ragged_opaque_and_unpolarised():
+    w = W.ragged(seed=54, S=9, L_max=8, n_lambda=7, n_theta=3)
+    n = oracle_index(w)
+    Eo = np.stack([ab.field_profile(pol, n, w.d, w.theta, w.lam, 3, L_per_stack=w.L_per_stack) for pol in "sp"])
+    E = gpu_field(w, "f64", 3)
+    assert np.max(np.abs(E - Eo) / np.maximum(1.0, np.abs(Eo))) <= 1e-10
+    for s in range(w.S):
+        assert np.all(E[:, s, w.L_per_stack[s]:] == 0.0)
+    Eu = gpu_field(w, "f64", 3, pols="u")
+    assert np.max(np.abs(Eu[0] - 0.5 * (Eo[0] + Eo[1]))) <= 1e-10
+    # an opaque metal layer: the profile stays finite and vanishes past the skin
+    # depth (beyond it the Im(delta) clamp of reading C6 sets the field's
+    # floor: far below any physical scale, identical in the oracle)
+    nd = np.array([[1.0, 1.7, 0.2 + 3.5j, 1.52]], dtype=np.complex128)
+    wo = W.Workload("opaque", theta=np.deg2rad([0.0, 40.0]), lam=np.array([550.0]), d=np.array([[90.0, 2e4]]),
+                    n_direct=nd)
+    E = gpu_field(wo, "f64", 8)
+    assert np.all(np.isfinite(E))
+    assert E[:, 0, 1, 0].max() < 1e-3 and E[:, 0, 1, 1:].max() < 1e-30
+    Eo = np.stack([ab.field_profile(pol, np.repeat(nd[:, :, None], 1, 2), wo.d, wo.theta, wo.lam, 8) for pol in "sp"])
+    assert np.max(np.abs(E - Eo)) <= 1e-10
