@@ -440,7 +440,8 @@ def bench_incoherent(args, torch, abi, W, flush, world, max_over_ranks):
 def bench_absorption(args, torch, abi, W, flush, world, max_over_ranks):
     """Absorbed fraction in every layer (the adjoint workload: 4096 stacks x
     40 absorbing layers, 512 lambda x 16 theta, s+p) with R and T from the
-    same sweep, vs the plain forward on the same stacks."""
+    same sweep, vs the plain forward on the same stacks; then the field
+    intensity at two depths in every layer of the same stacks."""
     w = W.adjoint()
     res = {"workload": w.name, "unit": "evals/s (A for every layer, R, T)"}
     for prec in ("f32", "f64"):
@@ -459,7 +460,18 @@ def bench_absorption(args, torch, abi, W, flush, world, max_over_ranks):
         ms_a, ms_f = max_over_ranks(sum(ta) / len(ta)), max_over_ranks(sum(tf) / len(tf))
         res[prec] = {"value": w.evals * world / (ms_a * 1e-3), "ms_per_step": ms_a, "forward_same_stacks_ms": ms_f,
                      "A_bytes": A.numel() * A.element_size(), "max_energy_balance_error": bal, "steps": steps}
-        del A, R, T, prob
+        del A, R, T
+        torch.cuda.empty_cache()
+        # |E(z)|^2 at n_z depths in every layer, same stacks
+        n_z = 2
+        E = torch.empty(prob.n_pol, w.S, w.L_max, n_z, w.n_theta, w.n_lambda, dtype=prob.real_dtype,
+                        device=prob.d.device)
+        te = time_steps(lambda: abi.tmm_field_profile(prob, n_z, E), steps, 3, torch, flush)
+        ms_e = max_over_ranks(sum(te) / len(te))
+        res[prec]["field_profile"] = {"n_z": n_z, "value": w.evals * world / (ms_e * 1e-3), "ms_per_step": ms_e,
+                                      "E_bytes": E.numel() * E.element_size(),
+                                      "finite": bool(torch.isfinite(E).all())}
+        del E, prob
         torch.cuda.empty_cache()
     return res
 
