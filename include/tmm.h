@@ -228,7 +228,9 @@ TMM_API tmm_status tmm_absorption_batched(const tmm_problem *p, void *A, void *R
  * layer j is tmm_absorption_batched's A_j times the incident flux.
  *   E    device [P][S][L_max][n_z][n_theta][n_lambda]; layers j >= L_s are 0;
  *        with TMM_POL_AVG one plane of the mean of s and p
- * Limits: L_max <= 127, n_z >= 1; prec TMM_F64 or TMM_F32.  Exact grazing
+ * Limits: n_z >= 1 (else TMM_ERR_INVALID_ARG); prec TMM_F64 or TMM_F32; one
+ * wavelength's staged stack, (L_max + 2) x 6 reals, must fit in shared memory
+ * (L_max up to about 4800 in FP64), else TMM_ERR_UNSUPPORTED.  Exact grazing
  * incidence gives 0.  Asynchronous on `stream`.
  */
 TMM_API tmm_status tmm_field_profile(const tmm_problem *p, int32_t n_z, void *E, void *stream);

@@ -27,14 +27,23 @@ namespace tmm {
 namespace {
 
 constexpr int kFieldThreads = 256;
-constexpr int kFieldMaxLayers = 127;
 
-// One polarisation's amplitudes of layer j with their scale bookkeeping.
-template <typename R> struct Amp {
-    Cx<R> aL, bR;  // forward at the left boundary, backward at the right boundary
-    R mL, mR;      // mantissas of D where each was taken
-    int eL, eR;    // exponents of D
-    R lyL, lyR;    // LY where each was taken
+// One polarisation's running sweep: the scaled amplitude pair and D as
+// mantissa and exponent.
+template <typename R> struct Wave {
+    Cx<R> x0, x1;
+    R m;
+    int e;
+};
+
+// Layer j's amplitudes as the sweep passes it: the backward one at the right
+// boundary (after interface j|j+1, before the phase) and the forward one at
+// the left boundary (after the phase and any rescaling), each with the
+// exponent of D where it was taken (the mantissa is the same at both).
+template <typename R> struct Taken {
+    Cx<R> bR, aL;
+    R m;
+    int eR, eL;
 };
 
 template <typename R> __device__ __forceinline__ void dmul_f(R &m, int &e, R v)
@@ -43,7 +52,82 @@ template <typename R> __device__ __forceinline__ void dmul_f(R &m, int &e, R v)
     renorm_scalar(m, e);
 }
 
-template <typename R, int POL, int KMAX>
+// The right-to-left sweep from the substrate through interface 1|2 (Eqs. 1-4),
+// calling visit(j, q_j, B_j, s amplitudes, p amplitudes, LY at the right
+// boundary, LY at the left boundary) after each layer j = L .. 1.  Leaves the
+// pairs and D ready for interface 0|1 and q_nx, g_nx those of layer 1.
+template <typename R, int POL, typename Visit>
+__device__ __forceinline__ void sweep_layers(const StageA<R> *sa, const StageB<R> *sb, int TL, int tl, int L,
+                                             R q0sq, Wave<R> &ws, Wave<R> &wp, R &LY, Cx<R> &q_nx, Cx<R> &g_nx,
+                                             Visit visit)
+{
+    constexpr int RN = RenormEvery<R>::value;
+    const R yi_max = R(kImDeltaMax / kTwoPi);
+    const R kLY = R(2.0 * kTwoPi * kLog2e);
+    R absz;
+    StageA<R> A = sa[(L + 1) * TL + tl];
+    q_nx = forward_root(Cx<R>{A.d2x + q0sq, A.n2y}, &absz);
+    g_nx = cmul(q_nx, Cx<R>{A.in2x, A.in2y});
+    ws = Wave<R>{{R(1), R(0)}, {R(0), R(0)}, R(1), 0};
+    wp = ws;
+    LY = R(0);
+    int cnt = 0;
+    for (int j = L; j >= 1; --j) {
+        A = sa[j * TL + tl];
+        const StageB<R> B = sb[j * TL + tl];
+        const Cx<R> q = forward_root(Cx<R>{A.d2x + q0sq, A.n2y}, &absz);
+        const R yr = B.dl * q.x;
+        const R yi = fmin(B.dl * q.y, yi_max);
+        R sn, cs;
+        sincos_turn(yr - rint_w(yr), &sn, &cs);
+        const R E2 = exp_m2_turn(yi);
+        const Cx<R> emi = {cs, -sn}, epi = {E2 * cs, E2 * sn};
+        const Cx<R> g = cmul(q, Cx<R>{A.in2x, A.in2y});
+        Taken<R> ts{}, tp{};
+        if (POL & 1) {
+            interface_pair(q, q_nx, ws.x0, ws.x1);
+            dmul_f(ws.m, ws.e, R(4) * absz);
+            ts.bR = ws.x1, ts.m = ws.m, ts.eR = ws.e;
+            ws.x0 = cmul(emi, ws.x0);
+            ws.x1 = cmul(epi, ws.x1);
+        }
+        if (POL & 2) {
+            interface_pair(g, g_nx, wp.x0, wp.x1);
+            dmul_f(wp.m, wp.e, R(4) * absz * B.ain2);
+            tp.bR = wp.x1, tp.m = wp.m, tp.eR = wp.e;
+            wp.x0 = cmul(emi, wp.x0);
+            wp.x1 = cmul(epi, wp.x1);
+        }
+        const R lyR = LY;
+        LY += kLY * yi;
+        if (++cnt == RN) {
+            cnt = 0;
+            if (POL & 1) {
+                int k = 0;
+                renorm_pair(ws.x0, ws.x1, k);
+                ws.e -= 2 * k;
+            }
+            if (POL & 2) {
+                int k = 0;
+                renorm_pair(wp.x0, wp.x1, k);
+                wp.e -= 2 * k;
+            }
+        }
+        if (POL & 1) ts.aL = ws.x0, ts.eL = ws.e;
+        if (POL & 2) tp.aL = wp.x0, tp.eL = wp.e;
+        visit(j, q, B, ts, tp, lyR, LY);
+        q_nx = q;
+        g_nx = g;
+    }
+}
+
+// Two sweeps per thread: the first only carries the chain to interface 0|1
+// for the incident amplitude x_0[0] and the final D and LY; the second
+// repeats the same arithmetic and writes each layer's profile as it passes
+// it.  Keeping the amplitudes of every layer instead (40 bytes per layer and
+// polarisation and thread) spills to DRAM at this occupancy and costs more
+// than the repeated sweep.
+template <typename R, int POL>
 __global__ void __launch_bounds__(kFieldThreads) tmm_field_kernel(const tmm_problem p, int n_z, int TL, int TT,
                                                                   int n_lt, int n_tt, R *__restrict__ Eout)
 {
@@ -88,108 +172,60 @@ __global__ void __launch_bounds__(kFieldThreads) tmm_field_kernel(const tmm_prob
                 for (int kz = 0; kz < n_z; ++kz) store(pi, j, kz, (j < L || L < 0) ? fill : R(0));
         return;
     }
-    constexpr int RN = RenormEvery<R>::value;
-    const R yi_max = R(kImDeltaMax / kTwoPi);
-    const R kLY = R(2.0 * kTwoPi * kLog2e);
-    Amp<R> as[(POL & 1) ? KMAX : 1], ap[(POL & 2) ? KMAX : 1];
-    StageA<R> A = sa[(L + 1) * TL + tl];
-    R absz;
-    Cx<R> q_nx = forward_root(Cx<R>{A.d2x + q0sq, A.n2y}, &absz);
-    Cx<R> g_nx = cmul(q_nx, Cx<R>{A.in2x, A.in2y});
-    Cx<R> s0 = {R(1), R(0)}, s1 = {R(0), R(0)}, p0 = s0, p1 = s1;
-    R Dsm = R(1), Dpm = R(1), LY = R(0);
-    int Dse = 0, Dpe = 0, cnt = 0;
-    for (int j = L; j >= 1; --j) {
-        A = sa[j * TL + tl];
-        const StageB<R> B = sb[j * TL + tl];
-        const Cx<R> q = forward_root(Cx<R>{A.d2x + q0sq, A.n2y}, &absz);
-        const R yr = B.dl * q.x;
-        const R yi = fmin(B.dl * q.y, yi_max);
-        R sn, cs;
-        sincos_turn(yr - rint_w(yr), &sn, &cs);
-        const R E2 = exp_m2_turn(yi);
-        const Cx<R> emi = {cs, -sn}, epi = {E2 * cs, E2 * sn};
-        const Cx<R> g = cmul(q, Cx<R>{A.in2x, A.in2y});
-        if (POL & 1) {
-            interface_pair(q, q_nx, s0, s1);
-            dmul_f(Dsm, Dse, R(4) * absz);
-            as[j].bR = s1, as[j].mR = Dsm, as[j].eR = Dse, as[j].lyR = LY;
-            s0 = cmul(emi, s0);
-            s1 = cmul(epi, s1);
-        }
-        if (POL & 2) {
-            interface_pair(g, g_nx, p0, p1);
-            dmul_f(Dpm, Dpe, R(4) * absz * B.ain2);
-            ap[j].bR = p1, ap[j].mR = Dpm, ap[j].eR = Dpe, ap[j].lyR = LY;
-            p0 = cmul(emi, p0);
-            p1 = cmul(epi, p1);
-        }
-        LY += kLY * yi;
-        if (++cnt == RN) {
-            cnt = 0;
-            if (POL & 1) {
-                int k = 0;
-                renorm_pair(s0, s1, k);
-                Dse -= 2 * k;
-            }
-            if (POL & 2) {
-                int k = 0;
-                renorm_pair(p0, p1, k);
-                Dpe -= 2 * k;
-            }
-        }
-        if (POL & 1) as[j].aL = s0, as[j].mL = Dsm, as[j].eL = Dse, as[j].lyL = LY;
-        if (POL & 2) ap[j].aL = p0, ap[j].mL = Dpm, ap[j].eL = Dpe, ap[j].lyL = LY;
-        q_nx = q;
-        g_nx = g;
-    }
+    Wave<R> ws, wp;
+    R LY;
+    Cx<R> q_nx, g_nx;
+    sweep_layers<R, POL>(sa, sb, TL, tl, L, q0sq, ws, wp, LY, q_nx, g_nx,
+                         [](int, const Cx<R> &, const StageB<R> &, const Taken<R> &, const Taken<R> &, R, R) {});
     // interface 0 | 1: the incident amplitude x_0[0]
-    A = sa[tl];
+    const StageA<R> A0 = sa[tl];
     const Cx<R> q0 = {c0, R(0)};
-    const Cx<R> g0 = cmul(q0, Cx<R>{A.in2x, A.in2y});
+    const Cx<R> g0 = cmul(q0, Cx<R>{A0.in2x, A0.in2y});
     R pre[2] = {R(0), R(0)};
     int e0[2] = {0, 0};
     if (POL & 1) {
-        interface_pair(q0, q_nx, s0, s1);
-        dmul_f(Dsm, Dse, R(4) * c0 * c0);
-        pre[0] = Dsm / abs2(s0);
-        e0[0] = Dse;
+        interface_pair(q0, q_nx, ws.x0, ws.x1);
+        dmul_f(ws.m, ws.e, R(4) * c0 * c0);
+        pre[0] = ws.m / abs2(ws.x0);
+        e0[0] = ws.e;
     }
     if (POL & 2) {
-        interface_pair(g0, g_nx, p0, p1);
-        dmul_f(Dpm, Dpe, R(4) * abs2(g0));
-        pre[1] = Dpm / abs2(p0) * n0 * n0;  // the incident E = H / n_0
-        e0[1] = Dpe;
+        interface_pair(g0, g_nx, wp.x0, wp.x1);
+        dmul_f(wp.m, wp.e, R(4) * abs2(g0));
+        pre[1] = wp.m / abs2(wp.x0) * n0 * n0;  // the incident E = H / n_0
+        e0[1] = wp.e;
     }
+    const R LY0 = LY;
     // |rho| of an amplitude taken at (m, e, ly)
     auto rho = [&](int k, R m, int e, R ly) {
-        const R w = ly - LY;  // <= 0
+        const R w = ly - LY0;  // <= 0
         const R wn = floor_w(w);
         return sqrt(ldexp_w(pre[k] / m * exp2_w(w - wn), e0[k] - e + (int)wn));
     };
-    for (int j = 1; j <= L; ++j) {
-        const StageA<R> Aj = sa[j * TL + tl];
-        const StageB<R> Bj = sb[j * TL + tl];
-        const Cx<R> q = forward_root(Cx<R>{Aj.d2x + q0sq, Aj.n2y}, &absz);
+    auto emit = [&](int j, const Cx<R> &q, const StageB<R> &Bj, const Taken<R> &ts, const Taken<R> &tp, R lyR,
+                    R lyL) {
         const R n4 = R(1) / Bj.ain2;  // |n_j|^4
         Cx<R> fa[2], fb[2];
         if (POL & 1) {
-            fa[0] = scale(rho(0, as[j].mL, as[j].eL, as[j].lyL), as[j].aL);
-            fb[0] = scale(rho(0, as[j].mR, as[j].eR, as[j].lyR), as[j].bR);
+            fa[0] = scale(rho(0, ts.m, ts.eL, lyL), ts.aL);
+            fb[0] = scale(rho(0, ts.m, ts.eR, lyR), ts.bR);
         }
         if (POL & 2) {
-            fa[1] = scale(rho(1, ap[j].mL, ap[j].eL, ap[j].lyL), ap[j].aL);
-            fb[1] = scale(rho(1, ap[j].mR, ap[j].eR, ap[j].lyR), ap[j].bR);
+            fa[1] = scale(rho(1, tp.m, tp.eL, lyL), tp.aL);
+            fb[1] = scale(rho(1, tp.m, tp.eR, lyR), tp.bR);
         }
-        for (int kz = 0; kz < n_z; ++kz) {
-            const R f = (R(kz) + R(0.5)) / R(n_z);  // z / d
-            // e^{i kappa z} and e^{i kappa (d - z)} in turns of the layer phase
-            R s1n, c1s, s2n, c2s;
-            const R y1r = Bj.dl * q.x * f, y2r = Bj.dl * q.x * (R(1) - f);
-            sincos_turn(y1r - rint_w(y1r), &s1n, &c1s);
-            sincos_turn(y2r - rint_w(y2r), &s2n, &c2s);
-            const R m1 = sqrt(exp_m2_turn(Bj.dl * q.y * f)), m2 = sqrt(exp_m2_turn(Bj.dl * q.y * (R(1) - f)));
-            const Cx<R> ez = {m1 * c1s, m1 * s1n}, edz = {m2 * c2s, m2 * s2n};
+        // e^{i kappa z_k} (z_k = (k + 1/2) d / n_z) from the layer phase in
+        // turns: modulus e^{-2 pi Im(y) f}, angle 2 pi Re(y) f with f = z / d
+        const R yr = Bj.dl * q.x, yi = Bj.dl * q.y;
+        auto depth_factor = [&](int k) {
+            const R f = (R(k) + R(0.5)) / R(n_z);
+            const R y = yr * f;
+            R sn, cs;
+            sincos_turn(y - rint_w(y), &sn, &cs);
+            const R m = exp_m2_turn(R(0.5) * yi * f);
+            return Cx<R>{m * cs, m * sn};
+        };
+        auto put = [&](int kz, const Cx<R> &ez, const Cx<R> &edz) {
             R v[2] = {R(0), R(0)};
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
@@ -204,8 +240,22 @@ __global__ void __launch_bounds__(kFieldThreads) tmm_field_kernel(const tmm_prob
                 if (POL & 1) store(pi++, j - 1, kz, v[0]);
                 if (POL & 2) store(pi, j - 1, kz, v[1]);
             }
+        };
+        // d - z_k = z_{n_z-1-k}: the backward wave's factor e^{i kappa (d - z)}
+        // at depth k is the forward wave's at depth n_z - 1 - k, so each
+        // factor is computed once and the depths are taken in mirrored pairs
+        for (int k = 0, kb = n_z - 1; k <= kb; ++k, --kb) {
+            const Cx<R> e1 = depth_factor(k);
+            if (k == kb) {
+                put(k, e1, e1);
+            } else {
+                const Cx<R> e2 = depth_factor(kb);
+                put(k, e1, e2);
+                put(kb, e2, e1);
+            }
         }
-    }
+    };
+    sweep_layers<R, POL>(sa, sb, TL, tl, L, q0sq, ws, wp, LY, q_nx, g_nx, emit);
     for (int pi = 0; pi < nplanes; ++pi)
         for (int j = L; j < p.L_max; ++j)
             for (int kz = 0; kz < n_z; ++kz) store(pi, j, kz, R(0));
@@ -217,11 +267,11 @@ size_t field_smem(const tmm_problem *p, int TL)
     return (size_t)(p->L_max + 2) * TL * (6 * r) + (size_t)TL * r;
 }
 
-template <typename R, int POL, int KMAX>
+template <typename R, int POL>
 tmm_status launch_field_k(const tmm_problem *p, int n_z, int TL, int TT, int n_lt, int n_tt, long long items,
                           size_t smem, R *E, cudaStream_t st)
 {
-    auto k = tmm_field_kernel<R, POL, KMAX>;
+    auto k = tmm_field_kernel<R, POL>;
     if (smem > 48 * 1024) {
         static int set_bytes[64] = {};
         int dev = 0;
@@ -238,27 +288,16 @@ tmm_status launch_field_k(const tmm_problem *p, int n_z, int TL, int TT, int n_l
     return check_launch();
 }
 
-template <typename R, int POL>
-tmm_status launch_field_km(const tmm_problem *p, int n_z, int TL, int TT, int n_lt, int n_tt, long long items,
-                           size_t smem, R *E, cudaStream_t st)
-{
-    const int need = p->L_max + 2;
-    if (need <= 18) return launch_field_k<R, POL, 18>(p, n_z, TL, TT, n_lt, n_tt, items, smem, E, st);
-    if (need <= 34) return launch_field_k<R, POL, 34>(p, n_z, TL, TT, n_lt, n_tt, items, smem, E, st);
-    if (need <= 66) return launch_field_k<R, POL, 66>(p, n_z, TL, TT, n_lt, n_tt, items, smem, E, st);
-    return launch_field_k<R, POL, kFieldMaxLayers + 2>(p, n_z, TL, TT, n_lt, n_tt, items, smem, E, st);
-}
-
 template <typename R>
 tmm_status launch_field_prec(const tmm_problem *p, int n_z, int TL, int TT, int n_lt, int n_tt, long long items,
                              size_t smem, void *E_, cudaStream_t st)
 {
     R *E = static_cast<R *>(E_);
     switch (p->pol_mask) {
-    case 1: return launch_field_km<R, 1>(p, n_z, TL, TT, n_lt, n_tt, items, smem, E, st);
-    case 2: return launch_field_km<R, 2>(p, n_z, TL, TT, n_lt, n_tt, items, smem, E, st);
-    case 3: return launch_field_km<R, 3>(p, n_z, TL, TT, n_lt, n_tt, items, smem, E, st);
-    case 7: return launch_field_km<R, 7>(p, n_z, TL, TT, n_lt, n_tt, items, smem, E, st);
+    case 1: return launch_field_k<R, 1>(p, n_z, TL, TT, n_lt, n_tt, items, smem, E, st);
+    case 2: return launch_field_k<R, 2>(p, n_z, TL, TT, n_lt, n_tt, items, smem, E, st);
+    case 3: return launch_field_k<R, 3>(p, n_z, TL, TT, n_lt, n_tt, items, smem, E, st);
+    case 7: return launch_field_k<R, 7>(p, n_z, TL, TT, n_lt, n_tt, items, smem, E, st);
     default: return TMM_ERR_INVALID_ARG;
     }
 }
@@ -274,11 +313,11 @@ extern "C" TMM_API tmm_status tmm_field_profile(const tmm_problem *p, int32_t n_
     tmm_status s = validate_problem(p);
     if (s != TMM_OK) return s;
     if (p->prec == TMM_F64X) return TMM_ERR_UNSUPPORTED;
-    if (p->L_max > kFieldMaxLayers) return TMM_ERR_UNSUPPORTED;
     if (n_z < 1) return TMM_ERR_INVALID_ARG;
     const long long pts = (long long)p->S * p->n_lambda * p->n_theta;
     if (pts == 0 || p->L_max == 0) return TMM_OK;
     if (!E) return TMM_ERR_INVALID_ARG;
+    if (field_smem(p, 1) > kSmemBlockCeiling) return TMM_ERR_UNSUPPORTED;
     DeviceInfo di;
     s = device_info(&di);
     if (s != TMM_OK) return s;

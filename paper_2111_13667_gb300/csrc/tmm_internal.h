@@ -24,6 +24,11 @@ struct DeviceInfo {
 };
 tmm_status device_info(DeviceInfo *out);
 
+// Largest dynamic shared memory a block of these kernels can be given on
+// sm_103a (227 KiB opt-in); a stage larger than this is rejected before any
+// device query.
+constexpr size_t kSmemBlockCeiling = 227 * 1024;
+
 int npol(uint32_t pol_mask);
 size_t real_size(int prec);
 

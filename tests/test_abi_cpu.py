@@ -152,6 +152,10 @@ def test_incoherent_absorption_reward_argument_checks(lib):
     # absorption keeps per-layer records: L_max <= 127
     big = _problem(L_max=200)
     assert lib.tmm_absorption_batched(ctypes.byref(big), fake, None, None, None) == abi.TMM_ERR_UNSUPPORTED
+    # the field profile only stages the stack in shared memory
+    deep = _problem(L_max=100000)
+    assert lib.tmm_field_profile(ctypes.byref(deep), 2, fake, None) == abi.TMM_ERR_UNSUPPORTED
+    assert lib.tmm_field_profile(ctypes.byref(p), 0, fake, None) == abi.TMM_ERR_INVALID_ARG
     # a reward launch has no status channel for an iteration limit
     cfg = abi.launch_cfg(persistent=1, max_items_per_block=3)
     assert lib.tmm_coh_reward(ctypes.byref(p), ctypes.byref(cfg), fake, fake, fake, 1 << 20,

@@ -128,3 +128,15 @@ def test_field_profile_ragged_opaque_and_unpolarised():
     assert E[:, 0, 1, 0].max() < 1e-3 and E[:, 0, 1, 1:].max() < 1e-30
     Eo = np.stack([ab.field_profile(pol, np.repeat(nd[:, :, None], 1, 2), wo.d, wo.theta, wo.lam, 8) for pol in "sp"])
     assert np.max(np.abs(E - Eo)) <= 1e-10
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_deep_stack_profile(prec):
+    # 160 lossy layers: the profile kernel sweeps the stack twice and keeps no
+    # per-layer state, so depth is bounded only by the shared-memory stage
+    w = lossy_workload(55, S=3, L=160, n_lambda=9, n_theta=3)
+    n = oracle_index(w)
+    Eo = np.stack([ab.field_profile(pol, n, w.d, w.theta, w.lam, 3) for pol in "sp"])
+    E = gpu_field(w, prec, 3)
+    rel = np.max(np.abs(E - Eo) / np.maximum(1.0, np.abs(Eo)))
+    assert rel <= (1e-10 if prec == "f64" else 1e-4), rel
