@@ -160,6 +160,79 @@ template <typename R> __device__ __forceinline__ Cx<R> forward_root(Cx<R> z, R *
     return q;
 }
 
+// ---------------------------------------------------------------- paired FP32 lanes
+// sm_100+ issues two FP32 lanes per instruction (fma/mul/add .f32x2) at the
+// scalar lane throughput: arithmetic that two points do alike costs half the
+// issue slots.  A value per lane is a float2, a complex value per lane a C2.
+struct C2 { float2 x, y; };
+
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 neg2(float2 a) { return __fmul2_rn(a, bc2(-1.f)); }
+// a - b, rounded once like the scalar subtraction: a + (-1) b
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, bc2(-1.f), a); }
+__device__ __forceinline__ C2 neg2(C2 a) { return C2{neg2(a.x), neg2(a.y)}; }
+__device__ __forceinline__ Cx<float> lane(const C2 &a, int i) { return i ? Cx<float>{a.x.y, a.y.y} : Cx<float>{a.x.x, a.y.x}; }
+__device__ __forceinline__ C2 pack2(Cx<float> a, Cx<float> b) { return C2{f2(a.x, b.x), f2(a.y, b.y)}; }
+
+// interface_pair per lane: X = k (x0 + x1), Y = k' (x0 - x1), x0 = X + Y,
+// x1 = X - Y.  Paired instructions take no sign modifiers, so the products
+// use carried negatives of the imaginary parts, nky = -Im k, nkny = -Im k'.
+__device__ __forceinline__ void interface_pair2(const C2 &k, float2 nky, const C2 &kn, float2 nkny, C2 &x0, C2 &x1)
+{
+    const C2 sg = {add2(x0.x, x1.x), add2(x0.y, x1.y)};
+    const C2 df = {sub2(x0.x, x1.x), sub2(x0.y, x1.y)};
+    const C2 X = {fma2(k.x, sg.x, mul2(nky, sg.y)), fma2(k.x, sg.y, mul2(k.y, sg.x))};
+    const C2 Y = {fma2(kn.x, df.x, mul2(nkny, df.y)), fma2(kn.x, df.y, mul2(kn.y, df.x))};
+    x0 = C2{add2(X.x, Y.x), add2(X.y, Y.y)};
+    x1 = C2{sub2(X.x, Y.x), sub2(X.y, Y.y)};
+}
+
+// x0 <- (cs - i sn) x0, x1 <- (ec + i es) x1 per lane (the layer phase); nsn,
+// nes the negatives
+__device__ __forceinline__ void phase2(float2 cs, float2 sn, float2 nsn, float2 ec, float2 es, float2 nes, C2 &x0,
+                                       C2 &x1)
+{
+    x0 = C2{fma2(cs, x0.x, mul2(sn, x0.y)), fma2(cs, x0.y, mul2(nsn, x0.x))};
+    x1 = C2{fma2(ec, x1.x, mul2(nes, x1.y)), fma2(ec, x1.y, mul2(es, x1.x))};
+}
+
+// renorm_pair per lane
+__device__ __forceinline__ void renorm_pair2(C2 &x0, C2 &x1, int &ea, int &eb)
+{
+    const float ma = fmaxf(fmaxf(fabsf(x0.x.x), fabsf(x0.y.x)), fmaxf(fabsf(x1.x.x), fabsf(x1.y.x)));
+    const float mb = fmaxf(fmaxf(fabsf(x0.x.y), fabsf(x0.y.y)), fmaxf(fabsf(x1.x.y), fabsf(x1.y.y)));
+    const int ka = exponent_of(ma), kb = exponent_of(mb);
+    const float2 sc = f2(pow2_neg<float>(ka), pow2_neg<float>(kb));
+    x0 = C2{mul2(sc, x0.x), mul2(sc, x0.y)};
+    x1 = C2{mul2(sc, x1.x), mul2(sc, x1.y)};
+    ea += ka;
+    eb += kb;
+}
+
+// forward_root for a finite layer inside the stack.  R and T do not depend on
+// the branch taken there (the sign flips cancel), so the tolerance band of the
+// bounding media is not needed: the root with Im q >= 0 (Im q = 0: Re q of the
+// sign of Im z) keeps the phase clamp and the rescaling bounds valid.  With
+// t = sqrt(u), o = Im z / (2 sqrt(u)), u = (|z| + |Re z|) / 2, that root is
+//   Re z >= 0: (sign(Im z) t, |o|);  Re z < 0: (sign(Im z) |o|, t).
+__device__ __forceinline__ Cx<float> inner_root(Cx<float> z, float *absz_out)
+{
+    const float hyp = fmaf(z.x, z.x, z.y * z.y);
+    const float tiny = min_normal<float>();
+    const float absz = hyp * rsqrtf(fmaxf(hyp, tiny));
+    const float u = 0.5f * (absz + fabsf(z.x));
+    const float ru = rsqrtf(fmaxf(u, tiny));
+    const float t = u * ru;
+    const float ao = fabsf(0.5f * z.y * ru);
+    const bool re_pos = z.x >= 0.f;
+    *absz_out = absz;
+    return Cx<float>{copysignf(re_pos ? t : ao, z.y), re_pos ? ao : t};
+}
+
 // ---------------------------------------------------------------- shared-memory stage
 // Per (medium j, wavelength): n_j^2 - n_0^2 (real part; the imaginary part is
 // that of n_j^2), 1 / n_j^2, |1 / n_j^2|^2 and d_j / lambda (0 for the two

@@ -19,6 +19,7 @@
 
 #include <algorithm>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "tmm_device.cuh"
@@ -28,6 +29,10 @@ namespace tmm {
 
 // Largest block of the forward kernels (threads); keeps 128 registers per thread.
 constexpr int kMaxThreads = 512;
+// Paired-lane (two angles per thread) instances: at most 256 threads, compiled
+// for three resident blocks per SM (<= 85 registers, 24 warps).
+constexpr int kPairThreads = 256;
+constexpr int kPairBlocks = 3;
 
 // One (lambda, theta) point of one stack, both polarisations as requested:
 // out = {R_s, T_s, R_p, T_p}.
@@ -87,6 +92,51 @@ __device__ __forceinline__ void layer_step(const StageA<R> *__restrict__ sa, con
     w.q_nx = q;
 }
 
+// Interface 0 | 1 and Eqs. 5-6 for one point, from the sweep's state after
+// layer 1: scaled pairs, |q|^2 product Ps0 (exponent eP), sum Y of Im delta /
+// (2 pi), p index product Pp (exponent ePp), pair exponents es, ep.
+template <typename R, int POL>
+__device__ __forceinline__ void finish_point(const StageA<R> &A, Cx<R> q_out, Cx<R> n2_out, Cx<R> q_nx, Cx<R> g_nx,
+                                             Cx<R> s0, Cx<R> s1, Cx<R> p0, Cx<R> p1, R Ps0, R Y, R Pp, int eP,
+                                             int ePp, int es, int ep, int L, R n0, R beta, R c0, R out[4])
+{
+    // interface 0 -> 1; the injection medium is real, so q_0 = n_0 cos(theta)
+    // (computed directly: n_0^2 - beta^2 cancels near grazing incidence)
+    const bool grazing = beta >= n0;  // false for a NaN (complex, rejected) n_0
+    const Cx<R> q0 = {c0, R(0)};
+    const R Ps = Ps0 * (q0.x * q0.x);
+    const int e4 = 2 * (L + 1);  // the factors 2 of every 2a
+    // 2^{-2 K Y} = 2^{yf} 2^{yn}, yn integer
+    R u = R(-2.0 * kTwoPi * kLog2e) * Y;
+    u = fmax(u, R(-1.0e6));
+    const R un = floor_w(u);
+    const R yscale = exp2_w(u - un);
+    const int yn = (int)un;
+    if (POL & 1) {
+        Cx<R> x0 = s0, x1 = s1;
+        interface_pair(q0, q_nx, x0, x1);
+        const R ax0 = abs2(x0);
+        R Rv = abs2(x1) / ax0;
+        R Tv = q_out.x / q0.x * ldexp_w(Ps * yscale / ax0, e4 + eP + yn - 2 * es);
+        if (grazing) { Rv = R(1); Tv = R(0); }
+        out[0] = Rv;
+        out[1] = Tv;
+    }
+    if (POL & 2) {
+        const Cx<R> g0 = cmul(q0, Cx<R>{A.in2x, A.in2y});
+        Cx<R> x0 = p0, x1 = p1;
+        interface_pair(g0, g_nx, x0, x1);
+        const R ax0 = abs2(x0);
+        R Rv = abs2(x1) / ax0;
+        const R num = cmul(n2_out, conj(q_out)).x;
+        const R den = n0 * n0 * q0.x;
+        R Tv = num / den * ldexp_w(Ps * Pp * yscale / ax0, e4 + eP + ePp + yn - 2 * ep);
+        if (grazing) { Rv = R(1); Tv = R(0); }
+        out[2] = Rv;
+        out[3] = Tv;
+    }
+}
+
 // Evaluate one (lambda, theta) point: right-to-left product (Eq. 4) applied to
 // the vector (1, 0) of the exit medium, then r, t (Eqs. 5-6) and R, T.
 template <typename R, int POL>
@@ -136,44 +186,8 @@ __device__ __forceinline__ void eval_point(const StageA<R> *__restrict__ sa, con
         if (POL & 2) renorm_pair(w.p0, w.p1, ep);
     }
     for (; j >= 1; --j) layer_step<R, POL>(sa, sb, TL, tl, j, q0sq, yi_max, w);
-    const Cx<R> q_nx = w.q_nx, g_nx = w.g_nx;
-    const R Ps0 = w.Ps, Y = w.Y;
-// interface 0 -> 1; the injection medium is real, so q_0 = n_0 cos(theta)
-    // (computed directly: n_0^2 - beta^2 cancels near grazing incidence)
-    A = sa[tl];
-    const bool grazing = beta >= n0;  // false for a NaN (complex, rejected) n_0
-    const Cx<R> q0 = {c0, R(0)};
-    const R Ps = Ps0 * (q0.x * q0.x);
-    const int e4 = 2 * (L + 1);  // the factors 2 of every 2a
-    // 2^{-2 K Y} = 2^{yf} 2^{yn}, yn integer
-    R u = R(-2.0 * kTwoPi * kLog2e) * Y;
-    u = fmax(u, R(-1.0e6));
-    const R un = floor_w(u);
-    const R yscale = exp2_w(u - un);
-    const int yn = (int)un;
-    if (POL & 1) {
-        Cx<R> x0 = w.s0, x1 = w.s1;
-        interface_pair(q0, q_nx, x0, x1);
-        const R ax0 = abs2(x0);
-        R Rv = abs2(x1) / ax0;
-        R Tv = q_out.x / q0.x * ldexp_w(Ps * yscale / ax0, e4 + eP + yn - 2 * es);
-        if (grazing) { Rv = R(1); Tv = R(0); }
-        out[0] = Rv;
-        out[1] = Tv;
-    }
-    if (POL & 2) {
-        const Cx<R> g0 = cmul(q0, Cx<R>{A.in2x, A.in2y});
-        Cx<R> x0 = w.p0, x1 = w.p1;
-        interface_pair(g0, g_nx, x0, x1);
-        const R ax0 = abs2(x0);
-        R Rv = abs2(x1) / ax0;
-        const R num = cmul(n2_out, conj(q_out)).x;
-        const R den = n0 * n0 * q0.x;
-        R Tv = num / den * ldexp_w(Ps * w.Pp * yscale / ax0, e4 + eP + ePp + yn - 2 * ep);
-        if (grazing) { Rv = R(1); Tv = R(0); }
-        out[2] = Rv;
-        out[3] = Tv;
-    }
+    finish_point<R, POL>(sa[tl], q_out, n2_out, w.q_nx, w.g_nx, w.s0, w.s1, w.p0, w.p1, w.Ps, w.Y, w.Pp, eP, ePp, es,
+                         ep, L, n0, beta, c0, out);
 }
 
 // Reduction mode (tmm_coh_reward): with Rt set, a work item writes no R, T
@@ -258,8 +272,223 @@ __device__ __forceinline__ void run_item(const tmm_problem &p, int s, int lt, in
     __syncthreads();
 }
 
-template <typename R, int POL, bool WITH_T, bool RED>
-__global__ void __launch_bounds__(kMaxThreads) tmm_fwd_kernel(const tmm_problem p, int TL, int TT, int n_lt, int n_tt,
+// ---------------------------------------------------------------- FP32: two angles per thread
+// An FP32 thread carries two angles of one wavelength on the two lanes of the
+// paired instructions: the amplitude pairs, |q|^2 products and phase sums are
+// float2 per component; the stage (per medium and wavelength) and the p index
+// product are shared.  Roots, sin/cos and exp2 stay per lane (one MUFU each).
+// The arithmetic is the scalar path's up to the order of two additions per
+// interface and the branch of q inside the stack, which R and T do not see.
+struct Sweep2 {
+    C2 q_nx, g_nx;        // q and q / n^2 of the medium to the right
+    float2 nqy_nx, ngy_nx;  // minus their imaginary parts
+    C2 s0, s1, p0, p1;
+    float2 Ps, Y;
+    float Pp;
+};
+
+template <int POL>
+__device__ __forceinline__ void layer_step2(const StageA<float> *__restrict__ sa, const StageB<float> *__restrict__ sb,
+                                            int TL, int tl, int j, float2 q0sq, float yi_max, Sweep2 &w)
+{
+    const StageA<float> A = sa[j * TL + tl];
+    const StageB<float> B = sb[j * TL + tl];
+    float absa, absb;
+    const Cx<float> qa = inner_root(Cx<float>{A.d2x + q0sq.x, A.n2y}, &absa);
+    const Cx<float> qb = inner_root(Cx<float>{A.d2x + q0sq.y, A.n2y}, &absb);
+    w.Ps = mul2(w.Ps, f2(absa, absb));
+    const float yra = B.dl * qa.x, yrb = B.dl * qb.x;
+    const float2 yi = f2(fminf(B.dl * qa.y, yi_max), fminf(B.dl * qb.y, yi_max));
+    w.Y = add2(w.Y, yi);
+    float2 sn, cs;
+    sincos_turn(yra - rintf(yra), &sn.x, &cs.x);
+    sincos_turn(yrb - rintf(yrb), &sn.y, &cs.y);
+    const float2 E2 = f2(exp_m2_turn(yi.x), exp_m2_turn(yi.y));
+    const float2 nsn = neg2(sn), ec = mul2(E2, cs), es = mul2(E2, sn), nes = neg2(es);
+    if (POL & 1) {
+        const C2 q = pack2(qa, qb);
+        const float2 nqy = neg2(q.y);
+        interface_pair2(q, nqy, w.q_nx, w.nqy_nx, w.s0, w.s1);
+        phase2(cs, sn, nsn, ec, es, nes, w.s0, w.s1);
+        w.q_nx = q;
+        w.nqy_nx = nqy;
+    }
+    if (POL & 2) {
+        w.Pp *= B.ain2;
+        const Cx<float> in2 = {A.in2x, A.in2y};
+        const C2 g = pack2(cmul(qa, in2), cmul(qb, in2));
+        const float2 ngy = neg2(g.y);
+        interface_pair2(g, ngy, w.g_nx, w.ngy_nx, w.p0, w.p1);
+        phase2(cs, sn, nsn, ec, es, nes, w.p0, w.p1);
+        w.g_nx = g;
+        w.ngy_nx = ngy;
+    }
+}
+
+// eval_point for the angles with (sin, cos) in the lanes of st, ct:
+// out[i] = {R_s, T_s, R_p, T_p} of lane i.
+template <int POL>
+__device__ __forceinline__ void eval_point2(const StageA<float> *__restrict__ sa, const StageB<float> *__restrict__ sb,
+                                            int TL, int tl, int L, float n0, float2 st, float2 ct, float out[2][4])
+{
+    constexpr int RN = RenormEvery<float>::value;
+    const float2 beta = f2(n0 * st.x, n0 * st.y), c0 = f2(n0 * ct.x, n0 * ct.y);
+    const float2 q0sq = f2(c0.x * c0.x, c0.y * c0.y);
+    const float yi_max = float(kImDeltaMax / kTwoPi);
+
+    const StageA<float> A = sa[(L + 1) * TL + tl];
+    float absz;
+    const Cx<float> qoa = forward_root(Cx<float>{A.d2x + q0sq.x, A.n2y}, &absz);
+    const Cx<float> qob = forward_root(Cx<float>{A.d2x + q0sq.y, A.n2y}, &absz);
+    const Cx<float> n2_out = {A.d2x + n0 * n0, A.n2y};
+    const Cx<float> in2 = {A.in2x, A.in2y};
+    Sweep2 w;
+    w.q_nx = pack2(qoa, qob);
+    w.nqy_nx = neg2(w.q_nx.y);
+    w.g_nx = pack2(cmul(qoa, in2), cmul(qob, in2));
+    w.ngy_nx = neg2(w.g_nx.y);
+    w.Ps = bc2(1.f);
+    w.Y = bc2(0.f);
+    w.Pp = (POL & 2) ? sb[(L + 1) * TL + tl].ain2 : 1.f;
+    int ePa = 0, ePb = 0, ePp = 0;
+    w.s0 = C2{bc2(1.f), bc2(0.f)};
+    w.s1 = C2{bc2(0.f), bc2(0.f)};
+    w.p0 = w.s0;
+    w.p1 = w.s1;
+    int esa = 0, esb = 0, epa = 0, epb = 0;
+
+    // the scalar kernel's grouping: RN layers, rescale the pairs, RN more,
+    // rescale the products and the pairs
+    int j = L;
+    for (; j >= 2 * RN; j -= 2 * RN) {
+#pragma unroll
+        for (int k = 0; k < RN; ++k) layer_step2<POL>(sa, sb, TL, tl, j - k, q0sq, yi_max, w);
+        if (POL & 1) renorm_pair2(w.s0, w.s1, esa, esb);
+        if (POL & 2) renorm_pair2(w.p0, w.p1, epa, epb);
+#pragma unroll
+        for (int k = RN; k < 2 * RN; ++k) layer_step2<POL>(sa, sb, TL, tl, j - k, q0sq, yi_max, w);
+        renorm_scalar(w.Ps.x, ePa);
+        renorm_scalar(w.Ps.y, ePb);
+        if (POL & 2) renorm_scalar(w.Pp, ePp);
+        if (POL & 1) renorm_pair2(w.s0, w.s1, esa, esb);
+        if (POL & 2) renorm_pair2(w.p0, w.p1, epa, epb);
+    }
+    for (; j >= RN; j -= RN) {
+#pragma unroll
+        for (int k = 0; k < RN; ++k) layer_step2<POL>(sa, sb, TL, tl, j - k, q0sq, yi_max, w);
+        renorm_scalar(w.Ps.x, ePa);
+        renorm_scalar(w.Ps.y, ePb);
+        if (POL & 2) renorm_scalar(w.Pp, ePp);
+        if (POL & 1) renorm_pair2(w.s0, w.s1, esa, esb);
+        if (POL & 2) renorm_pair2(w.p0, w.p1, epa, epb);
+    }
+    for (; j >= 1; --j) layer_step2<POL>(sa, sb, TL, tl, j, q0sq, yi_max, w);
+    finish_point<float, POL>(sa[tl], qoa, n2_out, lane(w.q_nx, 0), lane(w.g_nx, 0), lane(w.s0, 0), lane(w.s1, 0),
+                             lane(w.p0, 0), lane(w.p1, 0), w.Ps.x, w.Y.x, w.Pp, ePa, ePp, esa, epa, L, n0, beta.x,
+                             c0.x, out[0]);
+    finish_point<float, POL>(sa[tl], qob, n2_out, lane(w.q_nx, 1), lane(w.g_nx, 1), lane(w.s0, 1), lane(w.s1, 1),
+                             lane(w.p0, 1), lane(w.p1, 1), w.Ps.y, w.Y.y, w.Pp, ePb, ePp, esb, epb, L, n0, beta.y,
+                             c0.y, out[1]);
+}
+
+// run_item for FP32 with two angles per thread: the block is TL x ceil(TT/2)
+// threads, thread (x, y) taking angles t0 + 2y and t0 + 2y + 1.
+template <int POL, bool WITH_T, bool RED>
+__device__ __forceinline__ void run_item2(const tmm_problem &p, int s, int lt, int tt, int n_tt, int TL, int TT,
+                                          unsigned char *smem, float *__restrict__ Rout, float *__restrict__ Tout,
+                                          const Reduce<float> &red)
+{
+    StageA<float> *sa = reinterpret_cast<StageA<float> *>(smem);
+    StageB<float> *sb = reinterpret_cast<StageB<float> *>(sa + (size_t)(p.L_max + 2) * TL);
+    float *n0s = reinterpret_cast<float *>(sb + (size_t)(p.L_max + 2) * TL);
+
+    const int tid = threadIdx.y * TL + threadIdx.x;
+    const int nthr = TL * (int)blockDim.y;
+    const int L = layers_of(p, s);
+    const int l0 = lt * TL, t0 = tt * TT;
+    if (L >= 0) fill_stage<float>(p, s, L, l0, TL, sa, sb, n0s, tid, nthr);
+    __syncthreads();
+
+    const int tl = threadIdx.x, l = l0 + tl;
+    const int a0 = t0 + 2 * (int)threadIdx.y, t_end = min(t0 + TT, p.n_theta);
+    const bool v1 = a0 + 1 < t_end;
+    float contrib = 0.f;
+    if (l < p.n_lambda && a0 < t_end) {
+        float out[2][4];
+        if (L >= 0) {
+            const float *th = (const float *)p.theta;
+            float2 st, ct;
+            sincos_w(th[a0], &st.x, &ct.x);
+            sincos_w(th[v1 ? a0 + 1 : a0], &st.y, &ct.y);
+            eval_point2<POL>(sa, sb, TL, tl, L, n0s[tl], st, ct, out);
+        } else {
+#pragma unroll
+            for (int i = 0; i < 2; ++i) out[i][0] = out[i][1] = out[i][2] = out[i][3] = nan_w<float>();
+        }
+        const long long tplane = (long long)p.n_theta * p.n_lambda;
+        const long long plane = (long long)p.S * tplane;
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            if (i == 1 && !v1) break;
+            const int a = a0 + i;
+            if (RED) {
+                const long long ot = (long long)a * p.n_lambda + l;
+                if (POL & 4) {
+                    contrib += fabsf(red.Rt[ot] - 0.5f * (out[i][0] + out[i][2]));
+                } else {
+                    int pi = 0;
+                    if (POL & 1) contrib += fabsf(red.Rt[ot] - out[i][0]), ++pi;
+                    if (POL & 2) contrib += fabsf(red.Rt[pi * tplane + ot] - out[i][2]);
+                }
+            } else {
+                const long long o = ((long long)s * p.n_theta + a) * p.n_lambda + l;
+                int pi = 0;
+                if (POL & 4) {
+                    Rout[o] = 0.5f * (out[i][0] + out[i][2]);
+                    if (WITH_T) Tout[o] = 0.5f * (out[i][1] + out[i][3]);
+                } else if (POL & 1) {
+                    Rout[o] = out[i][0];
+                    if (WITH_T) Tout[o] = out[i][1];
+                    ++pi;
+                }
+                if ((POL & 2) && !(POL & 4)) {
+                    Rout[pi * plane + o] = out[i][2];
+                    if (WITH_T) Tout[pi * plane + o] = out[i][3];
+                }
+            }
+        }
+    }
+    if (RED) {
+        // fixed-order tree sum over the block (the stage is no longer read)
+        __syncthreads();
+        float *buf = reinterpret_cast<float *>(smem);
+        buf[tid] = contrib;
+        __syncthreads();
+        int half = 1;
+        while (half < nthr) half <<= 1;
+        for (half >>= 1; half > 0; half >>= 1) {
+            if (tid < half && tid + half < nthr) buf[tid] += buf[tid + half];
+            __syncthreads();
+        }
+        if (tid == 0) red.partial[(long long)s * red.n_tiles + lt * n_tt + tt] = buf[0];
+    }
+    __syncthreads();
+}
+
+// The item evaluator of a kernel instance: paired lanes (FP32 only) or scalar.
+template <typename R, int POL, bool WITH_T, bool RED, bool PAIR>
+__device__ __forceinline__ void run_any(const tmm_problem &p, int s, int lt, int tt, int n_tt, int TL, int TT,
+                                        unsigned char *smem, R *__restrict__ Rout, R *__restrict__ Tout,
+                                        const Reduce<R> &red)
+{
+    if constexpr (PAIR)
+        run_item2<POL, WITH_T, RED>(p, s, lt, tt, n_tt, TL, TT, smem, Rout, Tout, red);
+    else
+        run_item<R, POL, WITH_T, RED>(p, s, lt, tt, n_tt, TL, TT, smem, Rout, Tout, red);
+}
+
+template <typename R, int POL, bool WITH_T, bool RED, bool PAIR>
+__global__ void __launch_bounds__(PAIR ? kPairThreads : kMaxThreads, PAIR ? kPairBlocks : 1) tmm_fwd_kernel(const tmm_problem p, int TL, int TT, int n_lt, int n_tt,
                                                        R *__restrict__ Rout, R *__restrict__ Tout, const Reduce<R> red)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -267,13 +496,13 @@ __global__ void __launch_bounds__(kMaxThreads) tmm_fwd_kernel(const tmm_problem 
     const int per_stack = n_lt * n_tt;
     const int s = (int)(item / per_stack);
     const int r = (int)(item - (long long)s * per_stack);
-    run_item<R, POL, WITH_T, RED>(p, s, r / n_tt, r % n_tt, n_tt, TL, TT, smem, Rout, Tout, red);
+    run_any<R, POL, WITH_T, RED, PAIR>(p, s, r / n_tt, r % n_tt, n_tt, TL, TT, smem, Rout, Tout, red);
 }
 
 // Persistent variant: blocks pull work items from `counter`; item k belongs to
 // stack order[k / per_stack] (longest stacks first), tile k % per_stack.
-template <typename R, int POL, bool WITH_T, bool RED>
-__global__ void __launch_bounds__(kMaxThreads) tmm_fwd_persistent(const tmm_problem p, int TL, int TT, int n_lt, int n_tt,
+template <typename R, int POL, bool WITH_T, bool RED, bool PAIR>
+__global__ void __launch_bounds__(PAIR ? kPairThreads : kMaxThreads, PAIR ? kPairBlocks : 1) tmm_fwd_persistent(const tmm_problem p, int TL, int TT, int n_lt, int n_tt,
                                                            const int *__restrict__ order, unsigned int *counter,
                                                            int *err, unsigned int n_items, int max_items,
                                                            R *__restrict__ Rout, R *__restrict__ Tout,
@@ -295,7 +524,7 @@ __global__ void __launch_bounds__(kMaxThreads) tmm_fwd_persistent(const tmm_prob
         }
         const int k = (int)(item / per_stack);
         const int r = (int)(item - (unsigned int)k * per_stack);
-        run_item<R, POL, WITH_T, RED>(p, order[k], r / n_tt, r % n_tt, n_tt, TL, TT, smem, Rout, Tout, red);
+        run_any<R, POL, WITH_T, RED, PAIR>(p, order[k], r / n_tt, r % n_tt, n_tt, TL, TT, smem, Rout, Tout, red);
     }
 }
 
@@ -356,6 +585,12 @@ static size_t stage_bytes(const tmm_problem *p, int TL)
     return (size_t)(p->L_max + 2) * TL * (6 * r) + (size_t)TL * r;
 }
 
+// FP32 tiles of two or more angles run two angles per thread (paired lanes).
+static bool paired(const tmm_problem *p, int TT) { return p->prec == TMM_F32 && TT >= 2; }
+
+static int tile_threads(const tmm_problem *p, int TL, int TT) { return TL * (paired(p, TT) ? (TT + 1) / 2 : TT); }
+static int max_threads(const tmm_problem *p, int TT) { return paired(p, TT) ? kPairThreads : kMaxThreads; }
+
 tmm_status choose_tile(const tmm_problem *p, const tmm_launch_cfg *cfg, Tile *t)
 {
     DeviceInfo di;
@@ -363,13 +598,14 @@ tmm_status choose_tile(const tmm_problem *p, const tmm_launch_cfg *cfg, Tile *t)
     if (st != TMM_OK) return st;
     int TT = cfg && cfg->tile_theta > 0 ? cfg->tile_theta : std::min(p->n_theta, 32);
     int TL = cfg && cfg->tile_lambda > 0 ? cfg->tile_lambda : 0;
+    if (TT < 1 || TL < 0) return TMM_ERR_INVALID_ARG;
     if (TL == 0) {
         TL = 1;
-        while (TL * TT < 256 && TL * 2 * TT <= kMaxThreads) TL *= 2;
+        while (tile_threads(p, TL, TT) < 256 && tile_threads(p, 2 * TL, TT) <= max_threads(p, TT)) TL *= 2;
         while (TL > 1 && TL / 2 >= p->n_lambda) TL /= 2;
         while (TL > 1 && stage_bytes(p, TL) > (size_t)di.max_smem_optin) TL /= 2;
     }
-    if (TL < 1 || TT < 1 || TL * TT > kMaxThreads) return TMM_ERR_INVALID_ARG;
+    if (TL < 1 || tile_threads(p, TL, TT) > max_threads(p, TT)) return TMM_ERR_INVALID_ARG;
     t->TL = TL;
     t->TT = TT;
     t->n_lt = (p->n_lambda + TL - 1) / TL;
@@ -422,24 +658,25 @@ static tmm_status prepare_kernel(Kernel k, int threads, size_t smem, bool need_o
     return TMM_OK;
 }
 
-template <typename R, int POL, bool WITH_T, bool RED>
-static tmm_status launch_typed(const tmm_problem *p, const tmm_launch_cfg *cfg, const Tile &t, void *ws,
-                               R *Rout, R *Tout, const Reduce<R> &red, cudaStream_t st)
+template <typename R, int POL, bool WITH_T, bool RED, bool PAIR>
+static tmm_status launch_shaped(const tmm_problem *p, const tmm_launch_cfg *cfg, const Tile &t, void *ws,
+                                R *Rout, R *Tout, const Reduce<R> &red, cudaStream_t st)
 {
-    const dim3 block(t.TL, t.TT);
+    const dim3 block(t.TL, PAIR ? (t.TT + 1) / 2 : t.TT);
+    const int threads = (int)(block.x * block.y);
     const bool persistent = cfg && cfg->persistent;
     if (!persistent) {
-        auto k = tmm_fwd_kernel<R, POL, WITH_T, RED>;
-        tmm_status s = prepare_kernel(k, t.TL * t.TT, t.smem, false, nullptr);
+        auto k = tmm_fwd_kernel<R, POL, WITH_T, RED, PAIR>;
+        tmm_status s = prepare_kernel(k, threads, t.smem, false, nullptr);
         if (s != TMM_OK) return s;
         if (t.n_items > 0x7fffffffLL) return TMM_ERR_UNSUPPORTED;
         if (t.n_items == 0) return TMM_OK;
         k<<<(unsigned)t.n_items, block, t.smem, st>>>(*p, t.TL, t.TT, t.n_lt, t.n_tt, Rout, Tout, red);
         return check_launch();
     }
-    auto k = tmm_fwd_persistent<R, POL, WITH_T, RED>;
+    auto k = tmm_fwd_persistent<R, POL, WITH_T, RED, PAIR>;
     int occ = 0;
-    tmm_status s = prepare_kernel(k, t.TL * t.TT, t.smem, true, &occ);
+    tmm_status s = prepare_kernel(k, threads, t.smem, true, &occ);
     if (s != TMM_OK) return s;
     if (t.n_items > 0xffffffffLL) return TMM_ERR_UNSUPPORTED;
     const PersistentWs w = persistent_ws_layout(p);
@@ -473,6 +710,16 @@ static tmm_status launch_typed(const tmm_problem *p, const tmm_launch_cfg *cfg, 
                                              reinterpret_cast<int *>(base + w.err), (unsigned)t.n_items,
                                              cfg->max_items_per_block, Rout, Tout, red);
     return check_launch();
+}
+
+template <typename R, int POL, bool WITH_T, bool RED>
+static tmm_status launch_typed(const tmm_problem *p, const tmm_launch_cfg *cfg, const Tile &t, void *ws,
+                               R *Rout, R *Tout, const Reduce<R> &red, cudaStream_t st)
+{
+    if constexpr (std::is_same<R, float>::value) {
+        if (paired(p, t.TT)) return launch_shaped<R, POL, WITH_T, RED, true>(p, cfg, t, ws, Rout, Tout, red, st);
+    }
+    return launch_shaped<R, POL, WITH_T, RED, false>(p, cfg, t, ws, Rout, Tout, red, st);
 }
 
 template <typename R>
