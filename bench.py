@@ -37,10 +37,14 @@ FLUSH_BYTES = 512 * 1024 * 1024
 # shared) and the vector update (6 complex products + 2 adds): 88 per layer,
 # about 2.2 kflop per eval over the 25 interfaces of the dispersive workload.
 FLOPS_PER_EVAL_INTERFACE = 88.0
-# What this kernel executes per (eval, interface) with unnormalised interfaces
-# (no complex division), both polarisations sharing root and phase: shared 21
-# (n^2 - beta^2, root, phase, |q|^2 product), s 44, p 51 -> 116 / 2 pols.
-EXECUTED_FLOPS_PER_EVAL_INTERFACE = 58.0
+# What the kernels execute per (eval, interface) with unnormalised interfaces
+# (no complex division), both polarisations sharing root and phase.  FP32
+# (two angles per thread on paired lanes): shared 21 (n^2 - beta^2, root,
+# phase arguments and factors, |q|^2 product, two sign flips), s 39 (a sign
+# flip, interface 24, phase 12, rescaling 2), p 45.5 (q / n^2 6, the p index
+# product 0.5, the rest as s) -> 105.5 / 2 pols.  FP64 and double-float (one
+# point per thread, tolerance-band root): shared 21, s 44, p 51 -> 116 / 2.
+EXECUTED_FLOPS_PER_EVAL_INTERFACE = {"f32": 52.75, "f64": 58.0, "f64x": 58.0}
 # Unit-count peaks (152 SMs, max SM clock 2070 MHz): FP32 128 FMA lanes / SM;
 # FP64 from the nominal 1.25 TFLOP/s of the part.
 SMS = 152
@@ -219,7 +223,7 @@ def gpu_arm(args):
         flops = FLOPS_PER_EVAL_INTERFACE * interfaces * evals
         achieved = flops / (ms * 1e-3)
         peak = PEAK_F32_FLOPS if prec == "f32" else PEAK_F64_FLOPS
-        key = {"f32": "tmm_fwd_kernel<float,3,true>", "f64": "tmm_fwd_kernel<double,3,true>",
+        key = {"f32": "tmm_fwd_kernel<float,3,true,false,true>", "f64": "tmm_fwd_kernel<double,3,true,false,false>",
                "f64x": "tmm_fwd_df64_kernel<3,true>"}[prec]
         entry = {"value": value, "ms_per_step": ms, "steps": steps, "warmup": warmup, "wall_s": wall,
                  "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
@@ -229,7 +233,7 @@ def gpu_arm(args):
                               "work": f"{FLOPS_PER_EVAL_INTERFACE:g} flop per eval-interface x {interfaces} "
                                       f"interfaces x {evals} evals (standard count of the vector-sweep "
                                       f"method)",
-                              "executed_frac": achieved / peak * EXECUTED_FLOPS_PER_EVAL_INTERFACE
+                              "executed_frac": achieved / peak * EXECUTED_FLOPS_PER_EVAL_INTERFACE[prec]
                               / FLOPS_PER_EVAL_INTERFACE}}
         try:
             f, pms = abi.tmm_probe_fma_rate(abi.TMM_F64 if prec == "f64" else abi.TMM_F32)
