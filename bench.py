@@ -255,7 +255,7 @@ def gpu_arm(args):
             hT = torch.empty(T.shape, dtype=T.dtype).pin_memory()
             del R, T
             torch.cuda.empty_cache()
-            pipe = HostPipeline(prob, n_chunks=16)
+            pipe = HostPipeline(prob)
 
             def e2e_step():
                 pipe.run(h_in, hR, hT)
