@@ -108,7 +108,10 @@ __device__ __forceinline__ void fill_stage_grad(const tmm_problem &p, int s, int
 template <typename R> struct GradMinBlocks { static constexpr int value = 2; };
 template <> struct GradMinBlocks<float> { static constexpr int value = 4; };
 
-template <typename R, int KMAX>
+// WITH_DN = false (dm_dn not requested, as in the thickness optimiser) leaves
+// out the index terms: the root derivatives, three products per polarisation
+// and one warp sum per layer.
+template <typename R, int KMAX, bool WITH_DN>
 __global__ void __launch_bounds__(kGradThreads, GradMinBlocks<R>::value) tmm_grad_kernel(const tmm_problem p, const R *__restrict__ Rt,
                                                                 int TL, int TT, int n_lt, int n_tt, int G, R inv_N,
                                                                 R *__restrict__ merit, R *__restrict__ dm_dd,
@@ -236,7 +239,7 @@ __global__ void __launch_bounds__(kGradThreads, GradMinBlocks<R>::value) tmm_gra
 
         // ---- 3. left-to-right cotangent sweep
         // cur = medium j, nx = medium j+1 (with n-derivatives when it is a layer)
-        nx = medium_at(sa[1 * TL + tl], sn[1 * TL + tl], q0sq, L >= 1);
+        nx = medium_at(sa[1 * TL + tl], sn[1 * TL + tl], q0sq, WITH_DN && L >= 1);
         R dn_carry = R(0);  // right-side F term for layer j+1, from step j
         XState<R> Xc = X[1];  // the state of the current layer (x_j); unused at j = 0
         for (int j = 0; j <= L; ++j) {
@@ -256,7 +259,7 @@ __global__ void __launch_bounds__(kGradThreads, GradMinBlocks<R>::value) tmm_gra
                 epi = Cx<R>{E2 * cs, E2 * sn_};
                 // d delta / d d = 2 pi q / lambda; d delta / d n = 2 pi (d/lambda) n / q
                 ddel_d = scale(two_pi_inv_lam, cur.q);
-                ddel_n = scale(R(kTwoPi) * B.dl, cur.dq);
+                if (WITH_DN) ddel_n = scale(R(kTwoPi) * B.dl, cur.dq);
                 if (clamped) {
                     ddel_d.y = R(0);
                     ddel_n.y = R(0);
@@ -271,10 +274,13 @@ __global__ void __launch_bounds__(kGradThreads, GradMinBlocks<R>::value) tmm_gra
                     const R sc_a = pow2_w<R>(ews + Xc.es);
                     const Cx<R> D = mul_i(cmul(ws1, Xc.s1) - cmul(ws0, Xc.s0));
                     dd += R(2) * cmul(D, ddel_d).x * sc_a;
-                    dn += R(2) * cmul(D, ddel_n).x * sc_a;
-                    dn += R(2) * cmul(cmul(v0 + v1, Xn.s0 + Xn.s1), cur.dq).x * sc_b;
+                    if (WITH_DN) {
+                        dn += R(2) * cmul(D, ddel_n).x * sc_a;
+                        dn += R(2) * cmul(cmul(v0 + v1, Xn.s0 + Xn.s1), cur.dq).x * sc_b;
+                    }
                 }
-                if (j + 1 <= L) dn_carry += R(2) * cmul(cmul(v0 - v1, Xn.s0 - Xn.s1), nx.dq).x * sc_b;
+                if (WITH_DN && j + 1 <= L)
+                    dn_carry += R(2) * cmul(cmul(v0 - v1, Xn.s0 - Xn.s1), nx.dq).x * sc_b;
                 // (ws0, ws1) <- (v0 a + v1 b, v0 b + v1 a), a, b = q_j +- q_{j+1}
                 ws0 = v0, ws1 = v1;
                 interface_pair(cur.q, nx.q, ws0, ws1);
@@ -287,26 +293,29 @@ __global__ void __launch_bounds__(kGradThreads, GradMinBlocks<R>::value) tmm_gra
                     const R sc_a = pow2_w<R>(ewp + Xc.ep);
                     const Cx<R> D = mul_i(cmul(wp1, Xc.p1) - cmul(wp0, Xc.p0));
                     dd += R(2) * cmul(D, ddel_d).x * sc_a;
-                    dn += R(2) * cmul(D, ddel_n).x * sc_a;
-                    dn += R(2) * cmul(cmul(v0 + v1, Xn.p0 + Xn.p1), cur.dap).x * sc_b;
+                    if (WITH_DN) {
+                        dn += R(2) * cmul(D, ddel_n).x * sc_a;
+                        dn += R(2) * cmul(cmul(v0 + v1, Xn.p0 + Xn.p1), cur.dap).x * sc_b;
+                    }
                 }
-                if (j + 1 <= L) dn_carry += R(2) * cmul(cmul(v0 - v1, Xn.p0 - Xn.p1), nx.dap).x * sc_b;
+                if (WITH_DN && j + 1 <= L)
+                    dn_carry += R(2) * cmul(cmul(v0 - v1, Xn.p0 - Xn.p1), nx.dap).x * sc_b;
                 wp0 = v0, wp1 = v1;
                 interface_pair(cur.ap, nx.ap, wp0, wp1);
                 if (rn) renorm_pair(wp0, wp1, ewp);
             }
             if (j >= 1) {
                 dd = warp_sum(active ? dd : R(0));
-                dn = warp_sum(active ? dn : R(0));
+                if (WITH_DN) dn = warp_sum(active ? dn : R(0));
                 if (lane == 0) {
                     acc[warp * NP + (j - 1)] += dd;
-                    acc[warp * NP + p.L_max + (j - 1)] += dn;
+                    if (WITH_DN) acc[warp * NP + p.L_max + (j - 1)] += dn;
                 }
             }
             if (j + 1 <= L) {
                 cur = nx;
                 const int jn = j + 2;
-                nx = medium_at(sa[jn * TL + tl], sn[jn * TL + tl], q0sq, jn <= L);
+                nx = medium_at(sa[jn * TL + tl], sn[jn * TL + tl], q0sq, WITH_DN && jn <= L);
             }
             Xc = Xn;
         }
@@ -391,11 +400,11 @@ size_t grad_ws_bytes(const tmm_problem *p)
     return (size_t)p->S * g.G * (2 * p->L_max + 1) * real_size(p->prec);
 }
 
-template <typename R, int KMAX>
+template <typename R, int KMAX, bool WITH_DN>
 static tmm_status launch_grad_typed(const tmm_problem *p, const GradPlan &g, const void *Rt, void *merit,
                                     void *dm_dd, void *dm_dn, void *ws, cudaStream_t st)
 {
-    auto k = tmm_grad_kernel<R, KMAX>;
+    auto k = tmm_grad_kernel<R, KMAX, WITH_DN>;
     if (g.smem > 48 * 1024) {
         // set once per (instantiation, device): the launch sequence stays free of
         // attribute calls when it is recorded into a CUDA graph
@@ -428,10 +437,16 @@ static tmm_status launch_grad_prec(const tmm_problem *p, const GradPlan &g, cons
                                    void *dm_dn, void *ws, cudaStream_t st)
 {
     const int need = p->L_max + 2;
-    if (need <= 18) return launch_grad_typed<R, 18>(p, g, Rt, merit, dm_dd, dm_dn, ws, st);
-    if (need <= 34) return launch_grad_typed<R, 34>(p, g, Rt, merit, dm_dd, dm_dn, ws, st);
-    if (need <= 66) return launch_grad_typed<R, 66>(p, g, Rt, merit, dm_dd, dm_dn, ws, st);
-    return launch_grad_typed<R, kGradMaxLayers + 2>(p, g, Rt, merit, dm_dd, dm_dn, ws, st);
+    if (dm_dn) {
+        if (need <= 18) return launch_grad_typed<R, 18, true>(p, g, Rt, merit, dm_dd, dm_dn, ws, st);
+        if (need <= 34) return launch_grad_typed<R, 34, true>(p, g, Rt, merit, dm_dd, dm_dn, ws, st);
+        if (need <= 66) return launch_grad_typed<R, 66, true>(p, g, Rt, merit, dm_dd, dm_dn, ws, st);
+        return launch_grad_typed<R, kGradMaxLayers + 2, true>(p, g, Rt, merit, dm_dd, dm_dn, ws, st);
+    }
+    if (need <= 18) return launch_grad_typed<R, 18, false>(p, g, Rt, merit, dm_dd, dm_dn, ws, st);
+    if (need <= 34) return launch_grad_typed<R, 34, false>(p, g, Rt, merit, dm_dd, dm_dn, ws, st);
+    if (need <= 66) return launch_grad_typed<R, 66, false>(p, g, Rt, merit, dm_dd, dm_dn, ws, st);
+    return launch_grad_typed<R, kGradMaxLayers + 2, false>(p, g, Rt, merit, dm_dd, dm_dn, ws, st);
 }
 
 tmm_status launch_grad(const tmm_problem *p, const void *R_target, void *merit, void *dm_dd, void *dm_dn, void *ws,

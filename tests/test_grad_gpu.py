@@ -59,6 +59,29 @@ def test_adjoint_small_vs_oracle(prec, with_ws):
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("with_ws", [False, True])
+def test_thickness_only_launch(prec, with_ws):
+    # dm_dn = NULL takes the instance without the index terms (the optimiser's
+    # launch): merit and dm_dd against the oracle, and against the full launch
+    w = W.adjoint(seed=33, S=7, L=11, n_lambda=37, n_theta=6)
+    prob = abi.to_device(w, prec)
+    dt = prob.real_dtype
+    Rt = torch.as_tensor(w.R_target).to(device="cuda", dtype=dt).contiguous()
+    m = torch.empty(w.S, dtype=dt, device="cuda")
+    dd = torch.empty(w.S, w.L_max, dtype=dt, device="cuda")
+    abi.tmm_coh_grad(prob, Rt, m, dd, None, ag.grad_workspace(prob) if with_ws else None)
+    torch.cuda.synchronize()
+    mo, ddo, _ = oracle_grad(w)
+    m, dd = m.double().cpu().numpy(), dd.double().cpu().numpy()
+    assert np.max(np.abs(m - mo)) <= MTOL[prec]
+    scale = np.max(np.abs(ddo))
+    assert np.max(np.abs(dd - ddo)) <= GTOL[prec] * scale
+    mf, ddf, _ = gpu_grad(w, prec, with_ws)
+    assert np.max(np.abs(dd - ddf)) <= (1e-12 if prec == "f64" else 1e-6) * scale
+    assert np.max(np.abs(m - mf)) <= (1e-14 if prec == "f64" else 1e-7)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
 def test_adjoint_single_pol_and_nondispersive(prec):
     w = W.plain_fp64(seed=32, S=4, L=7)
     w.theta = w.theta[:4]
