@@ -20,8 +20,10 @@ Beside them: ``mlp.py`` (the surrogate network's reference forward/backward),
 ``optimize.py`` (many-start Adam over the thicknesses on top of
 ``merit_grad``, the merit-driven optimisation of the paper's Fig. 1c) and
 ``incoherent.py`` (thick incoherent layers combined by intensities between
-coherent blocks evaluated with ``coh_tmm``) and ``absorption.py`` (absorbed
-fraction per layer from the field amplitudes of right partial products).
+coherent blocks evaluated with ``coh_tmm``), ``absorption.py`` (absorbed
+fraction per layer from the field amplitudes of right partial products) and
+``partial.py`` (one partially coherent layer: the Gauss-Hermite expectation
+of ``coh_tmm`` over a Gaussian spread of its thickness).
 """
 from __future__ import annotations
 
