@@ -282,6 +282,8 @@ def gpu_arm(args):
             out["optimize"] = bench_optimize(args, torch, abi, W, flush, world, max_over_ranks)
         if "incoherent" in sections:
             out["incoherent"] = bench_incoherent(args, torch, abi, W, flush, world, max_over_ranks)
+        if "partial" in sections:
+            out["partial"] = bench_partial(args, torch, abi, W, flush, world, max_over_ranks)
         if "absorption" in sections:
             out["absorption"] = bench_absorption(args, torch, abi, W, flush, world, max_over_ranks)
         if "paper" in sections:
@@ -303,7 +305,7 @@ def gpu_arm(args):
         "roofline": head["roofline"], "clocks": head.get("clocks"), "e2e": head.get("e2e"),
         "gpu_launches": args.steps,
     }
-    for k in ("f64", "f64x", "ragged", "adjoint", "optimize", "incoherent", "absorption", "paper_shapes",
+    for k in ("f64", "f64x", "ragged", "adjoint", "optimize", "incoherent", "partial", "absorption", "paper_shapes",
               "surrogate"):
         if k in out:
             line[k] = out[k]
@@ -436,6 +438,33 @@ def bench_incoherent(args, torch, abi, W, flush, world, max_over_ranks):
         ms_i, ms_c = max_over_ranks(sum(ti) / len(ti)), max_over_ranks(sum(tc) / len(tc))
         res[prec] = {"value": w.evals * world / (ms_i * 1e-3), "ms_per_step": ms_i,
                      "coherent_same_stacks_ms": ms_c, "steps": steps}
+        del R, T, prob
+        torch.cuda.empty_cache()
+    return res
+
+
+def bench_partial(args, torch, abi, W, flush, world, max_over_ranks):
+    """The same coated plates with the 1 mm plate partially coherent: its
+    thickness spread by a Gaussian of sigma = 30 nm (phase spread up to about
+    1 rad), 32 Gauss-Hermite nodes; vs the coherent kernel on the same stacks."""
+    w = W.coated_substrate()
+    K, sig = 32, 30.0
+    res = {"workload": w.name.replace("incoherent plate", "plate") + f", plate thickness spread sigma {sig:g} nm, "
+           f"{K} Gauss-Hermite nodes", "unit": "evals/s"}
+    for prec in ("f32", "f64"):
+        if prec == "f64" and args.skip_f64:
+            continue
+        prob = abi.to_device(w, prec)
+        layer = torch.full((w.S,), w.L_max, dtype=torch.int32, device=prob.d.device)
+        sigma = torch.full((w.S,), sig, dtype=prob.real_dtype, device=prob.d.device)
+        R, T = prob.empty_out(), prob.empty_out()
+        steps = max(3, args.steps // 2) if prec == "f32" else 2
+        tp = time_steps(lambda: abi.tmm_pcoh_batched(prob, layer, sigma, K, R, T), steps, 3, torch, flush)
+        finite = bool(torch.isfinite(R).all() and torch.isfinite(T).all())
+        tc = time_steps(lambda: abi.tmm_coh_batched(prob, R, T), steps, 3, torch, flush)
+        ms_p, ms_c = max_over_ranks(sum(tp) / len(tp)), max_over_ranks(sum(tc) / len(tc))
+        res[prec] = {"value": w.evals * world / (ms_p * 1e-3), "ms_per_step": ms_p,
+                     "coherent_same_stacks_ms": ms_c, "finite": finite, "steps": steps}
         del R, T, prob
         torch.cuda.empty_cache()
     return res
@@ -667,9 +696,9 @@ def main():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-extras", action="store_true", help="headline only (no ragged / adjoint lines)")
     ap.add_argument("--skip-surrogate", action="store_true")
-    ap.add_argument("--sections", default="ragged,adjoint,optimize,incoherent,absorption,paper,surrogate",
+    ap.add_argument("--sections", default="ragged,adjoint,optimize,incoherent,partial,absorption,paper,surrogate",
                     help="extra sections after the headline (comma list of ragged, adjoint, optimize, incoherent, "
-                         "absorption, paper, surrogate)")
+                         "partial, absorption, paper, surrogate)")
     ap.add_argument("--sur-train", type=int, default=2_000_000, help="training spectra (GPU-generated)")
     ap.add_argument("--sur-steps", type=int, default=2000, help="training steps of 8192 spectra")
     ap.add_argument("--stacks", type=int, default=0, help="shrink the workload (profiling runs only)")

@@ -236,6 +236,31 @@ TMM_API tmm_status tmm_absorption_batched(const tmm_problem *p, void *A, void *R
 TMM_API tmm_status tmm_field_profile(const tmm_problem *p, int32_t n_z, void *E, void *stream);
 
 /*
+ * One partially coherent layer per stack (the paper treats coherent stacks
+ * only; this is a reading of partial coherence as a Gaussian spread of one
+ * layer's thickness, from nonuniformity or a finite coherence length).
+ * Finite layer j = layer[s] (1-based; 0 = a coherent stack) has the thickness
+ * d_j + D, D ~ N(0, sigma[s]^2) nm, and R, T are the expectations of the
+ * coherent R, T (Eqs. 1-6) over D, by the Gauss-Hermite rule with n_nodes
+ * nodes x_k and weights w_k: E[f] = sum_k (w_k / sqrt(pi)) f(sqrt(2) sigma x_k).
+ * A node whose thickness falls below zero counts as zero thickness.
+ *   layer    device int32 [S]
+ *   sigma    device real [S] (the problem's real type), nm
+ *   n_nodes  1 .. 256 (else TMM_ERR_INVALID_ARG).  The rule resolves fringe
+ *            harmonics up to a frequency growing like sqrt(n_nodes): phase
+ *            spreads 2 pi Re(n_j cos theta_j) sigma / lambda of about 1 need
+ *            some 30 nodes, of about 2 some 250; wider spreads are the
+ *            incoherent limit (tmm_inc_batched)
+ *   R, T     device [P][S][n_theta][n_lambda] as tmm_coh_batched (T may be
+ *            NULL; TMM_POL_AVG gives one plane of the mean of s and p)
+ * A stack whose layer is outside [0, L_s] or whose sigma is negative or not
+ * finite gets NaN.  prec TMM_F64 or TMM_F32 (else TMM_ERR_UNSUPPORTED); the
+ * stage limit on L_max of tmm_field_profile.  Asynchronous on `stream`.
+ */
+TMM_API tmm_status tmm_pcoh_batched(const tmm_problem *p, const int32_t *layer, const void *sigma, int32_t n_nodes,
+                                    void *R, void *T, void *stream);
+
+/*
  * Batched reward of the paper's reinforcement-learning environment (Sec. 5):
  *   reward[s] = - sum over (plane, theta, lambda) of |R_target - R|
  * for every stack, with the planes of pol_mask (s, p, or their mean for

@@ -36,7 +36,7 @@ EXPORTED = ("tmm_coh_batched", "tmm_coh_batched_ex", "tmm_workspace_size", "tmm_
             "tmm_coh_grad", "tmm_status_string", "tmm_last_cuda_error", "tmm_version",
             "tmm_probe_fma_rate", "tmm_gemm_bf16", "tmm_gemm_bf16_t", "tmm_coh_batched_noalloc",
             "tmm_optimize_workspace_size", "tmm_optimize_adam", "tmm_reward_workspace_size", "tmm_coh_reward",
-            "tmm_inc_batched", "tmm_absorption_batched", "tmm_field_profile", "tmm_surrogate_create", "tmm_surrogate_destroy", "tmm_surrogate_outputs", "tmm_surrogate_parameters",
+            "tmm_inc_batched", "tmm_absorption_batched", "tmm_field_profile", "tmm_pcoh_batched", "tmm_surrogate_create", "tmm_surrogate_destroy", "tmm_surrogate_outputs", "tmm_surrogate_parameters",
             "tmm_surrogate_generate", "tmm_surrogate_train_step", "tmm_surrogate_infer", "tmm_surrogate_layer",
             "tmm_surrogate_status", "tmm_surrogate_save", "tmm_surrogate_load")
 
@@ -131,6 +131,7 @@ def load(path: Optional[str] = None):
         lib.tmm_inc_batched.argtypes = [P, vp, vp, vp, vp]
         lib.tmm_absorption_batched.argtypes = [P, vp, vp, vp, vp]
         lib.tmm_field_profile.argtypes = [P, ctypes.c_int32, vp, vp]
+        lib.tmm_pcoh_batched.argtypes = [P, vp, vp, ctypes.c_int32, vp, vp, vp]
         lib.tmm_optimize_adam.argtypes = [P, vp, ctypes.POINTER(TmmAdamCfg), ctypes.c_int32, vp, vp, sz, vp]
         i32, f32 = ctypes.c_int32, ctypes.c_float
         lib.tmm_surrogate_create.argtypes = [ctypes.POINTER(TmmSurrogateDesc), ctypes.POINTER(vp)]
@@ -155,7 +156,7 @@ def load(path: Optional[str] = None):
                      "tmm_workspace_status", "tmm_coh_grad", "tmm_probe_fma_rate", "tmm_gemm_bf16",
                      "tmm_gemm_bf16_t", "tmm_coh_batched_noalloc", "tmm_optimize_workspace_size",
                      "tmm_optimize_adam", "tmm_reward_workspace_size", "tmm_coh_reward", "tmm_inc_batched",
-                     "tmm_absorption_batched", "tmm_field_profile"):
+                     "tmm_absorption_batched", "tmm_field_profile", "tmm_pcoh_batched"):
             getattr(lib, name).restype = ctypes.c_int
         if path is None:
             _lib = lib
@@ -385,6 +386,14 @@ def tmm_field_profile(prob: DeviceProblem, n_z: int, E: torch.Tensor, stream=Non
     """|E(z) / E_inc|^2 into E [P][S][L_max][n_z][N_theta][N_lambda]."""
     _check("tmm_field_profile", load().tmm_field_profile(ctypes.byref(prob.struct()), int(n_z), _ptr(E),
                                                          _stream(stream)))
+
+
+def tmm_pcoh_batched(prob: DeviceProblem, layer: torch.Tensor, sigma: torch.Tensor, n_nodes: int, R: torch.Tensor,
+                     T: Optional[torch.Tensor] = None, stream=None):
+    """R, T with one partially coherent layer per stack: layer int32 [S]
+    (1-based, 0 = none), sigma [S] nm in the problem's real type."""
+    _check("tmm_pcoh_batched", load().tmm_pcoh_batched(ctypes.byref(prob.struct()), _ptr(layer), _ptr(sigma),
+                                                       int(n_nodes), _ptr(R), _ptr(T), _stream(stream)))
 
 
 def adam_cfg(lr, beta1=0.9, beta2=0.999, eps=1e-8, d_min=0.0, d_max=1e30, step0=0) -> TmmAdamCfg:

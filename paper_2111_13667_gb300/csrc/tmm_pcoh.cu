@@ -1,0 +1,463 @@
+// tmm_pcoh.cu -- stacks with one partially coherent layer.
+//
+// Finite layer j = layer[s] of stack s has the thickness d_j + D with
+// D ~ N(0, sigma_s^2); R and T are the expectations of the coherent R, T
+// (Eqs. 1-6) over D, by the Gauss-Hermite rule
+//   E[f] = sum_k (w_k / sqrt(pi)) f(sqrt(2) sigma x_k)
+// (a reading: the paper treats coherent stacks only).  Only layer j's phase
+// depends on D, so one thread per (stack, lambda, theta) evaluates, for both
+// polarisations:
+//   y  = F_j x_{j+1}: the forward kernel's right-to-left sweep from the exit
+//        medium through interface j | j+1 (scaled, unnormalised interfaces);
+//   ML = F_0 P_1 F_1 ... P_{j-1} F_{j-1}: the block left of layer j, both
+//        columns carried through the same sweep from the identity;
+//   per node: x_0 = ML P_j(d_j + D_k) y, R_k = |x_0[1] / x_0[0]|^2 and T_k
+//        from the dropped scales exactly as the forward kernel's T; the
+//        products ML_ab y_b are formed once, so a node costs its phase
+//        factors, one complex product and one complex fma per row.
+// The nodes come from a Sturm-sequence bisection of the Hermite Jacobi matrix
+// on the host; they are symmetric, so the kernel takes the non-negative half.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "tmm_device.cuh"
+#include "tmm_internal.h"
+
+namespace tmm {
+
+namespace {
+
+constexpr int kPcThreads = 256;
+constexpr int kPcMaxNodes = 256;
+constexpr int kPcHalf = kPcMaxNodes / 2;
+
+// The non-negative Gauss-Hermite nodes h_i (descending) of an n_nodes rule
+// as sqrt(2) x, with their weights w / sqrt(pi); an odd rule's node 0 is the
+// last entry and is taken once.
+template <typename R> struct Nodes {
+    int n_half;   // entries
+    int odd;      // the last entry is the node 0
+    R off[kPcHalf + 1];
+    R w[kPcHalf + 1];
+};
+
+// Gauss-Hermite rule: the nodes are the eigenvalues of the symmetric
+// tridiagonal Jacobi matrix of the Hermite polynomials (zero diagonal,
+// off-diagonal sqrt(i / 2)), found by bisection on the Sturm count; the
+// weights are 1 / (K psi_{K-1}(x)^2) with psi the orthonormal Hermite
+// polynomials (psi_0 = pi^{-1/4}), here divided by sqrt(pi).
+static int eigen_below(const double *b2, int K, double x)
+{
+    double q = -x;
+    if (q == 0.0) q = -1e-300;
+    int c = q < 0.0 ? 1 : 0;
+    for (int i = 1; i < K; ++i) {
+        q = -x - b2[i - 1] / q;
+        if (q == 0.0) q = -1e-300;
+        if (q < 0.0) ++c;
+    }
+    return c;
+}
+
+static void gauss_hermite(int K, double *x, double *w)
+{
+    double b2[kPcMaxNodes];
+    for (int i = 1; i < K; ++i) b2[i - 1] = 0.5 * i;
+    const double bound = std::sqrt(2.0 * K) + 1.0;
+    const double pi = 3.14159265358979323846;
+    for (int k = 0; k < K; ++k) {
+        double lo = -bound, hi = bound;
+        for (int it = 0; it < 200; ++it) {
+            const double mid = 0.5 * (lo + hi);
+            if (mid == lo || mid == hi) break;
+            if (eigen_below(b2, K, mid) >= k + 1) hi = mid;
+            else lo = mid;
+        }
+        const double xk = 0.5 * (lo + hi);
+        double pm = std::pow(pi, -0.25), pc = std::sqrt(2.0) * xk * pm;
+        double pk1 = pm;
+        if (K > 1) {
+            for (int n = 1; n < K - 1; ++n) {
+                const double pn = std::sqrt(2.0 / (n + 1)) * xk * pc - std::sqrt(n / (n + 1.0)) * pm;
+                pm = pc;
+                pc = pn;
+            }
+            pk1 = pc;
+        }
+        x[k] = xk;
+        w[k] = 1.0 / (K * pk1 * pk1) / std::sqrt(pi);
+    }
+}
+
+template <typename R> static Nodes<R> make_nodes(int K)
+{
+    double x[kPcMaxNodes], w[kPcMaxNodes];
+    gauss_hermite(K, x, w);
+    Nodes<R> nd{};
+    nd.odd = K & 1;
+    nd.n_half = (K + 1) / 2;
+    // x ascends: the non-negative half from the top down, symmetric weights
+    // averaged with their mirror
+    for (int i = 0; i < nd.n_half; ++i) {
+        const int hi = K - 1 - i, lo = i;
+        const double xh = hi == lo ? 0.0 : 0.5 * (x[hi] - x[lo]);
+        nd.off[i] = R(std::sqrt(2.0) * xh);
+        nd.w[i] = R(hi == lo ? w[hi] : 0.5 * (w[hi] + w[lo]));
+    }
+    return nd;
+}
+
+// One coherent layer step (interface j | j+1, then the phase of layer j) on
+// the amplitude pair; the forward kernel's arithmetic.
+template <typename R> struct Step {
+    Cx<R> emi, epi;
+    R yi;
+};
+
+template <typename R>
+__device__ __forceinline__ Step<R> phase_of(R dl, Cx<R> q, R yi_max)
+{
+    Step<R> st;
+    const R yr = dl * q.x;
+    st.yi = fmin(dl * q.y, yi_max);
+    R sn, cs;
+    sincos_turn(yr - rint_w(yr), &sn, &cs);
+    const R E2 = exp_m2_turn(st.yi);
+    st.emi = Cx<R>{cs, -sn};
+    st.epi = Cx<R>{E2 * cs, E2 * sn};
+    return st;
+}
+
+// R and T of one point from x_0's pair and the scale bookkeeping (the
+// forward kernel's Eqs. 5-6 with the dropped factors restored).
+template <typename R>
+__device__ __forceinline__ void rt_of(Cx<R> x0, Cx<R> x1, R scale, int e, R kappa_out, R kappa_in, R &Rv, R &Tv)
+{
+    const R ax0 = abs2(x0);
+    Rv = abs2(x1) / ax0;
+    Tv = kappa_out / kappa_in * ldexp_w(scale / ax0, e);
+}
+
+template <typename R, int POL>
+__device__ __forceinline__ void pc_point(const StageA<R> *__restrict__ sa, const StageB<R> *__restrict__ sb, int TL,
+                                         int tl, int L, int jp, R sig, R inv_lam, R dj, R n0, R sth, R cth,
+                                         const Nodes<R> &nd, R out[4])
+{
+    constexpr int RN = RenormEvery<R>::value;
+    const R beta = n0 * sth, c0 = n0 * cth, q0sq = c0 * c0;
+    const R yi_max = R(kImDeltaMax / kTwoPi);
+    StageA<R> A = sa[(L + 1) * TL + tl];
+    R absz;
+    Cx<R> q_nx = forward_root(Cx<R>{A.d2x + q0sq, A.n2y}, &absz);
+    const Cx<R> q_out = q_nx, n2_out = {A.d2x + n0 * n0, A.n2y};
+    Cx<R> g_nx = cmul(q_nx, Cx<R>{A.in2x, A.in2y});
+    R Ps = R(1), Y = R(0), Pp = (POL & 2) ? sb[(L + 1) * TL + tl].ain2 : R(1);
+    int eP = 0, ePp = 0, es = 0, ep = 0;
+    Cx<R> s0 = {R(1), R(0)}, s1 = {R(0), R(0)}, p0 = s0, p1 = s1;
+    int cnt = 0;
+    auto rescale = [&]() {
+        renorm_scalar(Ps, eP);
+        if (POL & 2) renorm_scalar(Pp, ePp);
+        if (POL & 1) renorm_pair(s0, s1, es);
+        if (POL & 2) renorm_pair(p0, p1, ep);
+    };
+    // right of the partial layer (the whole stack when jp = 0)
+    for (int j = L; j > jp; --j) {
+        A = sa[j * TL + tl];
+        const StageB<R> B = sb[j * TL + tl];
+        const Cx<R> q = forward_root(Cx<R>{A.d2x + q0sq, A.n2y}, &absz);
+        Ps *= absz;
+        const Step<R> st = phase_of(B.dl, q, yi_max);
+        Y += st.yi;
+        if (POL & 1) {
+            interface_pair(q, q_nx, s0, s1);
+            s0 = cmul(st.emi, s0);
+            s1 = cmul(st.epi, s1);
+        }
+        if (POL & 2) {
+            Pp *= B.ain2;
+            const Cx<R> g = cmul(q, Cx<R>{A.in2x, A.in2y});
+            interface_pair(g, g_nx, p0, p1);
+            p0 = cmul(st.emi, p0);
+            p1 = cmul(st.epi, p1);
+            g_nx = g;
+        }
+        q_nx = q;
+        if (++cnt == RN) {
+            cnt = 0;
+            rescale();
+        }
+    }
+    const bool grazing = beta >= n0;
+    const Cx<R> q0 = {c0, R(0)};
+    const int e4 = 2 * (L + 1);
+    const StageA<R> A0 = sa[tl];
+    const Cx<R> g0 = cmul(q0, Cx<R>{A0.in2x, A0.in2y});
+    const R kout_p = cmul(n2_out, conj(q_out)).x, kin_p = n0 * n0 * q0.x;
+    auto finish = [&](Cx<R> xs0, Cx<R> xs1, Cx<R> xp0, Cx<R> xp1, R Yt, int esx, int epx, R res[4]) {
+        R u = R(-2.0 * kTwoPi * kLog2e) * Yt;
+        u = fmax(u, R(-1.0e6));
+        const R un = floor_w(u);
+        const R yscale = exp2_w(u - un);
+        const int yn = (int)un;
+        const R Pst = Ps * (q0.x * q0.x);
+        if (POL & 1) rt_of(xs0, xs1, Pst * yscale, e4 + eP + yn - 2 * esx, q_out.x, q0.x, res[0], res[1]);
+        if (POL & 2) rt_of(xp0, xp1, Pst * Pp * yscale, e4 + eP + ePp + yn - 2 * epx, kout_p, kin_p, res[2], res[3]);
+        if (grazing) res[0] = res[2] = R(1), res[1] = res[3] = R(0);
+    };
+    if (jp == 0) {
+        if (POL & 1) interface_pair(q0, q_nx, s0, s1);
+        if (POL & 2) interface_pair(g0, g_nx, p0, p1);
+        finish(s0, s1, p0, p1, Y, es, ep, out);
+        return;
+    }
+    // layer jp: its root and interface jp | jp+1; its phase waits for the nodes
+    A = sa[jp * TL + tl];
+    const Cx<R> qj = forward_root(Cx<R>{A.d2x + q0sq, A.n2y}, &absz);
+    Ps *= absz;
+    Cx<R> gj = {R(0), R(0)};
+    if (POL & 1) interface_pair(qj, q_nx, s0, s1);
+    if (POL & 2) {
+        Pp *= sb[jp * TL + tl].ain2;
+        gj = cmul(qj, Cx<R>{A.in2x, A.in2y});
+        interface_pair(gj, g_nx, p0, p1);
+    }
+    rescale();
+    // the block left of layer jp: both columns of ML, from the identity
+    Cx<R> sc00 = {R(1), R(0)}, sc10 = {R(0), R(0)}, sc01 = sc10, sc11 = sc00;
+    Cx<R> pc00 = sc00, pc10 = sc10, pc01 = sc01, pc11 = sc11;
+    int els = 0, elp = 0;
+    Cx<R> qr = qj, gr = gj;
+    cnt = 0;
+    for (int j = jp - 1; j >= 1; --j) {
+        A = sa[j * TL + tl];
+        const StageB<R> B = sb[j * TL + tl];
+        const Cx<R> q = forward_root(Cx<R>{A.d2x + q0sq, A.n2y}, &absz);
+        Ps *= absz;
+        const Step<R> st = phase_of(B.dl, q, yi_max);
+        Y += st.yi;
+        if (POL & 1) {
+            interface_pair(q, qr, sc00, sc10);
+            interface_pair(q, qr, sc01, sc11);
+            sc00 = cmul(st.emi, sc00), sc10 = cmul(st.epi, sc10);
+            sc01 = cmul(st.emi, sc01), sc11 = cmul(st.epi, sc11);
+        }
+        if (POL & 2) {
+            Pp *= B.ain2;
+            const Cx<R> g = cmul(q, Cx<R>{A.in2x, A.in2y});
+            interface_pair(g, gr, pc00, pc10);
+            interface_pair(g, gr, pc01, pc11);
+            pc00 = cmul(st.emi, pc00), pc10 = cmul(st.epi, pc10);
+            pc01 = cmul(st.emi, pc01), pc11 = cmul(st.epi, pc11);
+            gr = g;
+        }
+        qr = q;
+        if (++cnt == RN) {
+            cnt = 0;
+            renorm_scalar(Ps, eP);
+            if (POL & 2) renorm_scalar(Pp, ePp);
+            if (POL & 1) {
+                // one exponent for the whole matrix: renorm both columns together
+                int k0 = 0, k1 = 0;
+                Cx<R> a = sc00, b = sc10, c = sc01, d = sc11;
+                renorm_pair(a, b, k0);
+                renorm_pair(c, d, k1);
+                const int k = max(k0, k1);
+                const R f = pow2_neg<R>(k);
+                sc00 = scale(f, sc00), sc10 = scale(f, sc10), sc01 = scale(f, sc01), sc11 = scale(f, sc11);
+                els += k;
+            }
+            if (POL & 2) {
+                int k0 = 0, k1 = 0;
+                Cx<R> a = pc00, b = pc10, c = pc01, d = pc11;
+                renorm_pair(a, b, k0);
+                renorm_pair(c, d, k1);
+                const int k = max(k0, k1);
+                const R f = pow2_neg<R>(k);
+                pc00 = scale(f, pc00), pc10 = scale(f, pc10), pc01 = scale(f, pc01), pc11 = scale(f, pc11);
+                elp += k;
+            }
+        }
+    }
+    // interface 0 | 1
+    if (POL & 1) {
+        interface_pair(q0, qr, sc00, sc10);
+        interface_pair(q0, qr, sc01, sc11);
+    }
+    if (POL & 2) {
+        interface_pair(g0, gr, pc00, pc10);
+        interface_pair(g0, gr, pc01, pc11);
+    }
+    // node-independent products: x_0 = (ML00 y0) e^{-i delta} + (ML01 y1) e^{+i delta}
+    // (row 0), likewise row 1, with e^{+-i delta} the node's phase factors
+    Cx<R> sA = {R(0), R(0)}, sB = sA, sC = sA, sD = sA, pA = sA, pB = sA, pC = sA, pD = sA;
+    if (POL & 1) sA = cmul(sc00, s0), sB = cmul(sc01, s1), sC = cmul(sc10, s0), sD = cmul(sc11, s1);
+    if (POL & 2) pA = cmul(pc00, p0), pB = cmul(pc01, p1), pC = cmul(pc10, p0), pD = cmul(pc11, p1);
+    // the nodes: layer jp's phase at thickness d_jp + sqrt(2) sigma x_k
+    R acc[4] = {R(0), R(0), R(0), R(0)};
+    for (int i = 0; i < nd.n_half; ++i) {
+        const int nsign = (nd.odd && i == nd.n_half - 1) ? 1 : 2;
+        for (int sgn = 0; sgn < nsign; ++sgn) {
+            const R D = sig * (sgn ? -nd.off[i] : nd.off[i]);
+            const R dl = fmax(dj + D, R(0)) * inv_lam;
+            const Step<R> st = phase_of(dl, qj, yi_max);
+            Cx<R> xs0 = {R(0), R(0)}, xs1 = xs0, xp0 = xs0, xp1 = xs0;
+            if (POL & 1) {
+                xs0 = cfma(sB, st.epi, cmul(sA, st.emi));
+                xs1 = cfma(sD, st.epi, cmul(sC, st.emi));
+            }
+            if (POL & 2) {
+                xp0 = cfma(pB, st.epi, cmul(pA, st.emi));
+                xp1 = cfma(pD, st.epi, cmul(pC, st.emi));
+            }
+            R res[4] = {R(0), R(0), R(0), R(0)};
+            finish(xs0, xs1, xp0, xp1, Y + st.yi, es + els, ep + elp, res);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[c] = fma(nd.w[i], res[c], acc[c]);
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) out[c] = acc[c];
+}
+
+template <typename R, int POL, bool WITH_T>
+__global__ void __launch_bounds__(kPcThreads) tmm_pcoh_kernel(const tmm_problem p, const int32_t *__restrict__ layer,
+                                                               const R *__restrict__ sigma, const Nodes<R> nd, int TL,
+                                                               int TT, int n_lt, int n_tt, R *__restrict__ Rout,
+                                                               R *__restrict__ Tout)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    StageA<R> *sa = reinterpret_cast<StageA<R> *>(smem);
+    StageB<R> *sb = reinterpret_cast<StageB<R> *>(sa + (size_t)(p.L_max + 2) * TL);
+    R *n0s = reinterpret_cast<R *>(sb + (size_t)(p.L_max + 2) * TL);
+
+    const long long item = blockIdx.x;
+    const int per_stack = n_lt * n_tt;
+    const int s = (int)(item / per_stack);
+    const int rr = (int)(item - (long long)s * per_stack);
+    const int lt = rr / n_tt, ttile = rr % n_tt;
+    const int tid = threadIdx.y * TL + threadIdx.x, nthr = TL * TT;
+    const int L = layers_of(p, s);
+    const int l0 = lt * TL;
+    if (L >= 0) fill_stage<R>(p, s, L, l0, TL, sa, sb, n0s, tid, nthr);
+    __syncthreads();
+    const int tl = threadIdx.x, l = l0 + tl, a_ = ttile * TT + threadIdx.y;
+    if (l >= p.n_lambda || a_ >= p.n_theta) return;  // no barrier follows
+
+    R out[4] = {nan_w<R>(), nan_w<R>(), nan_w<R>(), nan_w<R>()};
+    const int jp = layer[s];
+    const R sig = sigma[s];
+    const bool valid = L >= 0 && jp >= 0 && jp <= L && sig >= R(0) && sig <= R(1e30);  // false for NaN
+    if (valid) {
+        R sth, cth;
+        sincos_w(((const R *)p.theta)[a_], &sth, &cth);
+        const R inv_lam = R(1) / ((const R *)p.lambda)[l];
+        const R dj = jp >= 1 ? ((const R *)p.d)[(long long)s * p.L_max + (jp - 1)] : R(0);
+        pc_point<R, POL>(sa, sb, TL, tl, L, jp, sig, inv_lam, dj, n0s[tl], sth, cth, nd, out);
+    }
+    const long long plane = (long long)p.S * p.n_theta * p.n_lambda;
+    const long long o = ((long long)s * p.n_theta + a_) * p.n_lambda + l;
+    if (POL & 4) {
+        Rout[o] = R(0.5) * (out[0] + out[2]);
+        if (WITH_T) Tout[o] = R(0.5) * (out[1] + out[3]);
+    } else {
+        int pi = 0;
+        if (POL & 1) {
+            Rout[o] = out[0];
+            if (WITH_T) Tout[o] = out[1];
+            ++pi;
+        }
+        if (POL & 2) {
+            Rout[pi * plane + o] = out[2];
+            if (WITH_T) Tout[pi * plane + o] = out[3];
+        }
+    }
+}
+
+size_t pcoh_smem(const tmm_problem *p, int TL)
+{
+    const size_t r = real_size(p->prec);
+    return (size_t)(p->L_max + 2) * TL * (6 * r) + (size_t)TL * r;
+}
+
+template <typename R, int POL, bool WITH_T>
+tmm_status launch_pcoh_k(const tmm_problem *p, const int32_t *layer, const R *sigma, const Nodes<R> &nd, int TL,
+                         int TT, int n_lt, int n_tt, long long items, size_t smem, R *Ro, R *To, cudaStream_t st)
+{
+    auto k = tmm_pcoh_kernel<R, POL, WITH_T>;
+    if (smem > 48 * 1024) {
+        // once per (instantiation, device) and size
+        static int set_bytes[64] = {};
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return cuda_fail(e);
+        if (dev < 0 || dev >= 64) return TMM_ERR_UNSUPPORTED;
+        if (set_bytes[dev] < (int)smem) {
+            e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return cuda_fail(e);
+            set_bytes[dev] = (int)smem;
+        }
+    }
+    k<<<(unsigned)items, dim3(TL, TT), smem, st>>>(*p, layer, sigma, nd, TL, TT, n_lt, n_tt, Ro, To);
+    return check_launch();
+}
+
+template <typename R>
+tmm_status launch_pcoh_prec(const tmm_problem *p, const int32_t *layer, const void *sigma_, int K, int TL, int TT,
+                            int n_lt, int n_tt, long long items, size_t smem, void *R_, void *T_, cudaStream_t st)
+{
+    const Nodes<R> nd = make_nodes<R>(K);
+    const R *sigma = static_cast<const R *>(sigma_);
+    R *Ro = static_cast<R *>(R_), *To = static_cast<R *>(T_);
+    const bool wt = To != nullptr;
+#define TMM_PC_CASE(P_)                                                                                          \
+    case P_:                                                                                                     \
+        return wt ? launch_pcoh_k<R, P_, true>(p, layer, sigma, nd, TL, TT, n_lt, n_tt, items, smem, Ro, To, st)  \
+                  : launch_pcoh_k<R, P_, false>(p, layer, sigma, nd, TL, TT, n_lt, n_tt, items, smem, Ro, To, st);
+    switch (p->pol_mask) {
+        TMM_PC_CASE(1)
+        TMM_PC_CASE(2)
+        TMM_PC_CASE(3)
+        TMM_PC_CASE(7)
+    default: return TMM_ERR_INVALID_ARG;
+    }
+#undef TMM_PC_CASE
+}
+
+}  // namespace
+
+}  // namespace tmm
+
+using namespace tmm;
+
+extern "C" TMM_API tmm_status tmm_pcoh_batched(const tmm_problem *p, const int32_t *layer, const void *sigma,
+                                               int32_t n_nodes, void *R, void *T, void *stream)
+{
+    tmm_status s = validate_problem(p);
+    if (s != TMM_OK) return s;
+    if (p->prec == TMM_F64X) return TMM_ERR_UNSUPPORTED;
+    if (n_nodes < 1 || n_nodes > kPcMaxNodes) return TMM_ERR_INVALID_ARG;
+    const long long pts = (long long)p->S * p->n_lambda * p->n_theta;
+    if (pts == 0) return TMM_OK;
+    if (!layer || !sigma || !R) return TMM_ERR_INVALID_ARG;
+    if (pcoh_smem(p, 1) > kSmemBlockCeiling) return TMM_ERR_UNSUPPORTED;
+    DeviceInfo di;
+    s = device_info(&di);
+    if (s != TMM_OK) return s;
+    const int TT = std::min(p->n_theta, 32);
+    int TL = 1;
+    while (TL * TT * 2 <= kPcThreads) TL *= 2;
+    while (TL > 1 && TL / 2 >= p->n_lambda) TL /= 2;
+    while (TL > 1 && pcoh_smem(p, TL) > (size_t)di.max_smem_optin) TL /= 2;
+    const size_t smem = pcoh_smem(p, TL);
+    if (smem > (size_t)di.max_smem_optin) return TMM_ERR_UNSUPPORTED;
+    const int n_lt = (p->n_lambda + TL - 1) / TL, n_tt = (p->n_theta + TT - 1) / TT;
+    const long long items = (long long)p->S * n_lt * n_tt;
+    if (items > 0x7fffffffLL) return TMM_ERR_UNSUPPORTED;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    return p->prec == TMM_F64
+               ? launch_pcoh_prec<double>(p, layer, sigma, n_nodes, TL, TT, n_lt, n_tt, items, smem, R, T, st)
+               : launch_pcoh_prec<float>(p, layer, sigma, n_nodes, TL, TT, n_lt, n_tt, items, smem, R, T, st);
+}

@@ -152,6 +152,13 @@ def test_incoherent_absorption_reward_argument_checks(lib):
     # absorption keeps per-layer records: L_max <= 127
     big = _problem(L_max=200)
     assert lib.tmm_absorption_batched(ctypes.byref(big), fake, None, None, None) == abi.TMM_ERR_UNSUPPORTED
+    # partial coherence: node count, pointers, precision
+    lay = ctypes.c_void_p(0x7100)
+    assert lib.tmm_pcoh_batched(ctypes.byref(p), lay, fake, 0, fake, None, None) == abi.TMM_ERR_INVALID_ARG
+    assert lib.tmm_pcoh_batched(ctypes.byref(p), lay, fake, 257, fake, None, None) == abi.TMM_ERR_INVALID_ARG
+    assert lib.tmm_pcoh_batched(ctypes.byref(p), None, fake, 8, fake, None, None) == abi.TMM_ERR_INVALID_ARG
+    assert lib.tmm_pcoh_batched(ctypes.byref(p), lay, None, 8, fake, None, None) == abi.TMM_ERR_INVALID_ARG
+    assert lib.tmm_pcoh_batched(ctypes.byref(px), lay, fake, 8, fake, None, None) == abi.TMM_ERR_UNSUPPORTED
     # the field profile only stages the stack in shared memory
     deep = _problem(L_max=100000)
     assert lib.tmm_field_profile(ctypes.byref(deep), 2, fake, None) == abi.TMM_ERR_UNSUPPORTED
@@ -165,6 +172,7 @@ def test_incoherent_absorption_reward_argument_checks(lib):
     assert lib.tmm_inc_batched(ctypes.byref(e), None, None, None, None) == abi.TMM_OK
     assert lib.tmm_absorption_batched(ctypes.byref(e), None, None, None, None) == abi.TMM_OK
     assert lib.tmm_coh_reward(ctypes.byref(e), None, None, None, None, 0, None) == abi.TMM_OK
+    assert lib.tmm_pcoh_batched(ctypes.byref(e), None, None, 8, None, None, None) == abi.TMM_OK
 
 
 def test_empty_problem_is_a_noop(lib):
