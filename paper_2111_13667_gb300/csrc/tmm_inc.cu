@@ -19,6 +19,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "tmm_device.cuh"
 #include "tmm_internal.h"
@@ -137,7 +138,248 @@ __device__ __forceinline__ void block_coeffs(const StageA<R> *__restrict__ sa, c
     }
 }
 
-template <typename R, int POL, bool WITH_T>
+// One point (one angle), both polarisations: Rv, Tv = {s, p}.  ok: the
+// stack is valid and its incoherent layers are non-absorbing.
+template <typename R, int POL>
+__device__ __forceinline__ void inc_point(const StageA<R> *__restrict__ sa, const StageB<R> *__restrict__ sb,
+                                          const unsigned char *flg, int TL, int tl, int L, R n0, R sth, R cth,
+                                          R Rv[2], R Tv[2])
+{
+    const R beta = n0 * sth, c0 = n0 * cth, q0sq = c0 * c0;
+    if (beta >= n0) {  // grazing (false for a NaN n_0)
+        Rv[0] = Rv[1] = R(1);
+        Tv[0] = Tv[1] = R(0);
+        return;
+    }
+    if (!(n0 == n0)) return;
+    // the first evanescent incoherent layer ends the stack
+    int e = L + 1;
+    bool cut = false;
+    for (int j = 1; j <= L; ++j)
+        if (flg[j] && sa[j * TL + tl].d2x + q0sq <= R(0)) {
+            e = j;
+            cut = true;
+            break;
+        }
+    R P[2] = {R(1), R(1)}, M[2] = {R(0), R(0)}, t[2] = {R(1), R(1)};
+    int b = e;
+    while (b > 0) {
+        int a = b - 1;
+        while (a > 0 && !flg[a]) --a;
+        const R qa = a == 0 ? c0 : sqrt(sa[a * TL + tl].d2x + q0sq);
+        R Rf[2] = {R(0), R(0)}, Rb[2] = {R(0), R(0)}, Tf[2] = {R(0), R(0)};
+        block_coeffs<R, POL>(sa, sb, TL, tl, a, b, q0sq, qa, n0, Rf, Rb, Tf);
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            if (!(POL & (1 << k))) continue;
+            const R P1 = P[k] - Rb[k] * M[k];
+            const R M1 = Rf[k] * P1 + Tf[k] * Tf[k] * M[k];
+            const R inv = R(1) / P1;  // keep P = 1
+            P[k] = R(1);
+            M[k] = M1 * inv;
+            t[k] = t[k] * Tf[k] * inv;
+        }
+        b = a;
+    }
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        Rv[k] = M[k];
+        Tv[k] = cut ? R(0) : t[k];
+    }
+}
+
+// ---------------------------------------------------------------- FP32: two angles per thread
+// Both columns of a block's matrix for the two angles of a thread, on the
+// lanes of the paired FP32 instructions (see tmm_fwd.cu).
+struct Cols2 {
+    C2 x0, x1, y0, y1;
+};
+
+__device__ __forceinline__ void renorm_cols2(Cols2 &c, int &ea, int &eb)
+{
+    auto mx = [](const C2 &v, int i) {
+        return i ? fmaxf(fabsf(v.x.y), fabsf(v.y.y)) : fmaxf(fabsf(v.x.x), fabsf(v.y.x));
+    };
+    const float ma = fmaxf(fmaxf(mx(c.x0, 0), mx(c.x1, 0)), fmaxf(mx(c.y0, 0), mx(c.y1, 0)));
+    const float mb = fmaxf(fmaxf(mx(c.x0, 1), mx(c.x1, 1)), fmaxf(mx(c.y0, 1), mx(c.y1, 1)));
+    const int ka = exponent_of(ma), kb = exponent_of(mb);
+    const float2 f = f2(pow2_neg<float>(ka), pow2_neg<float>(kb));
+    c.x0 = C2{mul2(f, c.x0.x), mul2(f, c.x0.y)}, c.x1 = C2{mul2(f, c.x1.x), mul2(f, c.x1.y)};
+    c.y0 = C2{mul2(f, c.y0.x), mul2(f, c.y0.y)}, c.y1 = C2{mul2(f, c.y1.x), mul2(f, c.y1.y)};
+    ea += ka;
+    eb += kb;
+}
+
+// block_coeffs for the two angles in the lanes of q0sq (qa: the real root of
+// medium a per lane); outputs [lane][pol].
+template <int POL>
+__device__ __forceinline__ void block_coeffs2(const StageA<float> *__restrict__ sa,
+                                              const StageB<float> *__restrict__ sb, int TL, int tl, int a, int b,
+                                              float2 q0sq, float2 qa, float n0, float Rf[2][2], float Rb[2][2],
+                                              float Tf[2][2])
+{
+    constexpr int RN = RenormEvery<float>::value;
+    const float yi_max = float(kImDeltaMax / kTwoPi);
+    StageA<float> A = sa[b * TL + tl];
+    float absz;
+    const Cx<float> qba = forward_root(Cx<float>{A.d2x + q0sq.x, A.n2y}, &absz);
+    const Cx<float> qbb = forward_root(Cx<float>{A.d2x + q0sq.y, A.n2y}, &absz);
+    const Cx<float> n2_b = {A.d2x + n0 * n0, A.n2y}, in2b = {A.in2x, A.in2y};
+    C2 q_nx = pack2(qba, qbb), g_nx = pack2(cmul(qba, in2b), cmul(qbb, in2b));
+    float2 nqy_nx = neg2(q_nx.y), ngy_nx = neg2(g_nx.y);
+    float Pp = sb[b * TL + tl].ain2;
+    int ePp = 0;
+    float2 Ps = bc2(1.f), Y = bc2(0.f);
+    int ePa = 0, ePb = 0, esa = 0, esb = 0, epa = 0, epb = 0;
+    const C2 one = {bc2(1.f), bc2(0.f)}, zero = {bc2(0.f), bc2(0.f)};
+    Cols2 cs{one, zero, zero, one}, cp{one, zero, zero, one};
+    int cnt = 0;
+    for (int j = b - 1; j > a; --j) {
+        A = sa[j * TL + tl];
+        const StageB<float> B = sb[j * TL + tl];
+        float absa, absb;
+        // a layer inside the block: the branch of q does not reach R and T
+        const Cx<float> qla = inner_root(Cx<float>{A.d2x + q0sq.x, A.n2y}, &absa);
+        const Cx<float> qlb = inner_root(Cx<float>{A.d2x + q0sq.y, A.n2y}, &absb);
+        Ps = mul2(Ps, f2(absa, absb));
+        const float yra = B.dl * qla.x, yrb = B.dl * qlb.x;
+        const float2 yi = f2(fminf(B.dl * qla.y, yi_max), fminf(B.dl * qlb.y, yi_max));
+        Y = add2(Y, yi);
+        float2 sn, cs_;
+        sincos_turn(yra - rintf(yra), &sn.x, &cs_.x);
+        sincos_turn(yrb - rintf(yrb), &sn.y, &cs_.y);
+        const float2 E2 = f2(exp_m2_turn(yi.x), exp_m2_turn(yi.y));
+        const float2 nsn = neg2(sn), ec = mul2(E2, cs_), es = mul2(E2, sn), nes = neg2(es);
+        const C2 q = pack2(qla, qlb);
+        if (POL & 1) {
+            const float2 nqy = neg2(q.y);
+            interface_pair2(q, nqy, q_nx, nqy_nx, cs.x0, cs.x1);
+            interface_pair2(q, nqy, q_nx, nqy_nx, cs.y0, cs.y1);
+            phase2(cs_, sn, nsn, ec, es, nes, cs.x0, cs.x1);
+            phase2(cs_, sn, nsn, ec, es, nes, cs.y0, cs.y1);
+            nqy_nx = nqy;
+        }
+        if (POL & 2) {
+            Pp *= B.ain2;
+            const Cx<float> in2 = {A.in2x, A.in2y};
+            const C2 g = pack2(cmul(qla, in2), cmul(qlb, in2));
+            const float2 ngy = neg2(g.y);
+            interface_pair2(g, ngy, g_nx, ngy_nx, cp.x0, cp.x1);
+            interface_pair2(g, ngy, g_nx, ngy_nx, cp.y0, cp.y1);
+            phase2(cs_, sn, nsn, ec, es, nes, cp.x0, cp.x1);
+            phase2(cs_, sn, nsn, ec, es, nes, cp.y0, cp.y1);
+            g_nx = g;
+            ngy_nx = ngy;
+        }
+        q_nx = q;
+        if (++cnt == RN) {
+            cnt = 0;
+            renorm_scalar(Ps.x, ePa);
+            renorm_scalar(Ps.y, ePb);
+            if (POL & 2) renorm_scalar(Pp, ePp);
+            if (POL & 1) renorm_cols2(cs, esa, esb);
+            if (POL & 2) renorm_cols2(cp, epa, epb);
+        }
+    }
+    // interface a | a+1 per lane; medium a is real
+    A = sa[a * TL + tl];
+    const int e4 = 2 * (b - a);
+    const float na2 = A.d2x + n0 * n0;
+    const Cx<float> in2a = {A.in2x, A.in2y};
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const float qai = i ? qa.y : qa.x, Psi = (i ? Ps.y : Ps.x) * (qai * qai), Yi = i ? Y.y : Y.x;
+        const int ePi = i ? ePb : ePa;
+        const Cx<float> q_a = {qai, 0.f}, q_b = i ? qbb : qba;
+        float u = float(-2.0 * kTwoPi * kLog2e) * Yi;
+        u = fmaxf(u, -1.0e6f);
+        const float un = floorf(u);
+        const float yscale = exp2f(u - un);
+        const int yn = (int)un;
+        if (POL & 1) {
+            Cx<float> x0 = lane(cs.x0, i), x1 = lane(cs.x1, i), y0 = lane(cs.y0, i), y1 = lane(cs.y1, i);
+            const Cx<float> qn = lane(q_nx, i);
+            interface_pair(q_a, qn, x0, x1);
+            interface_pair(q_a, qn, y0, y1);
+            const float ax0 = abs2(x0);
+            Rf[i][0] = abs2(x1) / ax0;
+            Rb[i][0] = abs2(y0) / ax0;
+            Tf[i][0] = q_b.x / qai * ldexpf(Psi * yscale / ax0, e4 + ePi + yn - 2 * (i ? esb : esa));
+        }
+        if (POL & 2) {
+            const Cx<float> g_a = cmul(q_a, in2a), gn = lane(g_nx, i);
+            Cx<float> x0 = lane(cp.x0, i), x1 = lane(cp.x1, i), y0 = lane(cp.y0, i), y1 = lane(cp.y1, i);
+            interface_pair(g_a, gn, x0, x1);
+            interface_pair(g_a, gn, y0, y1);
+            const float ax0 = abs2(x0);
+            Rf[i][1] = abs2(x1) / ax0;
+            Rb[i][1] = abs2(y0) / ax0;
+            const float num = cmul(n2_b, conj(q_b)).x;
+            Tf[i][1] = num / (na2 * qai) * ldexpf(Psi * Pp * yscale / ax0, e4 + ePi + ePp + yn - 2 * (i ? epb : epa));
+        }
+    }
+}
+
+// inc_point for the two angles (sin, cos in the lanes of st, ct): Rv, Tv
+// [lane][pol].  Lanes whose stacks end at different incoherent layers (an
+// evanescent one for one angle only), or at grazing incidence, take the
+// one-angle path each.
+template <int POL>
+__device__ __forceinline__ void inc_point2(const StageA<float> *__restrict__ sa,
+                                           const StageB<float> *__restrict__ sb, const unsigned char *flg, int TL,
+                                           int tl, int L, float n0, float2 st, float2 ct, float Rv[2][2],
+                                           float Tv[2][2])
+{
+    const float2 c0 = f2(n0 * ct.x, n0 * ct.y), q0sq = f2(c0.x * c0.x, c0.y * c0.y);
+    int e[2] = {L + 1, L + 1};
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+        for (int j = 1; j <= L; ++j)
+            if (flg[j] && sa[j * TL + tl].d2x + (i ? q0sq.y : q0sq.x) <= 0.f) {
+                e[i] = j;
+                break;
+            }
+    const bool graze = n0 * st.x >= n0 || n0 * st.y >= n0;
+    if (e[0] != e[1] || graze || !(n0 == n0)) {
+        inc_point<float, POL>(sa, sb, flg, TL, tl, L, n0, st.x, ct.x, Rv[0], Tv[0]);
+        inc_point<float, POL>(sa, sb, flg, TL, tl, L, n0, st.y, ct.y, Rv[1], Tv[1]);
+        return;
+    }
+    const bool cut = e[0] <= L;
+    float P[2][2] = {{1.f, 1.f}, {1.f, 1.f}}, M[2][2] = {{0.f, 0.f}, {0.f, 0.f}}, t[2][2] = {{1.f, 1.f}, {1.f, 1.f}};
+    int b = e[0];
+    while (b > 0) {
+        int a = b - 1;
+        while (a > 0 && !flg[a]) --a;
+        const float2 qa = a == 0 ? c0 : f2(sqrtf(sa[a * TL + tl].d2x + q0sq.x), sqrtf(sa[a * TL + tl].d2x + q0sq.y));
+        float Rf[2][2] = {}, Rb[2][2] = {}, Tf[2][2] = {};
+        block_coeffs2<POL>(sa, sb, TL, tl, a, b, q0sq, qa, n0, Rf, Rb, Tf);
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                if (!(POL & (1 << k))) continue;
+                const float P1 = P[i][k] - Rb[i][k] * M[i][k];
+                const float M1 = Rf[i][k] * P1 + Tf[i][k] * Tf[i][k] * M[i][k];
+                const float inv = 1.f / P1;
+                P[i][k] = 1.f;
+                M[i][k] = M1 * inv;
+                t[i][k] = t[i][k] * Tf[i][k] * inv;
+            }
+        b = a;
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            Rv[i][k] = M[i][k];
+            Tv[i][k] = cut ? 0.f : t[i][k];
+        }
+}
+
+// One block per (stack, tile of TL lambda x TT theta); PAIR: FP32 with two
+// angles per thread, TL x ceil(TT / 2) threads.
+template <typename R, int POL, bool WITH_T, bool PAIR>
 __global__ void __launch_bounds__(kIncThreads) tmm_inc_kernel(const tmm_problem p, const uint8_t *__restrict__ inc,
                                                               int TL, int TT, int n_lt, int n_tt,
                                                               R *__restrict__ Rout, R *__restrict__ Tout)
@@ -153,7 +395,7 @@ __global__ void __launch_bounds__(kIncThreads) tmm_inc_kernel(const tmm_problem 
     const int s = (int)(item / per_stack);
     const int rr = (int)(item - (long long)s * per_stack);
     const int lt = rr / n_tt, ttile = rr % n_tt;
-    const int tid = threadIdx.y * TL + threadIdx.x, nthr = TL * TT;
+    const int tid = threadIdx.y * TL + threadIdx.x, nthr = TL * (int)blockDim.y;
     const int L = layers_of(p, s);
     const int l0 = lt * TL;
     if (L >= 0) {
@@ -163,73 +405,49 @@ __global__ void __launch_bounds__(kIncThreads) tmm_inc_kernel(const tmm_problem 
     }
     __syncthreads();
 
-    const int tl = threadIdx.x, l = l0 + tl, a_ = ttile * TT + threadIdx.y;
-    if (l >= p.n_lambda || a_ >= p.n_theta) return;  // no barrier follows
-    R Rv[2] = {nan_w<R>(), nan_w<R>()}, Tv[2] = {nan_w<R>(), nan_w<R>()};
+    const int tl = threadIdx.x, l = l0 + tl;
+    const int t0 = ttile * TT, t_end = min(t0 + TT, p.n_theta);
+    const int a0 = PAIR ? t0 + 2 * (int)threadIdx.y : t0 + (int)threadIdx.y;
+    if (l >= p.n_lambda || a0 >= t_end) return;  // no barrier follows
+    const int np = PAIR && a0 + 1 < t_end ? 2 : 1;
+    R Rv[2][2], Tv[2][2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) Rv[i][0] = Rv[i][1] = Tv[i][0] = Tv[i][1] = nan_w<R>();
     bool ok = L >= 0;
     if (ok)
         for (int j = 1; j <= L; ++j)
             if (flg[j] && sa[j * TL + tl].n2y != R(0)) ok = false;  // absorbing incoherent layer
     if (ok) {
-        R sth, cth;
-        sincos_w(((const R *)p.theta)[a_], &sth, &cth);
+        const R *th = (const R *)p.theta;
         const R n0 = n0s[tl];
-        const R beta = n0 * sth, c0 = n0 * cth, q0sq = c0 * c0;
-        if (beta >= n0) {  // grazing (false for a NaN n_0)
-            Rv[0] = Rv[1] = R(1);
-            Tv[0] = Tv[1] = R(0);
-        } else if (n0 == n0) {
-            // the first evanescent incoherent layer ends the stack
-            int e = L + 1;
-            bool cut = false;
-            for (int j = 1; j <= L; ++j)
-                if (flg[j] && sa[j * TL + tl].d2x + q0sq <= R(0)) {
-                    e = j;
-                    cut = true;
-                    break;
-                }
-            R P[2] = {R(1), R(1)}, M[2] = {R(0), R(0)}, t[2] = {R(1), R(1)};
-            int b = e;
-            while (b > 0) {
-                int a = b - 1;
-                while (a > 0 && !flg[a]) --a;
-                const R qa = a == 0 ? c0 : sqrt(sa[a * TL + tl].d2x + q0sq);
-                R Rf[2] = {R(0), R(0)}, Rb[2] = {R(0), R(0)}, Tf[2] = {R(0), R(0)};
-                block_coeffs<R, POL>(sa, sb, TL, tl, a, b, q0sq, qa, n0, Rf, Rb, Tf);
-#pragma unroll
-                for (int k = 0; k < 2; ++k) {
-                    if (!(POL & (1 << k))) continue;
-                    const R P1 = P[k] - Rb[k] * M[k];
-                    const R M1 = Rf[k] * P1 + Tf[k] * Tf[k] * M[k];
-                    const R inv = R(1) / P1;  // keep P = 1
-                    P[k] = R(1);
-                    M[k] = M1 * inv;
-                    t[k] = t[k] * Tf[k] * inv;
-                }
-                b = a;
-            }
-#pragma unroll
-            for (int k = 0; k < 2; ++k) {
-                Rv[k] = M[k];
-                Tv[k] = cut ? R(0) : t[k];
-            }
+        if constexpr (PAIR) {
+            float2 st, ct;
+            sincos_w(th[a0], &st.x, &ct.x);
+            sincos_w(th[np == 2 ? a0 + 1 : a0], &st.y, &ct.y);
+            inc_point2<POL>(sa, sb, flg, TL, tl, L, n0, st, ct, Rv, Tv);
+        } else {
+            R sth, cth;
+            sincos_w(th[a0], &sth, &cth);
+            inc_point<R, POL>(sa, sb, flg, TL, tl, L, n0, sth, cth, Rv[0], Tv[0]);
         }
     }
     const long long plane = (long long)p.S * p.n_theta * p.n_lambda;
-    const long long o = ((long long)s * p.n_theta + a_) * p.n_lambda + l;
-    if (POL & 4) {
-        Rout[o] = R(0.5) * (Rv[0] + Rv[1]);
-        if (WITH_T) Tout[o] = R(0.5) * (Tv[0] + Tv[1]);
-    } else {
-        int pi = 0;
-        if (POL & 1) {
-            Rout[o] = Rv[0];
-            if (WITH_T) Tout[o] = Tv[0];
-            ++pi;
-        }
-        if (POL & 2) {
-            Rout[pi * plane + o] = Rv[1];
-            if (WITH_T) Tout[pi * plane + o] = Tv[1];
+    for (int i = 0; i < np; ++i) {
+        const long long o = ((long long)s * p.n_theta + a0 + i) * p.n_lambda + l;
+        if (POL & 4) {
+            Rout[o] = R(0.5) * (Rv[i][0] + Rv[i][1]);
+            if (WITH_T) Tout[o] = R(0.5) * (Tv[i][0] + Tv[i][1]);
+        } else {
+            int pi = 0;
+            if (POL & 1) {
+                Rout[o] = Rv[i][0];
+                if (WITH_T) Tout[o] = Tv[i][0];
+                ++pi;
+            }
+            if (POL & 2) {
+                Rout[pi * plane + o] = Rv[i][1];
+                if (WITH_T) Tout[pi * plane + o] = Tv[i][1];
+            }
         }
     }
 }
@@ -240,11 +458,11 @@ size_t inc_smem(const tmm_problem *p, int TL)
     return (size_t)(p->L_max + 2) * TL * (6 * r) + (size_t)TL * r + (size_t)(p->L_max + 2) + 16;
 }
 
-template <typename R, int POL, bool WITH_T>
-tmm_status launch_inc_typed(const tmm_problem *p, const uint8_t *inc, int TL, int TT, int n_lt, int n_tt,
-                            long long items, size_t smem, R *Ro, R *To, cudaStream_t st)
+template <typename R, int POL, bool WITH_T, bool PAIR>
+tmm_status launch_inc_shaped(const tmm_problem *p, const uint8_t *inc, int TL, int TT, int n_lt, int n_tt,
+                             long long items, size_t smem, R *Ro, R *To, cudaStream_t st)
 {
-    auto k = tmm_inc_kernel<R, POL, WITH_T>;
+    auto k = tmm_inc_kernel<R, POL, WITH_T, PAIR>;
     if (smem > 48 * 1024) {
         // once per (instantiation, device) and size: repeated launches and graph
         // capture stay free of attribute calls
@@ -259,8 +477,19 @@ tmm_status launch_inc_typed(const tmm_problem *p, const uint8_t *inc, int TL, in
             set_bytes[dev] = (int)smem;
         }
     }
-    k<<<(unsigned)items, dim3(TL, TT), smem, st>>>(*p, inc, TL, TT, n_lt, n_tt, Ro, To);
+    k<<<(unsigned)items, dim3(TL, PAIR ? (TT + 1) / 2 : TT), smem, st>>>(*p, inc, TL, TT, n_lt, n_tt, Ro, To);
     return check_launch();
+}
+
+// FP32 tiles of two or more angles run two angles per thread.
+template <typename R, int POL, bool WITH_T>
+tmm_status launch_inc_typed(const tmm_problem *p, const uint8_t *inc, int TL, int TT, int n_lt, int n_tt,
+                            long long items, size_t smem, R *Ro, R *To, cudaStream_t st)
+{
+    if constexpr (std::is_same<R, float>::value) {
+        if (TT >= 2) return launch_inc_shaped<R, POL, WITH_T, true>(p, inc, TL, TT, n_lt, n_tt, items, smem, Ro, To, st);
+    }
+    return launch_inc_shaped<R, POL, WITH_T, false>(p, inc, TL, TT, n_lt, n_tt, items, smem, Ro, To, st);
 }
 
 template <typename R>
@@ -302,8 +531,9 @@ extern "C" TMM_API tmm_status tmm_inc_batched(const tmm_problem *p, const uint8_
     s = device_info(&di);
     if (s != TMM_OK) return s;
     const int TT = std::min(p->n_theta, 32);
+    const int rows = (p->prec == TMM_F32 && TT >= 2) ? (TT + 1) / 2 : TT;  // thread rows per block
     int TL = 1;
-    while (TL * TT * 2 <= kIncThreads) TL *= 2;
+    while (TL * rows * 2 <= kIncThreads) TL *= 2;
     while (TL > 1 && TL / 2 >= p->n_lambda) TL /= 2;
     while (TL > 1 && inc_smem(p, TL) > (size_t)di.max_smem_optin) TL /= 2;
     const size_t smem = inc_smem(p, TL);

@@ -105,6 +105,23 @@ def test_evanescent_cut_and_absorbing_incoherent_layer():
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_evanescent_cut_at_some_angles(prec):
+    # FP32 runs two angles per thread: the pairs (0, 70 deg) end at different
+    # layers (one-angle fallback), (72, 75 deg) both at the evanescent slab,
+    # and the odd fifth angle rides alone
+    lam = np.array([600.0, 650.0, 700.0])
+    th = np.deg2rad([0.0, 70.0, 72.0, 75.0, 30.0])
+    nd = np.array([[1.8, 2.2, 1.5, 2.0, 1.0], [1.8, 1.6, 1.5, 2.3, 1.2]], dtype=np.complex128)
+    d = np.array([[110.0, 1e6, 90.0], [140.0, 1e5, 60.0]])
+    flags = np.array([[0, 1, 0], [0, 1, 0]], dtype=np.uint8)
+    w = W.Workload("cut", theta=th, lam=lam, d=d, n_direct=np.repeat(nd[:, :, None], 3, 2))
+    Ro, To = oracle_inc(w, flags)
+    R, T = gpu_inc(w, flags, prec)
+    assert np.max(np.abs(R - Ro)) <= TOL[prec] and np.max(np.abs(T - To)) <= TOL[prec]
+    assert np.all(T[:, :, 1:4, :] == 0.0)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
 def test_coated_substrate_workload_sample(prec):
     # the benchmark's workload (gathered material table, 1 mm incoherent plate)
     w = W.coated_substrate(S=4, n_lambda=23, n_theta=6)
