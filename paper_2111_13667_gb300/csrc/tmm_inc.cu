@@ -22,6 +22,7 @@
 #include <type_traits>
 
 #include "tmm_device.cuh"
+#include "tmm_pair.cuh"
 #include "tmm_internal.h"
 
 namespace tmm {
@@ -189,27 +190,6 @@ __device__ __forceinline__ void inc_point(const StageA<R> *__restrict__ sa, cons
 }
 
 // ---------------------------------------------------------------- FP32: two angles per thread
-// Both columns of a block's matrix for the two angles of a thread, on the
-// lanes of the paired FP32 instructions (see tmm_fwd.cu).
-struct Cols2 {
-    C2 x0, x1, y0, y1;
-};
-
-__device__ __forceinline__ void renorm_cols2(Cols2 &c, int &ea, int &eb)
-{
-    auto mx = [](const C2 &v, int i) {
-        return i ? fmaxf(fabsf(v.x.y), fabsf(v.y.y)) : fmaxf(fabsf(v.x.x), fabsf(v.y.x));
-    };
-    const float ma = fmaxf(fmaxf(mx(c.x0, 0), mx(c.x1, 0)), fmaxf(mx(c.y0, 0), mx(c.y1, 0)));
-    const float mb = fmaxf(fmaxf(mx(c.x0, 1), mx(c.x1, 1)), fmaxf(mx(c.y0, 1), mx(c.y1, 1)));
-    const int ka = exponent_of(ma), kb = exponent_of(mb);
-    const float2 f = f2(pow2_neg<float>(ka), pow2_neg<float>(kb));
-    c.x0 = C2{mul2(f, c.x0.x), mul2(f, c.x0.y)}, c.x1 = C2{mul2(f, c.x1.x), mul2(f, c.x1.y)};
-    c.y0 = C2{mul2(f, c.y0.x), mul2(f, c.y0.y)}, c.y1 = C2{mul2(f, c.y1.x), mul2(f, c.y1.y)};
-    ea += ka;
-    eb += kb;
-}
-
 // block_coeffs for the two angles in the lanes of q0sq (qa: the real root of
 // medium a per lane); outputs [lane][pol].
 template <int POL>

@@ -21,8 +21,10 @@
 
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 
 #include "tmm_device.cuh"
+#include "tmm_pair.cuh"
 #include "tmm_internal.h"
 
 namespace tmm {
@@ -322,7 +324,219 @@ __device__ __forceinline__ void pc_point(const StageA<R> *__restrict__ sa, const
     for (int c = 0; c < 4; ++c) out[c] = acc[c];
 }
 
-template <typename R, int POL, bool WITH_T>
+// ---------------------------------------------------------------- FP32: two angles per thread
+// pc_point for the two angles in the lanes of st, ct (see tmm_fwd.cu): the
+// sweeps and the node products on paired lanes; the nodes' thicknesses are
+// the same for both lanes.  out[lane][{R_s, T_s, R_p, T_p}].
+template <int POL>
+__device__ __forceinline__ void pc_point2(const StageA<float> *__restrict__ sa,
+                                          const StageB<float> *__restrict__ sb, int TL, int tl, int L, int jp,
+                                          float sig, float inv_lam, float dj, float n0, float2 st, float2 ct,
+                                          const Nodes<float> &nd, float out[2][4])
+{
+    constexpr int RN = RenormEvery<float>::value;
+    const float2 c0 = f2(n0 * ct.x, n0 * ct.y), q0sq = f2(c0.x * c0.x, c0.y * c0.y);
+    const float yi_max = float(kImDeltaMax / kTwoPi);
+    StageA<float> A = sa[(L + 1) * TL + tl];
+    float absz;
+    const Cx<float> qoa = forward_root(Cx<float>{A.d2x + q0sq.x, A.n2y}, &absz);
+    const Cx<float> qob = forward_root(Cx<float>{A.d2x + q0sq.y, A.n2y}, &absz);
+    const Cx<float> n2_out = {A.d2x + n0 * n0, A.n2y}, in2o = {A.in2x, A.in2y};
+    C2 q_nx = pack2(qoa, qob), g_nx = pack2(cmul(qoa, in2o), cmul(qob, in2o));
+    float2 nqy_nx = neg2(q_nx.y), ngy_nx = neg2(g_nx.y);
+    float2 Ps = bc2(1.f), Y = bc2(0.f);
+    float Pp = (POL & 2) ? sb[(L + 1) * TL + tl].ain2 : 1.f;
+    int ePa = 0, ePb = 0, ePp = 0, esa = 0, esb = 0, epa = 0, epb = 0;
+    C2 s0 = {bc2(1.f), bc2(0.f)}, s1 = {bc2(0.f), bc2(0.f)}, p0 = s0, p1 = s1;
+    int cnt = 0;
+    auto rescale = [&]() {
+        renorm_scalar(Ps.x, ePa);
+        renorm_scalar(Ps.y, ePb);
+        if (POL & 2) renorm_scalar(Pp, ePp);
+        if (POL & 1) renorm_pair2(s0, s1, esa, esb);
+        if (POL & 2) renorm_pair2(p0, p1, epa, epb);
+    };
+    // right of the partial layer (the whole stack when jp = 0)
+    for (int j = L; j > jp; --j) {
+        A = sa[j * TL + tl];
+        const StageB<float> B = sb[j * TL + tl];
+        float absa, absb;
+        const Cx<float> qa = inner_root(Cx<float>{A.d2x + q0sq.x, A.n2y}, &absa);
+        const Cx<float> qb = inner_root(Cx<float>{A.d2x + q0sq.y, A.n2y}, &absb);
+        Ps = mul2(Ps, f2(absa, absb));
+        const Phase2 f = phase_pair(B.dl, qa, qb, yi_max);
+        Y = add2(Y, f.yi);
+        const C2 q = pack2(qa, qb);
+        if (POL & 1) {
+            const float2 nqy = neg2(q.y);
+            interface_pair2(q, nqy, q_nx, nqy_nx, s0, s1);
+            phase2(f.cs, f.sn, f.nsn, f.ec, f.es, f.nes, s0, s1);
+            nqy_nx = nqy;
+        }
+        if (POL & 2) {
+            Pp *= B.ain2;
+            const Cx<float> in2 = {A.in2x, A.in2y};
+            const C2 g = pack2(cmul(qa, in2), cmul(qb, in2));
+            const float2 ngy = neg2(g.y);
+            interface_pair2(g, ngy, g_nx, ngy_nx, p0, p1);
+            phase2(f.cs, f.sn, f.nsn, f.ec, f.es, f.nes, p0, p1);
+            g_nx = g;
+            ngy_nx = ngy;
+        }
+        q_nx = q;
+        if (++cnt == RN) {
+            cnt = 0;
+            rescale();
+        }
+    }
+    const int e4 = 2 * (L + 1);
+    const StageA<float> A0 = sa[tl];
+    const Cx<float> in20 = {A0.in2x, A0.in2y};
+    auto finish = [&](int i, Cx<float> xs0, Cx<float> xs1, Cx<float> xp0, Cx<float> xp1, float Yt, int esx,
+                      int epx, float res[4]) {
+        const float c0i = i ? c0.y : c0.x;
+        const Cx<float> q_out = i ? qob : qoa;
+        float u = float(-2.0 * kTwoPi * kLog2e) * Yt;
+        u = fmaxf(u, -1.0e6f);
+        const float un = floorf(u);
+        const float yscale = exp2f(u - un);
+        const int yn = (int)un;
+        const float Pst = (i ? Ps.y : Ps.x) * (c0i * c0i);
+        const int ePi = i ? ePb : ePa;
+        if (POL & 1) rt_of(xs0, xs1, Pst * yscale, e4 + ePi + yn - 2 * esx, q_out.x, c0i, res[0], res[1]);
+        if (POL & 2)
+            rt_of(xp0, xp1, Pst * Pp * yscale, e4 + ePi + ePp + yn - 2 * epx, cmul(n2_out, conj(q_out)).x,
+                  n0 * n0 * c0i, res[2], res[3]);
+        if (n0 * (i ? st.y : st.x) >= n0) res[0] = res[2] = 1.f, res[1] = res[3] = 0.f;  // grazing
+    };
+    if (jp == 0) {
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const Cx<float> q0 = {i ? c0.y : c0.x, 0.f}, g0 = cmul(q0, in20);
+            Cx<float> xs0 = lane(s0, i), xs1 = lane(s1, i), xp0 = lane(p0, i), xp1 = lane(p1, i);
+            if (POL & 1) interface_pair(q0, lane(q_nx, i), xs0, xs1);
+            if (POL & 2) interface_pair(g0, lane(g_nx, i), xp0, xp1);
+            finish(i, xs0, xs1, xp0, xp1, i ? Y.y : Y.x, i ? esb : esa, i ? epb : epa, out[i]);
+        }
+        return;
+    }
+    // layer jp: its roots and interface jp | jp+1; its phase waits for the nodes
+    A = sa[jp * TL + tl];
+    float absa, absb;
+    const Cx<float> qja = inner_root(Cx<float>{A.d2x + q0sq.x, A.n2y}, &absa);
+    const Cx<float> qjb = inner_root(Cx<float>{A.d2x + q0sq.y, A.n2y}, &absb);
+    Ps = mul2(Ps, f2(absa, absb));
+    const C2 qj = pack2(qja, qjb);
+    const float2 nqjy = neg2(qj.y);
+    C2 gj = {bc2(0.f), bc2(0.f)};
+    float2 ngjy = bc2(0.f);
+    if (POL & 1) interface_pair2(qj, nqjy, q_nx, nqy_nx, s0, s1);
+    if (POL & 2) {
+        Pp *= sb[jp * TL + tl].ain2;
+        const Cx<float> in2 = {A.in2x, A.in2y};
+        gj = pack2(cmul(qja, in2), cmul(qjb, in2));
+        ngjy = neg2(gj.y);
+        interface_pair2(gj, ngjy, g_nx, ngy_nx, p0, p1);
+    }
+    rescale();
+    // the block left of layer jp: both columns of ML, from the identity
+    const C2 one = {bc2(1.f), bc2(0.f)}, zero = {bc2(0.f), bc2(0.f)};
+    Cols2 cs{one, zero, zero, one}, cp{one, zero, zero, one};
+    int elsa = 0, elsb = 0, elpa = 0, elpb = 0;
+    C2 qr = qj, gr = gj;
+    float2 nqry = nqjy, ngry = ngjy;
+    cnt = 0;
+    for (int j = jp - 1; j >= 1; --j) {
+        A = sa[j * TL + tl];
+        const StageB<float> B = sb[j * TL + tl];
+        float aa, ab;
+        const Cx<float> qa = inner_root(Cx<float>{A.d2x + q0sq.x, A.n2y}, &aa);
+        const Cx<float> qb = inner_root(Cx<float>{A.d2x + q0sq.y, A.n2y}, &ab);
+        Ps = mul2(Ps, f2(aa, ab));
+        const Phase2 f = phase_pair(B.dl, qa, qb, yi_max);
+        Y = add2(Y, f.yi);
+        const C2 q = pack2(qa, qb);
+        const float2 nqy = neg2(q.y);
+        if (POL & 1) cols_step2(cs, q, nqy, qr, nqry, f);
+        if (POL & 2) {
+            Pp *= B.ain2;
+            const Cx<float> in2 = {A.in2x, A.in2y};
+            const C2 g = pack2(cmul(qa, in2), cmul(qb, in2));
+            const float2 ngy = neg2(g.y);
+            cols_step2(cp, g, ngy, gr, ngry, f);
+            gr = g;
+            ngry = ngy;
+        }
+        qr = q;
+        nqry = nqy;
+        if (++cnt == RN) {
+            cnt = 0;
+            renorm_scalar(Ps.x, ePa);
+            renorm_scalar(Ps.y, ePb);
+            if (POL & 2) renorm_scalar(Pp, ePp);
+            if (POL & 1) renorm_cols2(cs, elsa, elsb);
+            if (POL & 2) renorm_cols2(cp, elpa, elpb);
+        }
+    }
+    // interface 0 | 1 (q_0 = n_0 cos(theta) real per lane)
+    const C2 Q0 = {c0, bc2(0.f)};
+    if (POL & 1) {
+        interface_pair2(Q0, bc2(0.f), qr, nqry, cs.x0, cs.x1);
+        interface_pair2(Q0, bc2(0.f), qr, nqry, cs.y0, cs.y1);
+    }
+    if (POL & 2) {
+        const C2 G0 = pack2(cmul(Cx<float>{c0.x, 0.f}, in20), cmul(Cx<float>{c0.y, 0.f}, in20));
+        interface_pair2(G0, neg2(G0.y), gr, ngry, cp.x0, cp.x1);
+        interface_pair2(G0, neg2(G0.y), gr, ngry, cp.y0, cp.y1);
+    }
+    // node-independent products: row a of x_0 = (ML_a0 y0) e^{-i delta} + (ML_a1 y1) e^{+i delta}
+    C2 sA = zero, sB = zero, sC = zero, sD = zero, pA = zero, pB = zero, pC = zero, pD = zero;
+    if (POL & 1) {
+        const float2 n0y = neg2(s0.y), n1y = neg2(s1.y);
+        sA = cmul2(cs.x0, s0, n0y), sB = cmul2(cs.y0, s1, n1y);
+        sC = cmul2(cs.x1, s0, n0y), sD = cmul2(cs.y1, s1, n1y);
+    }
+    if (POL & 2) {
+        const float2 n0y = neg2(p0.y), n1y = neg2(p1.y);
+        pA = cmul2(cp.x0, p0, n0y), pB = cmul2(cp.y0, p1, n1y);
+        pC = cmul2(cp.x1, p0, n0y), pD = cmul2(cp.y1, p1, n1y);
+    }
+    float acc[2][4] = {};
+    for (int i = 0; i < nd.n_half; ++i) {
+        const int nsign = (nd.odd && i == nd.n_half - 1) ? 1 : 2;
+        for (int sgn = 0; sgn < nsign; ++sgn) {
+            const float D = sig * (sgn ? -nd.off[i] : nd.off[i]);
+            const float dl = fmaxf(dj + D, 0.f) * inv_lam;
+            const Phase2 f = phase_pair(dl, qja, qjb, yi_max);
+            C2 xs0 = zero, xs1 = zero, xp0 = zero, xp1 = zero;
+            if (POL & 1) {
+                const C2 a = turn_minus(sA, f), b = turn_plus(sB, f), c = turn_minus(sC, f), d = turn_plus(sD, f);
+                xs0 = C2{add2(a.x, b.x), add2(a.y, b.y)};
+                xs1 = C2{add2(c.x, d.x), add2(c.y, d.y)};
+            }
+            if (POL & 2) {
+                const C2 a = turn_minus(pA, f), b = turn_plus(pB, f), c = turn_minus(pC, f), d = turn_plus(pD, f);
+                xp0 = C2{add2(a.x, b.x), add2(a.y, b.y)};
+                xp1 = C2{add2(c.x, d.x), add2(c.y, d.y)};
+            }
+#pragma unroll
+            for (int ln = 0; ln < 2; ++ln) {
+                float res[4] = {0.f, 0.f, 0.f, 0.f};
+                finish(ln, lane(xs0, ln), lane(xs1, ln), lane(xp0, ln), lane(xp1, ln),
+                       (ln ? Y.y : Y.x) + (ln ? f.yi.y : f.yi.x), (ln ? esb : esa) + (ln ? elsb : elsa),
+                       (ln ? epb : epa) + (ln ? elpb : elpa), res);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[ln][c] = fmaf(nd.w[i], res[c], acc[ln][c]);
+            }
+        }
+    }
+#pragma unroll
+    for (int ln = 0; ln < 2; ++ln)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) out[ln][c] = acc[ln][c];
+}
+
+template <typename R, int POL, bool WITH_T, bool PAIR>
 __global__ void __launch_bounds__(kPcThreads) tmm_pcoh_kernel(const tmm_problem p, const int32_t *__restrict__ layer,
                                                                const R *__restrict__ sigma, const Nodes<R> nd, int TL,
                                                                int TT, int n_lt, int n_tt, R *__restrict__ Rout,
@@ -338,40 +552,55 @@ __global__ void __launch_bounds__(kPcThreads) tmm_pcoh_kernel(const tmm_problem 
     const int s = (int)(item / per_stack);
     const int rr = (int)(item - (long long)s * per_stack);
     const int lt = rr / n_tt, ttile = rr % n_tt;
-    const int tid = threadIdx.y * TL + threadIdx.x, nthr = TL * TT;
+    const int tid = threadIdx.y * TL + threadIdx.x, nthr = TL * (int)blockDim.y;
     const int L = layers_of(p, s);
     const int l0 = lt * TL;
     if (L >= 0) fill_stage<R>(p, s, L, l0, TL, sa, sb, n0s, tid, nthr);
     __syncthreads();
-    const int tl = threadIdx.x, l = l0 + tl, a_ = ttile * TT + threadIdx.y;
-    if (l >= p.n_lambda || a_ >= p.n_theta) return;  // no barrier follows
+    const int tl = threadIdx.x, l = l0 + tl;
+    const int t0 = ttile * TT, t_end = min(t0 + TT, p.n_theta);
+    const int a0 = PAIR ? t0 + 2 * (int)threadIdx.y : t0 + (int)threadIdx.y;
+    if (l >= p.n_lambda || a0 >= t_end) return;  // no barrier follows
+    const int np = PAIR && a0 + 1 < t_end ? 2 : 1;
 
-    R out[4] = {nan_w<R>(), nan_w<R>(), nan_w<R>(), nan_w<R>()};
+    R out[2][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) out[i][0] = out[i][1] = out[i][2] = out[i][3] = nan_w<R>();
     const int jp = layer[s];
     const R sig = sigma[s];
     const bool valid = L >= 0 && jp >= 0 && jp <= L && sig >= R(0) && sig <= R(1e30);  // false for NaN
     if (valid) {
-        R sth, cth;
-        sincos_w(((const R *)p.theta)[a_], &sth, &cth);
+        const R *th = (const R *)p.theta;
         const R inv_lam = R(1) / ((const R *)p.lambda)[l];
         const R dj = jp >= 1 ? ((const R *)p.d)[(long long)s * p.L_max + (jp - 1)] : R(0);
-        pc_point<R, POL>(sa, sb, TL, tl, L, jp, sig, inv_lam, dj, n0s[tl], sth, cth, nd, out);
+        if constexpr (PAIR) {
+            float2 st, ct;
+            sincos_w(th[a0], &st.x, &ct.x);
+            sincos_w(th[np == 2 ? a0 + 1 : a0], &st.y, &ct.y);
+            pc_point2<POL>(sa, sb, TL, tl, L, jp, sig, inv_lam, dj, n0s[tl], st, ct, nd, out);
+        } else {
+            R sth, cth;
+            sincos_w(th[a0], &sth, &cth);
+            pc_point<R, POL>(sa, sb, TL, tl, L, jp, sig, inv_lam, dj, n0s[tl], sth, cth, nd, out[0]);
+        }
     }
     const long long plane = (long long)p.S * p.n_theta * p.n_lambda;
-    const long long o = ((long long)s * p.n_theta + a_) * p.n_lambda + l;
-    if (POL & 4) {
-        Rout[o] = R(0.5) * (out[0] + out[2]);
-        if (WITH_T) Tout[o] = R(0.5) * (out[1] + out[3]);
-    } else {
-        int pi = 0;
-        if (POL & 1) {
-            Rout[o] = out[0];
-            if (WITH_T) Tout[o] = out[1];
-            ++pi;
-        }
-        if (POL & 2) {
-            Rout[pi * plane + o] = out[2];
-            if (WITH_T) Tout[pi * plane + o] = out[3];
+    for (int i = 0; i < np; ++i) {
+        const long long o = ((long long)s * p.n_theta + a0 + i) * p.n_lambda + l;
+        if (POL & 4) {
+            Rout[o] = R(0.5) * (out[i][0] + out[i][2]);
+            if (WITH_T) Tout[o] = R(0.5) * (out[i][1] + out[i][3]);
+        } else {
+            int pi = 0;
+            if (POL & 1) {
+                Rout[o] = out[i][0];
+                if (WITH_T) Tout[o] = out[i][1];
+                ++pi;
+            }
+            if (POL & 2) {
+                Rout[pi * plane + o] = out[i][2];
+                if (WITH_T) Tout[pi * plane + o] = out[i][3];
+            }
         }
     }
 }
@@ -382,11 +611,12 @@ size_t pcoh_smem(const tmm_problem *p, int TL)
     return (size_t)(p->L_max + 2) * TL * (6 * r) + (size_t)TL * r;
 }
 
-template <typename R, int POL, bool WITH_T>
-tmm_status launch_pcoh_k(const tmm_problem *p, const int32_t *layer, const R *sigma, const Nodes<R> &nd, int TL,
-                         int TT, int n_lt, int n_tt, long long items, size_t smem, R *Ro, R *To, cudaStream_t st)
+template <typename R, int POL, bool WITH_T, bool PAIR>
+tmm_status launch_pcoh_shaped(const tmm_problem *p, const int32_t *layer, const R *sigma, const Nodes<R> &nd,
+                              int TL, int TT, int n_lt, int n_tt, long long items, size_t smem, R *Ro, R *To,
+                              cudaStream_t st)
 {
-    auto k = tmm_pcoh_kernel<R, POL, WITH_T>;
+    auto k = tmm_pcoh_kernel<R, POL, WITH_T, PAIR>;
     if (smem > 48 * 1024) {
         // once per (instantiation, device) and size
         static int set_bytes[64] = {};
@@ -400,8 +630,23 @@ tmm_status launch_pcoh_k(const tmm_problem *p, const int32_t *layer, const R *si
             set_bytes[dev] = (int)smem;
         }
     }
-    k<<<(unsigned)items, dim3(TL, TT), smem, st>>>(*p, layer, sigma, nd, TL, TT, n_lt, n_tt, Ro, To);
+    k<<<(unsigned)items, dim3(TL, PAIR ? (TT + 1) / 2 : TT), smem, st>>>(*p, layer, sigma, nd, TL, TT, n_lt, n_tt,
+                                                                       Ro, To);
     return check_launch();
+}
+
+// FP32 tiles of two or more angles run two angles per thread.
+template <typename R, int POL, bool WITH_T>
+tmm_status launch_pcoh_k(const tmm_problem *p, const int32_t *layer, const R *sigma, const Nodes<R> &nd, int TL,
+                         int TT, int n_lt, int n_tt, long long items, size_t smem, R *Ro, R *To, cudaStream_t st)
+{
+    if constexpr (std::is_same<R, float>::value) {
+        if (TT >= 2)
+            return launch_pcoh_shaped<R, POL, WITH_T, true>(p, layer, sigma, nd, TL, TT, n_lt, n_tt, items, smem, Ro,
+                                                             To, st);
+    }
+    return launch_pcoh_shaped<R, POL, WITH_T, false>(p, layer, sigma, nd, TL, TT, n_lt, n_tt, items, smem, Ro, To,
+                                                      st);
 }
 
 template <typename R>
@@ -447,8 +692,9 @@ extern "C" TMM_API tmm_status tmm_pcoh_batched(const tmm_problem *p, const int32
     s = device_info(&di);
     if (s != TMM_OK) return s;
     const int TT = std::min(p->n_theta, 32);
+    const int rows = (p->prec == TMM_F32 && TT >= 2) ? (TT + 1) / 2 : TT;  // thread rows per block
     int TL = 1;
-    while (TL * TT * 2 <= kPcThreads) TL *= 2;
+    while (TL * rows * 2 <= kPcThreads) TL *= 2;
     while (TL > 1 && TL / 2 >= p->n_lambda) TL /= 2;
     while (TL > 1 && pcoh_smem(p, TL) > (size_t)di.max_smem_optin) TL /= 2;
     const size_t smem = pcoh_smem(p, TL);
