@@ -140,3 +140,17 @@ def test_deep_stack_profile(prec):
     E = gpu_field(w, prec, 3)
     rel = np.max(np.abs(E - Eo) / np.maximum(1.0, np.abs(Eo)))
     assert rel <= (1e-10 if prec == "f64" else 1e-4), rel
+
+
+def test_field_profile_f32_pairs_grazing_and_unpolarised():
+    # FP32 runs two angles per thread: the pair (20, 90 deg) meets grazing
+    # incidence (the one-angle path per lane), 55 deg rides alone
+    w0 = lossy_workload(56, S=3, L=4, n_lambda=5, n_theta=3)
+    w = W.Workload("lossy", theta=np.deg2rad([20.0, 90.0, 55.0]), lam=w0.lam, d=w0.d, n_direct=w0.n_direct)
+    n = oracle_index(w)
+    Eo = np.stack([ab.field_profile(pol, n, w.d, w.theta, w.lam, 3) for pol in "sp"])
+    E = gpu_field(w, "f32", 3)
+    assert np.max(np.abs(E - Eo) / np.maximum(1.0, np.abs(Eo))) <= 1e-4
+    assert np.all(E[:, :, :, :, 1, :] == 0.0)
+    Eu = gpu_field(w, "f32", 3, pols="u")
+    assert np.max(np.abs(Eu[0] - 0.5 * (Eo[0] + Eo[1])) / np.maximum(1.0, np.abs(Eo[0]))) <= 1e-4
