@@ -22,6 +22,7 @@
 
 #include "tmm_device.cuh"
 #include "tmm_df64.cuh"
+#include "tmm_df64x2.cuh"
 #include "tmm_internal.h"
 
 namespace tmm {
@@ -32,6 +33,7 @@ using df::dd;
 namespace {
 
 constexpr int kDfMaxThreads = 512;
+constexpr int kDfPairThreads = 256;
 
 struct DfTables {
     float4 sc[64];  // {sin hi, sin lo, cos hi, cos lo} of 2 pi k / 256
@@ -148,6 +150,51 @@ __device__ __forceinline__ void renorm_dd(dd &m, int &e)
 
 __device__ __forceinline__ cdd ld_c(float h1, float l1, float h2, float l2) { return cdd{dd{h1, l1}, dd{h2, l2}}; }
 
+// Interface 0 | 1 and Eqs. 5-6 for one point from the sweep's state after
+// layer 1 (the dd form of tmm_fwd.cu's finish_point).
+template <int POL>
+__device__ __forceinline__ void finish_dd(const DStage &A, const float2 *e2, const cdd &q_out, const cdd &n2_out,
+                                          const cdd &q_nx, const cdd &g_nx, const cdd &s0, const cdd &s1,
+                                          const cdd &p0, const cdd &p1, dd Ps, int eP, dd Y, int es, int ep, int L,
+                                          dd n0, dd cth, dd beta, dd c0, dd q0sq, dd Pp, int Pp_e, double out[4])
+{
+    // grazing: cos(theta) <= 0 or beta >= n_0 (both false for a NaN n_0)
+    const bool grazing = cth.hi <= 0.0f || (!dd_less(beta, n0) && beta.hi == beta.hi);
+    const cdd q0{c0, df::make(0.0f)};
+    Ps = df::mul(Ps, q0sq);
+    const int e4 = 2 * (L + 1);
+    // 2^{-2 K Y} split as m * 2^n
+    int yn;
+    const dd ym = exp2_dd(df::mul(Y, dconst(-4.0 * kPi * 1.4426950408889634073599246810019)), e2, &yn);
+    const double ys = df::to_double(ym);
+    if (POL & 1) {
+        cdd x0 = s0, x1 = s1;
+        df::interface_pair(q0, q_nx, x0, x1);
+        const dd ax0 = df::cabs2(x0);
+        double Rv = df::to_double(df::div(df::cabs2(x1), ax0));
+        double Tv = df::to_double(df::div(df::mul(q_out.x, Ps), df::mul(q0.x, ax0)));
+        Tv = ldexp(Tv * ys, e4 + eP + yn - 2 * es);
+        if (grazing) { Rv = 1.0; Tv = 0.0; }
+        out[0] = Rv;
+        out[1] = Tv;
+    }
+    if (POL & 2) {
+        const cdd g0 = df::cmul(q0, ld_c(A.in2xh, A.in2xl, A.in2yh, A.in2yl));
+        cdd x0 = p0, x1 = p1;
+        df::interface_pair(g0, g_nx, x0, x1);
+        const dd ax0 = df::cabs2(x0);
+        double Rv = df::to_double(df::div(df::cabs2(x1), ax0));
+        // Re(n_out^2 conj(q_out)) / (n_0^2 q_0)
+        const dd num = df::dot2(n2_out.x, q_out.x, n2_out.y, q_out.y, 1.0f);
+        const dd den = df::mul(df::sqr(n0), q0.x);
+        double Tv = df::to_double(df::div(df::mul(num, df::mul(Ps, Pp)), df::mul(den, ax0)));
+        Tv = ldexp(Tv * ys, e4 + eP + Pp_e + yn - 2 * ep);
+        if (grazing) { Rv = 1.0; Tv = 0.0; }
+        out[2] = Rv;
+        out[3] = Tv;
+    }
+}
+
 template <int POL>
 __device__ __forceinline__ void eval_point_dd(const DStage *__restrict__ st, const float4 *sc, const float2 *e2, int TL,
                                               int tl, int L, dd n0, dd sth, dd cth, dd Pp, int Pp_e, double out[4])
@@ -204,46 +251,212 @@ __device__ __forceinline__ void eval_point_dd(const DStage *__restrict__ st, con
             if (POL & 2) renorm_dd_pair(p0, p1, ep);
         }
     }
-    A = st[tl];
-    // grazing: cos(theta) <= 0 or beta >= n_0 (both false for a NaN n_0)
-    const bool grazing = cth.hi <= 0.0f || (!dd_less(beta, n0) && beta.hi == beta.hi);
-    const cdd q0{c0, df::make(0.0f)};
-    Ps = df::mul(Ps, q0sq);
-    const int e4 = 2 * (L + 1);
-    // 2^{-2 K Y} split as m * 2^n
-    int yn;
-    const dd ym = exp2_dd(df::mul(Y, dconst(-4.0 * kPi * 1.4426950408889634073599246810019)), e2, &yn);
-    const double ys = df::to_double(ym);
-    if (POL & 1) {
-        cdd x0 = s0, x1 = s1;
-        df::interface_pair(q0, q_nx, x0, x1);
-        const dd ax0 = df::cabs2(x0);
-        double Rv = df::to_double(df::div(df::cabs2(x1), ax0));
-        double Tv = df::to_double(df::div(df::mul(q_out.x, Ps), df::mul(q0.x, ax0)));
-        Tv = ldexp(Tv * ys, e4 + eP + yn - 2 * es);
-        if (grazing) { Rv = 1.0; Tv = 0.0; }
-        out[0] = Rv;
-        out[1] = Tv;
-    }
-    if (POL & 2) {
-        const cdd g0 = df::cmul(q0, ld_c(A.in2xh, A.in2xl, A.in2yh, A.in2yl));
-        cdd x0 = p0, x1 = p1;
-        df::interface_pair(g0, g_nx, x0, x1);
-        const dd ax0 = df::cabs2(x0);
-        double Rv = df::to_double(df::div(df::cabs2(x1), ax0));
-        // Re(n_out^2 conj(q_out)) / (n_0^2 q_0)
-        const dd num = df::dot2(n2_out.x, q_out.x, n2_out.y, q_out.y, 1.0f);
-        const dd den = df::mul(df::sqr(n0), q0.x);
-        double Tv = df::to_double(df::div(df::mul(num, df::mul(Ps, Pp)), df::mul(den, ax0)));
-        Tv = ldexp(Tv * ys, e4 + eP + Pp_e + yn - 2 * ep);
-        if (grazing) { Rv = 1.0; Tv = 0.0; }
-        out[2] = Rv;
-        out[3] = Tv;
-    }
+    finish_dd<POL>(st[tl], e2, q_out, n2_out, q_nx, g_nx, s0, s1, p0, p1, Ps, eP, Y, es, ep, L, n0, cth, beta, c0,
+                   q0sq, Pp, Pp_e, out);
 }
 
-template <int POL, bool WITH_T>
-__global__ void __launch_bounds__(kDfMaxThreads) tmm_fwd_df64_kernel(const tmm_problem p, const __grid_constant__ DfTables tabs,
+// ---------------------------------------------------------------- two angles per thread
+// eval_point_dd for two angles of one wavelength on the lanes of the paired
+// FP32 instructions (tmm_df64x2.cuh): the sweep, roots, phase factors and
+// renormalisation per lane in dd2 arithmetic; table lookups and branch
+// choices per lane by selects; interface 0 | 1 and R, T per lane in dd.
+using df2::cdd2;
+using df2::dd2;
+
+__device__ __forceinline__ void sincos_turn_dd2(const dd2 &f, const float4 *tab, dd2 *s, dd2 *c)
+{
+    const float2 jf = df2::p2(rintf(__fmul_rn(f.hi.x, 256.0f)), rintf(__fmul_rn(f.hi.y, 256.0f)));
+    const dd2 r = df2::add_f(f, df2::pneg(df2::pmul(jf, df2::b2(1.0f / 256.0f))));
+    const dd2 x = df2::mul(r, df2::bcast(dconst(2.0 * kPi)));
+    const dd2 x2 = df2::sqr(x);
+    const dd2 t = df2::mul(x2, df2::bcast(dconst(1.0 / 6.0)));
+    const float2 x4 = df2::pmul(x2.hi, x2.hi);
+    const dd2 p = df2::add_f(df2::sub(df2::make(1.0f), t), df2::pmul(x4, df2::b2(1.0f / 120.0f)));
+    const dd2 sx = df2::mul(x, p);
+    const float2 h4 = df2::psub(df2::pmul(x4, df2::b2(1.0f / 24.0f)),
+                                df2::pmul(df2::pmul(x4, x2.hi), df2::b2(1.0f / 720.0f)));
+    const dd2 cx = df2::add_f(df2::sub(df2::make(1.0f), df2::scale2(x2, df2::b2(0.5f))), h4);
+    dd sj[2], cj[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const int jj = (int)(i ? jf.y : jf.x) & 255, quad = jj >> 6, k = jj & 63;
+        const float4 e = tab[k];
+        const dd sk{e.x, e.y}, ck{e.z, e.w};
+        if (quad == 0) { sj[i] = sk; cj[i] = ck; }
+        else if (quad == 1) { sj[i] = ck; cj[i] = df::neg(sk); }
+        else if (quad == 2) { sj[i] = df::neg(sk); cj[i] = df::neg(ck); }
+        else { sj[i] = df::neg(ck); cj[i] = sk; }
+    }
+    const dd2 S = df2::pack(sj[0], sj[1]), C = df2::pack(cj[0], cj[1]);
+    *s = df2::dot2(S, cx, C, sx, 1.0f);
+    *c = df2::dot2(C, cx, S, sx, -1.0f);
+}
+
+// 2^v as m * 2^n per lane, m in [2^-0.5, 2^0.5]
+__device__ __forceinline__ dd2 exp2_dd2(const dd2 &v, const float2 *tab, int n_out[2])
+{
+    const float2 nf = df2::p2(rintf(v.hi.x), rintf(v.hi.y));
+    const dd2 r = df2::add_f(v, df2::pneg(nf));
+    const float2 i_f = df2::p2(rintf(__fmul_rn(r.hi.x, 64.0f)), rintf(__fmul_rn(r.hi.y, 64.0f)));
+    const dd2 s = df2::add_f(r, df2::pneg(df2::pmul(i_f, df2::b2(1.0f / 64.0f))));
+    const dd2 t = df2::mul(s, df2::bcast(dconst(0.69314718055994530941723212145818)));
+    const dd2 t2 = df2::sqr(t);
+    const dd2 t3_6 = df2::mul(t2, df2::mul(t, df2::bcast(dconst(1.0 / 6.0))));
+    const float2 t4 = df2::pmul(t2.hi, t2.hi);
+    const float2 tail = df2::padd(df2::pmul(t4, df2::b2(1.0f / 24.0f)),
+                                  df2::pmul(df2::pmul(t4, t.hi), df2::b2(1.0f / 120.0f)));
+    dd2 p = df2::add(df2::make(1.0f), t);
+    p = df2::add(p, df2::scale2(t2, df2::b2(0.5f)));
+    p = df2::add(p, t3_6);
+    p = df2::add_f(p, tail);
+    const float2 ea = tab[(int)i_f.x + 32], eb = tab[(int)i_f.y + 32];
+    n_out[0] = (int)nf.x;
+    n_out[1] = (int)nf.y;
+    return df2::mul(p, dd2{df2::p2(ea.x, eb.x), df2::p2(ea.y, eb.y)});
+}
+
+__device__ __forceinline__ bool dd_less_lane(const dd2 &a, const dd2 &b, int i)
+{
+    return dd_less(df2::lane(a, i), df2::lane(b, i));
+}
+
+// root_dd per lane
+__device__ __forceinline__ cdd2 root_dd2(const cdd2 &z, dd2 *absz)
+{
+    const dd2 hyp = df2::cabs2(z);
+    const bool v0 = !(hyp.hi.x <= 0.0f), v1 = !(hyp.hi.y <= 0.0f);
+    dd2 az, rh;
+    df2::sqrt_rsqrt(df2::sel(v0, v1, hyp, df2::make(1.0f)), &az, &rh);
+    const float2 sgx = df2::p2(z.x.hi.x < 0.0f ? -1.0f : 1.0f, z.x.hi.y < 0.0f ? -1.0f : 1.0f);
+    const dd2 u = df2::scale2(df2::add(az, df2::scale2(z.x, sgx)), df2::b2(0.5f));
+    dd2 t, ru;
+    df2::sqrt_rsqrt(u, &t, &ru);
+    const dd2 o = df2::scale2(df2::mul(z.y, ru), df2::b2(0.5f));
+    const float2 sgo = df2::p2(o.hi.x < 0.0f ? -1.0f : 1.0f, o.hi.y < 0.0f ? -1.0f : 1.0f);
+    const dd2 ao = df2::scale2(o, sgo);
+    auto yneg = [](float h) { return h < 0.0f || (h == 0.0f && signbit(h)); };
+    const float2 sgt = df2::p2(yneg(z.y.hi.x) ? -1.0f : 1.0f, yneg(z.y.hi.y) ? -1.0f : 1.0f);
+    const bool rp0 = z.x.hi.x >= 0.0f, rp1 = z.x.hi.y >= 0.0f;
+    cdd2 q{df2::sel(rp0, rp1, t, ao), df2::sel(rp0, rp1, o, df2::scale2(t, sgt))};
+    // decaying root unless Im q is zero to rounding (|Im q| <= 100 * 2^-46 |q|)
+    const float tol = 100.0f * 1.4210855e-14f;
+    const bool f0 = q.y.hi.x < 0.0f && q.y.hi.x * q.y.hi.x > tol * tol * az.hi.x;
+    const bool f1 = q.y.hi.y < 0.0f && q.y.hi.y * q.y.hi.y > tol * tol * az.hi.y;
+    const float2 sgf = df2::p2(f0 ? -1.0f : 1.0f, f1 ? -1.0f : 1.0f);
+    q = cdd2{df2::scale2(q.x, sgf), df2::scale2(q.y, sgf)};
+    const dd2 zero = df2::make(0.0f);
+    q = cdd2{df2::sel(v0, v1, q.x, zero), df2::sel(v0, v1, q.y, zero)};
+    *absz = df2::sel(v0, v1, az, zero);
+    return q;
+}
+
+__device__ __forceinline__ void renorm_dd_pair2(cdd2 &a, cdd2 &b, int e[2])
+{
+    int k[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const float m = fmaxf(fmaxf(fabsf(i ? a.x.hi.y : a.x.hi.x), fabsf(i ? a.y.hi.y : a.y.hi.x)),
+                              fmaxf(fabsf(i ? b.x.hi.y : b.x.hi.x), fabsf(i ? b.y.hi.y : b.y.hi.x)));
+        k[i] = exponent_of(m);
+        e[i] += k[i];
+    }
+    const float2 f = df2::p2(pow2_neg<float>(k[0]), pow2_neg<float>(k[1]));
+    a = cdd2{df2::scale2(a.x, f), df2::scale2(a.y, f)};
+    b = cdd2{df2::scale2(b.x, f), df2::scale2(b.y, f)};
+}
+
+__device__ __forceinline__ void renorm_dd2(dd2 &m, int e[2])
+{
+    const int k0 = exponent_of(m.hi.x), k1 = exponent_of(m.hi.y);
+    m = df2::scale2(m, df2::p2(pow2_neg<float>(k0), pow2_neg<float>(k1)));
+    e[0] += k0;
+    e[1] += k1;
+}
+
+__device__ __forceinline__ cdd2 bc_c(float h1, float l1, float h2, float l2)
+{
+    return cdd2{dd2{df2::b2(h1), df2::b2(l1)}, dd2{df2::b2(h2), df2::b2(l2)}};
+}
+
+template <int POL>
+__device__ __forceinline__ void eval_point_dd2(const DStage *__restrict__ st, const float4 *sc, const float2 *e2,
+                                               int TL, int tl, int L, dd n0, const dd sth[2], const dd cth[2], dd Pp,
+                                               int Pp_e, double out[2][4])
+{
+    dd beta[2], c0[2], q0sq[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        beta[i] = df::mul(n0, sth[i]);
+        c0[i] = df::mul(n0, cth[i]);
+        q0sq[i] = df::sqr(c0[i]);
+    }
+    const dd2 Q0SQ = df2::pack(q0sq[0], q0sq[1]);
+    const dd2 yi_max = df2::bcast(dconst(35.0 / (2.0 * kPi)));
+    const dd2 kE = df2::bcast(dconst(-4.0 * kPi * 1.4426950408889634073599246810019));
+
+    DStage A = st[(L + 1) * TL + tl];
+    dd2 absz;
+    cdd2 q_nx = root_dd2(cdd2{df2::add(df2::bcast(dd{A.d2h, A.d2l}), Q0SQ), df2::bcast(dd{A.n2yh, A.n2yl})}, &absz);
+    const cdd2 q_out = q_nx;
+    const cdd n2_out{df::add(dd{A.d2h, A.d2l}, df::sqr(n0)), dd{A.n2yh, A.n2yl}};
+    cdd2 g_nx = df2::cmul(q_nx, bc_c(A.in2xh, A.in2xl, A.in2yh, A.in2yl));
+    dd2 Ps = df2::make(1.0f), Y = df2::make(0.0f);
+    int eP[2] = {0, 0};
+    const cdd2 one{df2::make(1.0f), df2::make(0.0f)}, zero{df2::make(0.0f), df2::make(0.0f)};
+    cdd2 s0 = one, s1 = zero, p0 = one, p1 = zero;
+    int es[2] = {0, 0}, ep[2] = {0, 0};
+
+    for (int j = L; j >= 1; --j) {
+        A = st[j * TL + tl];
+        const cdd2 q = root_dd2(cdd2{df2::add(df2::bcast(dd{A.d2h, A.d2l}), Q0SQ), df2::bcast(dd{A.n2yh, A.n2yl})},
+                                &absz);
+        Ps = df2::mul(Ps, absz);
+        const dd2 dl = df2::bcast(dd{A.dlh, A.dll});
+        const dd2 yr = df2::mul(dl, q.x);
+        dd2 yi = df2::mul(dl, q.y);
+        yi = df2::sel(dd_less_lane(yi_max, yi, 0), dd_less_lane(yi_max, yi, 1), yi_max, yi);
+        Y = df2::add(Y, yi);
+        dd2 sn, cs;
+        sincos_turn_dd2(df2::add_f(yr, df2::pneg(df2::p2(rintf(yr.hi.x), rintf(yr.hi.y)))), sc, &sn, &cs);
+        int n2[2];
+        const dd2 m2 = exp2_dd2(df2::mul(yi, kE), e2, n2);
+        const dd2 E2 = df2::scale2(m2, df2::p2(ldexpf(1.0f, n2[0]), ldexpf(1.0f, n2[1])));
+        const cdd2 emi{cs, df2::neg(sn)};
+        const cdd2 epi{df2::mul(E2, cs), df2::mul(E2, sn)};
+        if (POL & 1) {
+            df2::interface_pair(q, q_nx, s0, s1);
+            s0 = df2::cmul(emi, s0);
+            s1 = df2::cmul(epi, s1);
+        }
+        if (POL & 2) {
+            const cdd2 g = df2::cmul(q, bc_c(A.in2xh, A.in2xl, A.in2yh, A.in2yl));
+            df2::interface_pair(g, g_nx, p0, p1);
+            p0 = df2::cmul(emi, p0);
+            p1 = df2::cmul(epi, p1);
+            g_nx = g;
+        }
+        q_nx = q;
+        if (((L - j) & 1) == 1) {
+            renorm_dd2(Ps, eP);
+            if (POL & 1) renorm_dd_pair2(s0, s1, es);
+            if (POL & 2) renorm_dd_pair2(p0, p1, ep);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+        finish_dd<POL>(st[tl], e2, df2::lane(q_out, i), n2_out, df2::lane(q_nx, i), df2::lane(g_nx, i),
+                       df2::lane(s0, i), df2::lane(s1, i), df2::lane(p0, i), df2::lane(p1, i), df2::lane(Ps, i), eP[i],
+                       df2::lane(Y, i), es[i], ep[i], L, n0, cth[i], beta[i], c0[i], q0sq[i], Pp, Pp_e, out[i]);
+}
+
+// PAIR: two angles per thread, TL x ceil(TT / 2) threads (at most 256),
+// compiled for two resident blocks per SM.  The dd chains are long and
+// dependent, so the kernel is latency-bound: the paired lanes halve its issue
+// slots but not its latency, and their doubled state costs occupancy
+// (measured on the dispersive workload: 214 ms one angle per thread, 236 ms
+// paired at one block per SM, 203 ms paired at two).
+template <int POL, bool WITH_T, bool PAIR>
+__global__ void __launch_bounds__(PAIR ? kDfPairThreads : kDfMaxThreads, PAIR ? 2 : 1) tmm_fwd_df64_kernel(const tmm_problem p, const __grid_constant__ DfTables tabs,
                                                                      int TL, int TT, int n_lt, int n_tt,
                                                                      double *__restrict__ Rout, double *__restrict__ Tout)
 {
@@ -260,7 +473,7 @@ __global__ void __launch_bounds__(kDfMaxThreads) tmm_fwd_df64_kernel(const tmm_p
     const int s = (int)(item / per_stack);
     const int rr = (int)(item - (long long)s * per_stack);
     const int lt = rr / n_tt, ttile = rr % n_tt;
-    const int tid = threadIdx.y * TL + threadIdx.x, nthr = TL * TT;
+    const int tid = threadIdx.y * TL + threadIdx.x, nthr = TL * (int)blockDim.y;
     const int L = layers_of(p, s);
     const int l0 = lt * TL;
     const double *lam = (const double *)p.lambda;
@@ -306,34 +519,48 @@ __global__ void __launch_bounds__(kDfMaxThreads) tmm_fwd_df64_kernel(const tmm_p
     }
     __syncthreads();
 
-    const int tl = threadIdx.x, l = l0 + tl, a = ttile * TT + threadIdx.y;
-    if (l < p.n_lambda && a < p.n_theta) {
-        double out[4];
+    const int tl = threadIdx.x, l = l0 + tl;
+    const int t0 = ttile * TT, t_end = min(t0 + TT, p.n_theta);
+    const int a0 = PAIR ? t0 + 2 * (int)threadIdx.y : t0 + (int)threadIdx.y;
+    if (l < p.n_lambda && a0 < t_end) {
+        const int np = PAIR && a0 + 1 < t_end ? 2 : 1;
+        double out[2][4];
         if (L >= 0) {
             // sin, cos of theta through the same turn-based routine: f = theta / (2 pi)
-            const dd f = df::mul(df::from_double(((const double *)p.theta)[a]), dconst(1.0 / (2.0 * kPi)));
-            dd sth, cth;
-            sincos_turn_dd(df::add_f(f, -rintf(f.hi)), sc, &sth, &cth);
+            dd sth[2], cth[2];
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const int a = i < np ? a0 + i : a0;
+                const dd f = df::mul(df::from_double(((const double *)p.theta)[a]), dconst(1.0 / (2.0 * kPi)));
+                sincos_turn_dd(df::add_f(f, -rintf(f.hi)), sc, &sth[i], &cth[i]);
+            }
             const float2 n0 = n0s[tl];
-            eval_point_dd<POL>(st, sc, e2, TL, tl, L, dd{n0.x, n0.y}, sth, cth,
-                               (POL & 2) ? dd{ppm[tl].x, ppm[tl].y} : df::make(1.0f), (POL & 2) ? ppe[tl] : 0, out);
+            const dd Ppd = (POL & 2) ? dd{ppm[tl].x, ppm[tl].y} : df::make(1.0f);
+            const int Ppe = (POL & 2) ? ppe[tl] : 0;
+            if constexpr (PAIR)
+                eval_point_dd2<POL>(st, sc, e2, TL, tl, L, dd{n0.x, n0.y}, sth, cth, Ppd, Ppe, out);
+            else
+                eval_point_dd<POL>(st, sc, e2, TL, tl, L, dd{n0.x, n0.y}, sth[0], cth[0], Ppd, Ppe, out[0]);
         } else {
-            out[0] = out[1] = out[2] = out[3] = __longlong_as_double(0x7ff8000000000000LL);
+#pragma unroll
+            for (int i = 0; i < 2; ++i) out[i][0] = out[i][1] = out[i][2] = out[i][3] = __longlong_as_double(0x7ff8000000000000LL);
         }
         const long long plane = (long long)p.S * p.n_theta * p.n_lambda;
-        const long long o = ((long long)s * p.n_theta + a) * p.n_lambda + l;
-        int pi = 0;
-        if (POL & 4) {  // unpolarised: the mean of s and p in one plane
-            Rout[o] = 0.5 * (out[0] + out[2]);
-            if (WITH_T) Tout[o] = 0.5 * (out[1] + out[3]);
-        } else if (POL & 1) {
-            Rout[o] = out[0];
-            if (WITH_T) Tout[o] = out[1];
-            ++pi;
-        }
-        if ((POL & 2) && !(POL & 4)) {
-            Rout[pi * plane + o] = out[2];
-            if (WITH_T) Tout[pi * plane + o] = out[3];
+        for (int i = 0; i < np; ++i) {
+            const long long o = ((long long)s * p.n_theta + a0 + i) * p.n_lambda + l;
+            int pi = 0;
+            if (POL & 4) {  // unpolarised: the mean of s and p in one plane
+                Rout[o] = 0.5 * (out[i][0] + out[i][2]);
+                if (WITH_T) Tout[o] = 0.5 * (out[i][1] + out[i][3]);
+            } else if (POL & 1) {
+                Rout[o] = out[i][0];
+                if (WITH_T) Tout[o] = out[i][1];
+                ++pi;
+            }
+            if ((POL & 2) && !(POL & 4)) {
+                Rout[pi * plane + o] = out[i][2];
+                if (WITH_T) Tout[pi * plane + o] = out[i][3];
+            }
         }
     }
 }
@@ -364,11 +591,11 @@ size_t df_stage_bytes(const tmm_problem *p, int TL)
            (size_t)TL * (2 * sizeof(float2) + sizeof(int));
 }
 
-template <int POL, bool WITH_T>
-tmm_status launch_df_typed(const tmm_problem *p, int TL, int TT, int n_lt, int n_tt, long long n_items, size_t smem,
-                           double *R, double *T, cudaStream_t st)
+template <int POL, bool WITH_T, bool PAIR>
+tmm_status launch_df_shaped(const tmm_problem *p, int TL, int TT, int n_lt, int n_tt, long long n_items, size_t smem,
+                            double *R, double *T, cudaStream_t st)
 {
-    auto k = tmm_fwd_df64_kernel<POL, WITH_T>;
+    auto k = tmm_fwd_df64_kernel<POL, WITH_T, PAIR>;
     static int set_bytes[64] = {};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -380,8 +607,18 @@ tmm_status launch_df_typed(const tmm_problem *p, int TL, int TT, int n_lt, int n
         set_bytes[dev] = (int)smem;
     }
     if (n_items > 0x7fffffffLL) return TMM_ERR_UNSUPPORTED;
-    k<<<(unsigned)n_items, dim3(TL, TT), smem, st>>>(*p, host_tables(), TL, TT, n_lt, n_tt, R, T);
+    k<<<(unsigned)n_items, dim3(TL, PAIR ? (TT + 1) / 2 : TT), smem, st>>>(*p, host_tables(), TL, TT, n_lt, n_tt, R,
+                                                                          T);
     return check_launch();
+}
+
+// tiles of two or more angles run two angles per thread
+template <int POL, bool WITH_T>
+tmm_status launch_df_typed(const tmm_problem *p, int TL, int TT, int n_lt, int n_tt, long long n_items, size_t smem,
+                           double *R, double *T, cudaStream_t st)
+{
+    if (TT >= 2) return launch_df_shaped<POL, WITH_T, true>(p, TL, TT, n_lt, n_tt, n_items, smem, R, T, st);
+    return launch_df_shaped<POL, WITH_T, false>(p, TL, TT, n_lt, n_tt, n_items, smem, R, T, st);
 }
 
 }  // namespace
@@ -394,13 +631,16 @@ tmm_status launch_forward_df64(const tmm_problem *p, const tmm_launch_cfg *cfg, 
     if (s != TMM_OK) return s;
     int TT = cfg && cfg->tile_theta > 0 ? cfg->tile_theta : std::min(p->n_theta, 32);
     int TL = cfg && cfg->tile_lambda > 0 ? cfg->tile_lambda : 0;
+    if (TT < 1 || TL < 0) return TMM_ERR_INVALID_ARG;
+    const int rows = TT >= 2 ? (TT + 1) / 2 : TT;  // thread rows: two angles per thread
+    const int max_threads = TT >= 2 ? kDfPairThreads : kDfMaxThreads;
     if (TL == 0) {
         TL = 1;
-        while (TL * TT < 256 && TL * 2 * TT <= kDfMaxThreads) TL *= 2;
+        while (TL * rows < 256 && TL * 2 * rows <= max_threads) TL *= 2;
         while (TL > 1 && TL / 2 >= p->n_lambda) TL /= 2;
         while (TL > 1 && df_stage_bytes(p, TL) > (size_t)di.max_smem_optin) TL /= 2;
     }
-    if (TL < 1 || TT < 1 || TL * TT > kDfMaxThreads) return TMM_ERR_INVALID_ARG;
+    if (TL < 1 || TL * rows > max_threads) return TMM_ERR_INVALID_ARG;
     const size_t smem = df_stage_bytes(p, TL);
     if (smem > (size_t)di.max_smem_optin) return TMM_ERR_UNSUPPORTED;
     const int n_lt = (p->n_lambda + TL - 1) / TL, n_tt = (p->n_theta + TT - 1) / TT;
