@@ -116,8 +116,11 @@ typedef struct {
 
 /*
  * Launch shape (all fields 0 = library default).  One block evaluates one
- * work item: one stack x tile_lambda wavelengths x tile_theta angles, one
- * thread per (lambda, theta) pair covering the requested polarisations.
+ * work item: one stack x tile_lambda wavelengths x tile_theta angles, each
+ * thread covering the requested polarisations.  FP32 and double-float tiles
+ * of two or more angles run two adjacent angles per thread (the two lanes of
+ * the paired FP32 instructions): tile_lambda x ceil(tile_theta / 2) threads,
+ * at most 256; otherwise one (lambda, theta) per thread, at most 512.
  *   persistent   0: one block per work item.  1: a persistent grid pulls work
  *                items from a device counter, longest stacks first (ragged
  *                batches); needs a workspace (tmm_workspace_size).

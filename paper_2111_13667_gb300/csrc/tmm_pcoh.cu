@@ -111,8 +111,8 @@ template <typename R> static Nodes<R> make_nodes(int K)
     return nd;
 }
 
-// One coherent layer step (interface j | j+1, then the phase of layer j) on
-// the amplitude pair; the forward kernel's arithmetic.
+// The phase factors of one layer, e^{-i delta} and e^{+i delta} divided by
+// e^{Im delta}, with the clamped Im(delta) / (2 pi): the forward kernel's.
 template <typename R> struct Step {
     Cx<R> emi, epi;
     R yi;
