@@ -13,8 +13,8 @@
 //   F_j = f_j 2^{LY_j - LY_0} (D_0 / D_j) / (k_0 |x_0[0]|^2),
 // F_{L+1} = T, F_1 = 1 - R, and the absorbed fraction of layer j is
 //   A_j = F_j - F_{j+1}   (flux is continuous across interfaces).
-// Each thread keeps (f_j / mantissa(D_j), exponent(D_j), LY_j) of its layers
-// in local memory until the end of the sweep.
+// Each thread keeps its layers' (f_j / mantissa(D_j) with 2^{frac(LY_j)},
+// floor(LY_j) - exponent(D_j)) in local memory until the end of the sweep.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -29,10 +29,19 @@ namespace {
 constexpr int kAbsThreads = 256;
 constexpr int kAbsMaxLayers = 127;
 
+// f_j / mantissa(D_j) 2^{frac(LY_j)} for s and p, and floor(LY_j) - exponent(D_j)
+// for s (low 16 bits) and p (high 16 bits).  |LY_j| <= 101 per layer (the
+// Im delta clamp) and the exponent of D moves by at most about 60 per layer,
+// so with L_max <= 127 both fit 16 bits.  (Records of 3 reals and 2 ints
+// made the kernel memory-bound on them.)
 template <typename R> struct AbsRec {
-    R hs, hp, ly;  // f_j / mantissa(D_j) for s and p; LY_j
-    int es, ep;    // exponent(D_j) for s and p
+    R hs, hp;
+    int k;
 };
+
+__device__ __forceinline__ int pack_k(int ks, int kp) { return (ks & 0xffff) | (kp << 16); }
+__device__ __forceinline__ int k_s(int k) { return (int)(short)(k & 0xffff); }
+__device__ __forceinline__ int k_p(int k) { return k >> 16; }
 
 template <typename R> __device__ __forceinline__ R flux(Cx<R> k, Cx<R> x0, Cx<R> x1)
 {
@@ -98,7 +107,7 @@ __global__ void __launch_bounds__(kAbsThreads) tmm_abs_kernel(const tmm_problem 
         Cx<R> q_nx = forward_root(Cx<R>{A.d2x + q0sq, A.n2y}, &absz);
         Cx<R> g_nx = cmul(q_nx, Cx<R>{A.in2x, A.in2y});
         // exit medium: x = (1, 0), D = 1, LY = 0
-        rec[L + 1] = AbsRec<R>{q_nx.x, g_nx.x, R(0), 0, 0};
+        rec[L + 1] = AbsRec<R>{q_nx.x, g_nx.x, 0};
         Cx<R> s0 = {R(1), R(0)}, s1 = {R(0), R(0)}, p0 = s0, p1 = s1;
         R Dsm = R(1), Dpm = R(1), LY = R(0);
         int Dse = 0, Dpe = 0, cnt = 0;
@@ -139,11 +148,12 @@ __global__ void __launch_bounds__(kAbsThreads) tmm_abs_kernel(const tmm_problem 
                     Dpe -= 2 * k;
                 }
             }
+            const R lyf = floor_w(LY);
+            const R fr = exp2_w(LY - lyf);
             AbsRec<R> rj;
-            rj.hs = (POL & 1) ? flux(q, s0, s1) / Dsm : R(0);
-            rj.hp = (POL & 2) ? flux(g, p0, p1) / Dpm : R(0);
-            rj.ly = LY;
-            rj.es = Dse, rj.ep = Dpe;
+            rj.hs = (POL & 1) ? flux(q, s0, s1) / Dsm * fr : R(0);
+            rj.hp = (POL & 2) ? flux(g, p0, p1) / Dpm * fr : R(0);
+            rj.k = pack_k((int)lyf - Dse, (int)lyf - Dpe);
             rec[j] = rj;
             q_nx = q;
             g_nx = g;
@@ -170,18 +180,19 @@ __global__ void __launch_bounds__(kAbsThreads) tmm_abs_kernel(const tmm_problem 
             pre[1] = Dpm / (ax0 * g0.x);
             e0[1] = Dpe;
         }
-        // F_j from the records, then A_j = F_j - F_{j+1} (j = L .. 1)
+        // F_j from the records, then A_j = F_j - F_{j+1} (j = L .. 1):
+        // F_j = h_j pre 2^{-LY_0} 2^{floor(LY_j) - e_j + e0}
+        const R LYf = floor_w(LY);
+        const R sc = exp2_w(LYf - LY);  // 2^{-frac(LY_0)}
+        const int kb = -(int)LYf;
         R Fn[2];
 #pragma unroll
         for (int k = 0; k < 2; ++k) Fn[k] = R(0);
         for (int j = L + 1; j >= 1; --j) {
             const AbsRec<R> rj = rec[j];
-            const R w = rj.ly - LY;  // <= 0
-            const R wn = floor_w(w);
-            const R sc = exp2_w(w - wn);
             R F[2] = {R(0), R(0)};
-            if (POL & 1) F[0] = ldexp_w(rj.hs * pre[0] * sc, e0[0] - rj.es + (int)wn);
-            if (POL & 2) F[1] = ldexp_w(rj.hp * pre[1] * sc, e0[1] - rj.ep + (int)wn);
+            if (POL & 1) F[0] = ldexp_w(rj.hs * pre[0] * sc, e0[0] + k_s(rj.k) + kb);
+            if (POL & 2) F[1] = ldexp_w(rj.hp * pre[1] * sc, e0[1] + k_p(rj.k) + kb);
             if (j == L + 1) {
                 Tv[0] = F[0], Tv[1] = F[1];
             } else {
