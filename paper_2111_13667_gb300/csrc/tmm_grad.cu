@@ -36,10 +36,16 @@ constexpr int kGradThreads = 256;
 constexpr int kGradMaxLayers = 127;  // L_max + 2 <= 129 media
 
 // Stored right-sweep state of one layer (both polarisations).
+// The pairs' exponents share one int, s in the low and p in the high 16
+// bits: they move by the rescalings only (at most about 63 per two layers),
+// so L_max <= 127 keeps them within 16 bits; 36 bytes per layer in FP32.
 template <typename R> struct XState {
     Cx<R> s0, s1, p0, p1;
-    int es, ep;
+    int e;
+    __device__ int es() const { return (int)(short)(e & 0xffff); }
+    __device__ int ep() const { return e >> 16; }
 };
+__device__ __forceinline__ int pack_e(int es, int ep) { return (es & 0xffff) | (ep << 16); }
 
 template <typename R> __device__ __forceinline__ R warp_sum(R v)
 {
@@ -160,7 +166,7 @@ __global__ void __launch_bounds__(kGradThreads, GradMinBlocks<R>::value) tmm_gra
         Medium<R> nx = medium_at(sa[(L + 1) * TL + tl], sn[(L + 1) * TL + tl], q0sq, false);
         Cx<R> s0 = {R(1), R(0)}, s1 = {R(0), R(0)}, p0 = s0, p1 = s1;
         int es = 0, ep = 0;
-        X[L + 1] = XState<R>{s0, s1, p0, p1, 0, 0};
+        X[L + 1] = XState<R>{s0, s1, p0, p1, 0};
         // The phase matrix is applied divided by its real factor e^{Im delta}
         // (one exponential per layer).  Stored states and, below, the row
         // cotangents then carry inverse scales, so every gradient term --
@@ -187,7 +193,7 @@ __global__ void __launch_bounds__(kGradThreads, GradMinBlocks<R>::value) tmm_gra
                 p1 = cmul(epi, p1);
                 if (rn) renorm_pair(p0, p1, ep);
             }
-            X[j] = XState<R>{s0, s1, p0, p1, es, ep};
+            X[j] = XState<R>{s0, s1, p0, p1, pack_e(es, ep)};
             nx = m;
         }
         // interface 0 -> 1 and the cotangent of R at x_0
@@ -269,9 +275,9 @@ __global__ void __launch_bounds__(kGradThreads, GradMinBlocks<R>::value) tmm_gra
             // s polarisation
             if (do_s) {
                 const Cx<R> v0 = cmul(ws0, emi), v1 = cmul(ws1, epi);
-                const R sc_b = pow2_w<R>(ews + Xn.es);
+                const R sc_b = pow2_w<R>(ews + Xn.es());
                 if (j >= 1) {
-                    const R sc_a = pow2_w<R>(ews + Xc.es);
+                    const R sc_a = pow2_w<R>(ews + Xc.es());
                     const Cx<R> D = mul_i(cmul(ws1, Xc.s1) - cmul(ws0, Xc.s0));
                     dd += R(2) * cmul(D, ddel_d).x * sc_a;
                     if (WITH_DN) {
@@ -288,9 +294,9 @@ __global__ void __launch_bounds__(kGradThreads, GradMinBlocks<R>::value) tmm_gra
             }
             if (do_p) {
                 const Cx<R> v0 = cmul(wp0, emi), v1 = cmul(wp1, epi);
-                const R sc_b = pow2_w<R>(ewp + Xn.ep);
+                const R sc_b = pow2_w<R>(ewp + Xn.ep());
                 if (j >= 1) {
-                    const R sc_a = pow2_w<R>(ewp + Xc.ep);
+                    const R sc_a = pow2_w<R>(ewp + Xc.ep());
                     const Cx<R> D = mul_i(cmul(wp1, Xc.p1) - cmul(wp0, Xc.p0));
                     dd += R(2) * cmul(D, ddel_d).x * sc_a;
                     if (WITH_DN) {
