@@ -1,14 +1,15 @@
 """R, T for problems whose inputs and outputs live in host memory.
 
 ``HostPipeline`` copies the (small) inputs to the device, then evaluates the
-stacks in chunks with ``tmm_coh_batched`` on a compute stream while copy
-streams bring each finished chunk's R, T back into the caller's pinned host
-arrays; chunk k's copies overlap the kernels of the chunks after it.  The
-copies of one chunk are spread over two streams, so two copy engines run at
-once (one device-to-host copy stream alone sustains about 160 GB/s on
-GB300, below the rate at which the forward kernel produces R and T).  Only
-argument marshalling and copies happen here; every evaluation is the library
-kernel.
+stacks in chunks with ``tmm_coh_batched`` on a compute stream while a copy
+stream brings each finished chunk's R, T back into the caller's pinned host
+arrays; chunk k's copies overlap the kernels of the chunks after it.  Chunks
+are small (32 by default) and three ring slots let the kernels run two chunks
+ahead of the copies, so only the last chunk's copy is exposed.  The copies
+can be spread over more streams (``N_COPY_STREAMS``): on GB300 two streams
+measured the same as one in quiet conditions and about three times slower in
+some full benchmark runs, so one is the default.  Only argument marshalling
+and copies happen here; every evaluation is the library kernel.
 """
 from __future__ import annotations
 
@@ -24,7 +25,7 @@ _INPUTS = ("theta", "lam", "d", "n_direct", "table", "mat_idx", "L_per_stack")
 
 class HostPipeline:
     N_SLOTS = 3
-    N_COPY_STREAMS = 2
+    N_COPY_STREAMS = 1
 
     def __init__(self, prob: abi.DeviceProblem, n_chunks: int = 32, with_T: bool = True):
         """``prob`` holds device buffers sized for the whole problem (they
