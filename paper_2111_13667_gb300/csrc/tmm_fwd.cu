@@ -2,8 +2,10 @@
 // (stack, lambda, theta, polarisation) of a batch (arXiv 2111.13667, Sec. 2).
 //
 // Design (sm_103a):
-//   * one thread per (stack, lambda, theta); it carries both polarisations,
-//     which share Snell's law and the layer phase;
+//   * one thread per (stack, lambda, theta) -- in FP32 per (stack, lambda,
+//     pair of angles), the two angles on the lanes of the paired FP32
+//     instructions; it carries both polarisations, which share Snell's law
+//     and the layer phase;
 //   * the layer loop runs right to left in registers on the 2-vector
 //     x_j = M_j x_{j+1}, x_{L+1} = (1, 0) -- the first column of the product of
 //     Eq. 4, which is all Eqs. 5-6 need;
@@ -11,8 +13,9 @@
 //     2a (a = q_j for s, q_j / n_j^2 for p, q = n cos(theta)), so no layer needs
 //     a complex division; the dropped scale factors only enter |t|^2 and are
 //     carried as a product of |q_j|^2 (and |1/n_j^2|^2 for p);
-//   * all running products are rescaled by exact powers of two every layer,
-//     which keeps the FP32 path finite through opaque layers;
+//   * all running products are rescaled by exact powers of two every few
+//     layers (two in FP32, eight in FP64), which keeps the FP32 path finite
+//     through opaque layers;
 //   * per-(medium, wavelength) data (n^2, 1/n^2, d/lambda) are staged once per
 //     block in shared memory and reused by every angle of the block.
 #include <cuda_runtime.h>

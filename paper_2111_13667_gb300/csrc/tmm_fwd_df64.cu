@@ -3,9 +3,9 @@
 // arithmetic on the FP32 pipes (see tmm_df64.cuh).
 //
 // Same method and layout as tmm_fwd.cu (one thread per (stack, lambda,
-// theta), both polarisations, right-to-left 2-vector sweep of Eq. 3 with
-// unnormalised interfaces, phase applied divided by e^{Im delta}, power-of-two
-// rescaling every two layers).  Transcendentals:
+// theta), or per pair of angles on paired FP32 lanes; both polarisations,
+// right-to-left 2-vector sweep of Eq. 3 with unnormalised interfaces, phase
+// applied divided by e^{Im delta}, power-of-two rescaling every two layers).  Transcendentals:
 //   sin, cos of 2 pi f: f = j/256 + r, |r| <= 1/512; Taylor series of
 //     sin, cos (2 pi r) to x^5 / x^6, recombined with a table of
 //     sin, cos(2 pi k / 256) by the angle-addition formulas;

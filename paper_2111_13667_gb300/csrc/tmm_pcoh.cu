@@ -5,8 +5,8 @@
 // (Eqs. 1-6) over D, by the Gauss-Hermite rule
 //   E[f] = sum_k (w_k / sqrt(pi)) f(sqrt(2) sigma x_k)
 // (a reading: the paper treats coherent stacks only).  Only layer j's phase
-// depends on D, so one thread per (stack, lambda, theta) evaluates, for both
-// polarisations:
+// depends on D, so one thread per (stack, lambda, theta) -- in FP32 per pair
+// of angles on paired lanes -- evaluates, for both polarisations:
 //   y  = F_j x_{j+1}: the forward kernel's right-to-left sweep from the exit
 //        medium through interface j | j+1 (scaled, unnormalised interfaces);
 //   ML = F_0 P_1 F_1 ... P_{j-1} F_{j-1}: the block left of layer j, both
