@@ -161,6 +161,7 @@ static tmm_status gemm_entry(const void *A, const void *B, const float *bias, in
 extern "C" TMM_API tmm_status tmm_gemm_bf16(const void *A, const void *B, const float *bias, int32_t M, int32_t N,
                                             int32_t K, int32_t epilogue, void *out, void *aux, void *stream)
 {
+    TraceRange trace("tmm_gemm_bf16");
     return gemm_entry(A, B, bias, M, N, K, epilogue, out, aux, nullptr, 0, stream);
 }
 
@@ -168,6 +169,7 @@ extern "C" TMM_API tmm_status tmm_gemm_bf16_t(const void *A, const void *B, cons
                                               int32_t K, int32_t epilogue, void *out, void *aux, void *outT,
                                               int32_t ldoT, void *stream)
 {
+    TraceRange trace("tmm_gemm_bf16_t");
     if (!outT || (epilogue != gemm::EPI_GELU && epilogue != gemm::EPI_DGELU) || ldoT < M) return TMM_ERR_INVALID_ARG;
     return gemm_entry(A, B, bias, M, N, K, epilogue, out, aux, outT, ldoT, stream);
 }

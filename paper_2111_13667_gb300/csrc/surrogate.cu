@@ -500,6 +500,7 @@ TMM_API int64_t tmm_surrogate_parameters(const tmm_surrogate *s)
 
 TMM_API tmm_status tmm_surrogate_generate(tmm_surrogate *s, const float *d, int32_t B, float *R, void *stream)
 {
+    TraceRange trace("tmm_surrogate_generate");
     if (!s || !d || !R || B < 0) return TMM_ERR_INVALID_ARG;
     if (B == 0) return TMM_OK;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -513,6 +514,7 @@ TMM_API tmm_status tmm_surrogate_generate(tmm_surrogate *s, const float *d, int3
 TMM_API tmm_status tmm_surrogate_train_step(tmm_surrogate *s, const float *d, const float *R_target, int32_t B,
                                             float lr, float *loss, void *stream)
 {
+    TraceRange trace("tmm_surrogate_train_step");
     if (!s || !d || !R_target || B < 128 || B % 8 != 0 || !(lr > 0)) return TMM_ERR_INVALID_ARG;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     tmm_status r = ensure_batch(s, B);
@@ -581,6 +583,7 @@ TMM_API tmm_status tmm_surrogate_train_step(tmm_surrogate *s, const float *d, co
 TMM_API tmm_status tmm_surrogate_infer(tmm_surrogate *s, const float *d, int32_t B, float *R, float judge_fraction,
                                        float tol, int32_t *n_fallback, float *max_err, void *stream)
 {
+    TraceRange trace("tmm_surrogate_infer");
     if (!s || !d || !R || B < 0 || !(judge_fraction >= 0.0f) || judge_fraction > 1.0f || !(tol >= 0.0f))
         return TMM_ERR_INVALID_ARG;
     if (B == 0) return TMM_OK;

@@ -87,6 +87,7 @@ extern "C" {
 tmm_status tmm_coh_batched_ex(const tmm_problem *p, const tmm_launch_cfg *cfg, void *workspace,
                               size_t workspace_bytes, void *R, void *T, void *stream)
 {
+    TraceRange trace("tmm_coh_batched_ex");
     tmm_status s = validate_problem(p);
     if (s != TMM_OK) return s;
     if ((long long)p->S * p->n_lambda * p->n_theta == 0) return TMM_OK;
@@ -129,6 +130,7 @@ tmm_status tmm_workspace_status(const void *workspace, void *stream)
 tmm_status tmm_coh_grad(const tmm_problem *p, const void *R_target, void *merit, void *dm_dd, void *dm_dn,
                         void *workspace, size_t workspace_bytes, void *stream)
 {
+    TraceRange trace("tmm_coh_grad");
     tmm_status s = validate_problem(p);
     if (s != TMM_OK) return s;
     if (p->S == 0) return TMM_OK;
@@ -157,6 +159,7 @@ tmm_status tmm_reward_workspace_size(const tmm_problem *p, const tmm_launch_cfg 
 tmm_status tmm_coh_reward(const tmm_problem *p, const tmm_launch_cfg *cfg, const void *R_target, void *reward,
                           void *workspace, size_t workspace_bytes, void *stream)
 {
+    TraceRange trace("tmm_coh_reward");
     tmm_status s = validate_problem(p);
     if (s != TMM_OK) return s;
     if (p->prec == TMM_F64X) return TMM_ERR_UNSUPPORTED;

@@ -298,6 +298,7 @@ using namespace tmm;
 
 extern "C" TMM_API tmm_status tmm_absorption_batched(const tmm_problem *p, void *A, void *R, void *T, void *stream)
 {
+    TraceRange trace("tmm_absorption_batched");
     tmm_status s = validate_problem(p);
     if (s != TMM_OK) return s;
     if (p->prec == TMM_F64X) return TMM_ERR_UNSUPPORTED;

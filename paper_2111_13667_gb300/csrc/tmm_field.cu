@@ -605,6 +605,7 @@ using namespace tmm;
 
 extern "C" TMM_API tmm_status tmm_field_profile(const tmm_problem *p, int32_t n_z, void *E, void *stream)
 {
+    TraceRange trace("tmm_field_profile");
     tmm_status s = validate_problem(p);
     if (s != TMM_OK) return s;
     if (p->prec == TMM_F64X) return TMM_ERR_UNSUPPORTED;

@@ -6,9 +6,21 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/tmm.h"
 
 namespace tmm {
+
+// A named NVTX range around one ABI call, so that Nsight Systems timelines and
+// ncu's range filters show the library's calls by name; with no tool
+// attached the push and pop are no-ops.
+struct TraceRange {
+    explicit TraceRange(const char *name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange &) = delete;
+    TraceRange &operator=(const TraceRange &) = delete;
+};
 
 struct Tile {
     int TL = 0, TT = 0;        // wavelengths x angles per work item

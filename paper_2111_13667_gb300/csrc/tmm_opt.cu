@@ -93,6 +93,7 @@ extern "C" TMM_API tmm_status tmm_optimize_adam(const tmm_problem *p, const void
                                                 int32_t steps, void *merit_hist, void *workspace,
                                                 size_t workspace_bytes, void *stream)
 {
+    TraceRange trace("tmm_optimize_adam");
     tmm_status s = validate_problem(p);
     if (s != TMM_OK) return s;
     if (p->prec == TMM_F64X || (p->pol_mask & TMM_POL_AVG)) return TMM_ERR_UNSUPPORTED;

@@ -680,6 +680,7 @@ using namespace tmm;
 extern "C" TMM_API tmm_status tmm_pcoh_batched(const tmm_problem *p, const int32_t *layer, const void *sigma,
                                                int32_t n_nodes, void *R, void *T, void *stream)
 {
+    TraceRange trace("tmm_pcoh_batched");
     tmm_status s = validate_problem(p);
     if (s != TMM_OK) return s;
     if (p->prec == TMM_F64X) return TMM_ERR_UNSUPPORTED;
