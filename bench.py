@@ -581,13 +581,21 @@ def bench_paper_shapes(args, torch, abi, W, flush):
         ent = {"evals": w.evals, "paper": paper}
         if pols:
             ent["output"] = "one plane of (R_s + R_p) / 2 and (T_s + T_p) / 2 (pol_mask 7)"
+        R64 = T64 = None
         for prec in ("f64", "f64x", "f32"):
             prob = abi.to_device(w, prec, pols=pols)
             R, T = prob.empty_out(), prob.empty_out()
             t = time_steps(lambda: abi.tmm_coh_batched(prob, R, T), 5, 3, torch, flush)
             ms = sum(t) / len(t)
             ent[prec] = {"ms": ms, "evals_per_s": w.evals / (ms * 1e-3)}
+            if R64 is None:
+                R64, T64 = R.double(), T.double()
+            else:
+                # max |R - R_f64|, |T - T_f64| (the FP64 path is held to 1e-10 of the oracle)
+                ent[prec]["max_abs_diff_vs_f64"] = max(float((R.double() - R64).abs().max()),
+                                                       float((T.double() - T64).abs().max()))
             del R, T, prob
+        del R64, T64
         if name == "speedup_x1" and not args.skip_cpu:
             import oracle
             n = oracle.assemble_index(w.n_direct, w.table, w.mat_idx, w.n_lambda)
