@@ -33,6 +33,14 @@
  *     range, a layer count outside [0, L_max], a complex injection index)
  *     poison the outputs of the affected stack with NaN instead of reading
  *     out of bounds.
+ *   - Host threads: the library's host-side caches (device facts, each
+ *     kernel's shared-memory limit) are guarded by locks, and a kernel's
+ *     limit only ever grows, so calls may come from several host threads at
+ *     once, each with its own stream and buffers.  Two exceptions share state
+ *     across calls: tmm_coh_batched_noalloc (one scratch array, see there) and
+ *     the bf16 GEMMs of the surrogate and tmm_gemm_bf16(_t), which report an
+ *     expired pipeline wait through one flag per device, so concurrent calls
+ *     of those can attribute a timeout to the wrong call.
  */
 #ifndef TMM_GB300_TMM_H
 #define TMM_GB300_TMM_H

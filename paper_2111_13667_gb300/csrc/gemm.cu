@@ -59,18 +59,10 @@ static tmm_status launch_bn(const CUtensorMap &ta, const CUtensorMap &tb, int M,
 {
     auto k = gemm_bf16_kernel<BN, STAGES>;
     constexpr size_t smem = GemmSmem<BN, STAGES>::total;
-    static int set_dev[64] = {};
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return cuda_fail(e);
-    if (dev < 0 || dev >= 64) return TMM_ERR_UNSUPPORTED;
-    if (!set_dev[dev]) {
-        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return cuda_fail(e);
-        set_dev[dev] = 1;
-    }
+    tmm_status s = ensure_dynamic_smem(reinterpret_cast<const void *>(k), smem);
+    if (s != TMM_OK) return s;
     DeviceInfo di;
-    tmm_status s = device_info(&di);
+    s = device_info(&di);
     if (s != TMM_OK) return s;
     const long long tiles = (long long)((M + BM - 1) / BM) * ((N + BN - 1) / BN);
     const int grid = (int)std::min<long long>(tiles, di.sms);

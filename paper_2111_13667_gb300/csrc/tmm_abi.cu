@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "tmm_internal.h"
 
@@ -48,6 +49,34 @@ tmm_status device_info(DeviceInfo *out)
         have[dev] = true;
     }
     *out = cache[dev];
+    return TMM_OK;
+}
+
+tmm_status ensure_dynamic_smem(const void *fn, size_t bytes)
+{
+    if (bytes <= 48 * 1024) return TMM_OK;
+    if (bytes > (size_t)0x7fffffff) return TMM_ERR_UNSUPPORTED;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e);
+    struct Granted {
+        const void *fn;
+        int dev;
+        size_t bytes;
+    };
+    static std::mutex mu;
+    static std::vector<Granted> granted;
+    std::lock_guard<std::mutex> lk(mu);
+    Granted *g = nullptr;
+    for (auto &x : granted)
+        if (x.fn == fn && x.dev == dev) g = &x;
+    if (g && g->bytes >= bytes) return TMM_OK;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (g)
+        g->bytes = bytes;
+    else
+        granted.push_back(Granted{fn, dev, bytes});
     return TMM_OK;
 }
 

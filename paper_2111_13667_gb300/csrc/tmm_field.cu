@@ -554,17 +554,9 @@ template <typename Out, void (*k)(const tmm_problem, int, int, int, int, int, Ou
 tmm_status launch_field_with(const tmm_problem *p, int n_z, int TL, int TT, int rows, int n_lt, int n_tt,
                              long long items, size_t smem, Out *E, cudaStream_t st)
 {
-    if (smem > 48 * 1024) {
-        static int set_bytes[64] = {};
-        int dev = 0;
-        cudaError_t e = cudaGetDevice(&dev);
-        if (e != cudaSuccess) return cuda_fail(e);
-        if (dev < 0 || dev >= 64) return TMM_ERR_UNSUPPORTED;
-        if (set_bytes[dev] < (int)smem) {
-            e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) return cuda_fail(e);
-            set_bytes[dev] = (int)smem;
-        }
+    {
+        const tmm_status ss = ensure_dynamic_smem(reinterpret_cast<const void *>(k), smem);
+        if (ss != TMM_OK) return ss;
     }
     k<<<(unsigned)items, dim3(TL, rows), smem, st>>>(*p, n_z, TL, TT, n_lt, n_tt, E);
     return check_launch();

@@ -625,7 +625,7 @@ struct KernelFacts {
     const void *fn;
     int dev, threads;
     size_t smem;
-    int smem_set, per_sm;
+    int per_sm;
 };
 static std::mutex g_facts_mu;
 static std::vector<KernelFacts> g_facts;
@@ -634,7 +634,7 @@ static KernelFacts *facts_for(const void *fn, int dev, int threads, size_t smem)
 {
     for (auto &f : g_facts)
         if (f.fn == fn && f.dev == dev && f.threads == threads && f.smem == smem) return &f;
-    g_facts.push_back(KernelFacts{fn, dev, threads, smem, 0, 0});
+    g_facts.push_back(KernelFacts{fn, dev, threads, smem, 0});
     return &g_facts.back();
 }
 
@@ -646,11 +646,10 @@ static tmm_status prepare_kernel(Kernel k, int threads, size_t smem, bool need_o
     if (e != cudaSuccess) return cuda_fail(e);
     std::lock_guard<std::mutex> lk(g_facts_mu);
     KernelFacts *f = facts_for(reinterpret_cast<const void *>(k), dev, threads, smem);
-    if (smem > 48 * 1024 && !f->smem_set) {
-        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return cuda_fail(e);
-        f->smem_set = 1;
-    }
+    // the limit is granted per kernel (the largest size so far), not per entry:
+    // setting it per size could lower it below an entry that was already set
+    const tmm_status ss = ensure_dynamic_smem(reinterpret_cast<const void *>(k), smem);
+    if (ss != TMM_OK) return ss;
     if (need_occupancy && f->per_sm == 0) {
         int n = 0;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, threads, smem);

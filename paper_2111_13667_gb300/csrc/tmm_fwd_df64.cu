@@ -596,16 +596,8 @@ tmm_status launch_df_shaped(const tmm_problem *p, int TL, int TT, int n_lt, int 
                             double *R, double *T, cudaStream_t st)
 {
     auto k = tmm_fwd_df64_kernel<POL, WITH_T, PAIR>;
-    static int set_bytes[64] = {};
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return cuda_fail(e);
-    if (dev < 0 || dev >= 64) return TMM_ERR_UNSUPPORTED;
-    if (smem > 48 * 1024 && set_bytes[dev] < (int)smem) {
-        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return cuda_fail(e);
-        set_bytes[dev] = (int)smem;
-    }
+    const tmm_status ss = ensure_dynamic_smem(reinterpret_cast<const void *>(k), smem);
+    if (ss != TMM_OK) return ss;
     if (n_items > 0x7fffffffLL) return TMM_ERR_UNSUPPORTED;
     k<<<(unsigned)n_items, dim3(TL, PAIR ? (TT + 1) / 2 : TT), smem, st>>>(*p, host_tables(), TL, TT, n_lt, n_tt, R,
                                                                           T);

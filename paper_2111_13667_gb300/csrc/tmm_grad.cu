@@ -411,19 +411,9 @@ static tmm_status launch_grad_typed(const tmm_problem *p, const GradPlan &g, con
                                     void *dm_dd, void *dm_dn, void *ws, cudaStream_t st)
 {
     auto k = tmm_grad_kernel<R, KMAX, WITH_DN>;
-    if (g.smem > 48 * 1024) {
-        // set once per (instantiation, device): the launch sequence stays free of
-        // attribute calls when it is recorded into a CUDA graph
-        static int set_bytes[64] = {};
-        int dev = 0;
-        cudaError_t e = cudaGetDevice(&dev);
-        if (e != cudaSuccess) return cuda_fail(e);
-        if (dev < 0 || dev >= 64) return TMM_ERR_UNSUPPORTED;
-        if (set_bytes[dev] < (int)g.smem) {
-            e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
-            if (e != cudaSuccess) return cuda_fail(e);
-            set_bytes[dev] = (int)g.smem;
-        }
+    {
+        const tmm_status ss = ensure_dynamic_smem(reinterpret_cast<const void *>(k), g.smem);
+        if (ss != TMM_OK) return ss;
     }
     const long long blocks = (long long)p->S * g.G;
     if (blocks > 0x7fffffffLL) return TMM_ERR_UNSUPPORTED;

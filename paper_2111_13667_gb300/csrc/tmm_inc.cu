@@ -443,19 +443,9 @@ tmm_status launch_inc_shaped(const tmm_problem *p, const uint8_t *inc, int TL, i
                              long long items, size_t smem, R *Ro, R *To, cudaStream_t st)
 {
     auto k = tmm_inc_kernel<R, POL, WITH_T, PAIR>;
-    if (smem > 48 * 1024) {
-        // once per (instantiation, device) and size: repeated launches and graph
-        // capture stay free of attribute calls
-        static int set_bytes[64] = {};
-        int dev = 0;
-        cudaError_t e = cudaGetDevice(&dev);
-        if (e != cudaSuccess) return cuda_fail(e);
-        if (dev < 0 || dev >= 64) return TMM_ERR_UNSUPPORTED;
-        if (set_bytes[dev] < (int)smem) {
-            e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) return cuda_fail(e);
-            set_bytes[dev] = (int)smem;
-        }
+    {
+        const tmm_status ss = ensure_dynamic_smem(reinterpret_cast<const void *>(k), smem);
+        if (ss != TMM_OK) return ss;
     }
     k<<<(unsigned)items, dim3(TL, PAIR ? (TT + 1) / 2 : TT), smem, st>>>(*p, inc, TL, TT, n_lt, n_tt, Ro, To);
     return check_launch();

@@ -41,6 +41,13 @@ tmm_status device_info(DeviceInfo *out);
 // device query.
 constexpr size_t kSmemBlockCeiling = 227 * 1024;
 
+// Allow the kernel fn to be launched with `bytes` of dynamic shared memory on
+// the current device.  Above the 48 KiB default the attribute is raised to the
+// largest size asked for so far and never lowered, under one process-wide
+// lock: a launch of another size, in this host thread or another, cannot
+// shrink the limit below what an earlier check granted.
+tmm_status ensure_dynamic_smem(const void *fn, size_t bytes);
+
 int npol(uint32_t pol_mask);
 size_t real_size(int prec);
 

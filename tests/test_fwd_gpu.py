@@ -123,6 +123,20 @@ def rounded_to_f32(w):
     return replace(w, d=r(w.d), theta=r(w.theta), lam=r(w.lam), n_direct=nd)
 
 
+def assert_f32_conditioned(w, R, T, Ro, To, what):
+    """The FP32 tolerance read per angle: 1e-4, or six times the movement of
+    the exact R, T when only the inputs are rounded to FP32, where that is
+    larger.  Returns the largest error per angle."""
+    Rr, Tr = oracle_RT(rounded_to_f32(w))
+    floor = np.maximum(np.abs(Rr - Ro), np.abs(Tr - To)).max(axis=(0, 1, 3))
+    err = np.maximum(np.abs(R - Ro), np.abs(T - To)).max(axis=(0, 1, 3))
+    bound = np.maximum(TOL["f32"], 6.0 * floor)
+    assert np.all(np.isfinite(R)) and np.all(np.isfinite(T)), what
+    assert np.all(err <= bound), (what, [(round(float(np.rad2deg(t)), 1), float(e), float(b))
+                                         for t, e, b in zip(w.theta, err, bound)])
+    return err
+
+
 @pytest.mark.parametrize("prec", ["f64", "f32", "f64x"])
 def test_timing_shape_to_grazing_and_input_conditioning(prec):
     # Sec. 4 timing run: 19 layers of real index up to 5 between air, theta
@@ -140,16 +154,29 @@ def test_timing_shape_to_grazing_and_input_conditioning(prec):
         assert_close(R, Ro, TOL[prec], "R")
         assert_close(T, To, TOL[prec], "T")
         return
-    Rr, Tr = oracle_RT(rounded_to_f32(w))
-    floor = np.maximum(np.abs(Rr - Ro), np.abs(Tr - To)).max(axis=(0, 1, 3))
-    err = np.maximum(np.abs(R - Ro), np.abs(T - To)).max(axis=(0, 1, 3))
-    bound = np.maximum(TOL["f32"], 6.0 * floor)
-    assert np.all(np.isfinite(R)) and np.all(np.isfinite(T))
-    assert np.all(err <= bound), [(round(float(np.rad2deg(t)), 1), e, b) for t, e, b in zip(w.theta, err, bound)]
+    err = assert_f32_conditioned(w, R, T, Ro, To, "timing shape")
     # the plain FP32 tolerance holds at every angle up to 81 deg; only the most
     # grazing finite angle (85.3 deg) needs the relaxed bound
     below = np.rad2deg(w.theta) <= 81.0
     assert below.sum() == 18 and np.all(err[below] <= TOL["f32"]), err[below].max()
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32", "f64x"])
+def test_alternating_shared_memory_sizes(prec):
+    # One kernel launched for a deeper, a shallower and again the deeper stack;
+    # all three stage more than the 48 KiB default of shared memory, so the
+    # limit granted for the first launch must still hold for the third.  These
+    # stacks reflect up to 0.9996, where FP32 meets the per-angle reading of
+    # its tolerance rather than 1e-4 at every angle.
+    for L in (97, 71, 97):
+        w = W.plain_fp64(seed=40 + L, S=3, L=L)
+        Ro, To = oracle_RT(w)
+        R, T = gpu_RT(w, prec)
+        if prec == "f32":
+            assert_f32_conditioned(w, R, T, Ro, To, f"L={L}")
+        else:
+            assert_close(R, Ro, TOL[prec], f"R L={L}")
+            assert_close(T, To, TOL[prec], f"T L={L}")
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32", "f64x"])
