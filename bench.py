@@ -667,7 +667,7 @@ def reference_arm(args):
         return
     from paper_2111_13667_gb300 import workloads as W
     w = W.dispersive()
-    per_step = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+    per_step = max(1.0, 60.0 / max(1, args.steps + args.warmup))
     rates = []
     for i in range(args.warmup + args.steps):
         rate, k, t = oracle_sample_rate(w, per_step)
