@@ -4,7 +4,6 @@ slowest rank's time."""
 import os
 import socket
 
-import numpy as np
 import pytest
 import torch.distributed as dist
 import torch.multiprocessing as mp

@@ -9,7 +9,6 @@ import numpy as np
 import pytest
 import torch
 
-import oracle
 from paper_2111_13667_gb300 import abi
 from paper_2111_13667_gb300 import workloads as W
 from tests.helpers import oracle_index, oracle_RT

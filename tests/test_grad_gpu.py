@@ -8,11 +8,10 @@ import numpy as np
 import pytest
 import torch
 
-import oracle
 from paper_2111_13667_gb300 import abi
 from paper_2111_13667_gb300 import autograd as ag
 from paper_2111_13667_gb300 import workloads as W
-from tests.helpers import oracle_grad, oracle_index
+from tests.helpers import oracle_grad
 
 pytestmark = pytest.mark.gpu
 

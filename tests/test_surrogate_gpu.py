@@ -1,7 +1,6 @@
 """The learned surrogate on the GPU: exact training spectra, gradients of the
 tcgen05 training step against a CPU reference, training progress, the exact
 judge with per-row fallback, and checkpoint / resume."""
-import os
 
 import numpy as np
 import pytest

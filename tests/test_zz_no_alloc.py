@@ -5,7 +5,6 @@ workspace, on two calls in a row (the second one starts from the first one's
 leftover scratch contents).  Kept in a file of its own, collected last."""
 import ctypes
 
-import numpy as np
 import pytest
 import torch
 
