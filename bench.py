@@ -358,6 +358,8 @@ def bench_ragged(args, torch, abi, W, flush, world, max_over_ranks):
     return {"workload": w.name, "unit": "evals/s", "dtype": "f32",
             "graph_persistent": {"value": evals / (ms_g * 1e-3), "ms_per_step": ms_g,
                                  "tile_lambda": cfg.tile_lambda, "tile_theta": cfg.tile_theta,
+                                 "tile_note": ("0 x 0: the library's default tile" if cfg.tile_lambda == 0
+                                               else "autotuned tile"),
                                  "persistent": cfg.persistent, "status": status},
             "padded_L120": {"value": evals / (ms_p * 1e-3), "ms_per_step": ms_p},
             "reward": {"value": evals / (ms_r * 1e-3), "ms_per_step": ms_r, "stacks_per_s": w.S * world / (ms_r * 1e-3),

@@ -32,10 +32,14 @@ def shape_key(prob: abi.DeviceProblem, with_T: bool) -> str:
 
 
 def candidates(prob: abi.DeviceProblem, persistent_options=(0, 1)) -> List[abi.TmmLaunchCfg]:
+    """Launch shapes to time.  The library's own shape for the problem (tile
+    fields 0) comes first, so the tuned choice is never slower than the default
+    beyond timing noise, and a problem too small for every listed tile still
+    has a candidate; then tiles of 128, 256 or 512 (lambda, theta) points."""
     nt = int(prob.theta.shape[0])
     nl = int(prob.lam.shape[0])
     tts = sorted({t for t in (nt, (nt + 1) // 2, (nt + 3) // 4, 32, 16, 8) if 1 <= t <= min(nt, 32)})
-    out = []
+    out = [abi.launch_cfg(persistent=pers) for pers in persistent_options]
     for tt in tts:
         for threads in (128, 256, 512):
             tl = threads // tt
@@ -82,7 +86,8 @@ def _store(key, entry):
 
 def tune(prob: abi.DeviceProblem, with_T: bool = True, reps: int = 3, use_cache: bool = True,
          persistent_options=(0, 1), report: Optional[list] = None) -> abi.TmmLaunchCfg:
-    """Fastest launch shape for this problem (cached per GPU and shape class)."""
+    """Fastest launch shape for this problem (cached per GPU and shape class);
+    tile fields 0 in the result mean the library's default shape."""
     key = shape_key(prob, with_T)
     if use_cache:
         ent = _load_cache().get(key)
