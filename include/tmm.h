@@ -74,8 +74,24 @@ typedef enum {
  *           sum of two floats, ~48 significant bits) on the FP32 pipes: the
  *           FP64 tolerance at several times the native FP64 throughput of this
  *           part.  Forward only (tmm_coh_batched / _ex, non-persistent).
+ * TMM_F32D  FP32 arithmetic on double inputs: n_direct / mat_table, d, theta
+ *           and lambda are double (as for TMM_F64), R and T are float.  The
+ *           per-(layer, wavelength) part of each layer phase is formed from
+ *           the double values, so rounding the inputs to float costs nothing;
+ *           the FP32 result then holds the FP32 tolerance also where the
+ *           stack magnifies input rounding (thick resonant stacks near
+ *           grazing incidence).  Forward only (tmm_coh_batched / _ex,
+ *           persistent or not, and tmm_coh_batched_noalloc); every other entry
+ *           point returns TMM_ERR_UNSUPPORTED.
+ *
+ * FP32 layer phase (TMM_F32 and TMM_F32D): the phase of layer j in turns,
+ * (d_j / lambda) Re q_j with q_j = n_j cos(theta_j), is evaluated as
+ * (d_j / lambda) Re n_j -- angle-independent, staged per (layer, wavelength)
+ * in double-float arithmetic -- plus (d_j / lambda) Re(q_j - n_j), where
+ * q_j - n_j = -beta^2 / (q_j + n_j) by Snell's law (beta = n_0 sin theta):
+ * float roundings act only on the angle-dependent part of the phase.
  */
-typedef enum { TMM_F64 = 0, TMM_F32 = 1, TMM_F64X = 2 } tmm_prec;
+typedef enum { TMM_F64 = 0, TMM_F32 = 1, TMM_F64X = 2, TMM_F32D = 3 } tmm_prec;
 
 /* Polarisation bits of tmm_problem.pol_mask; outputs store s before p.
  * TMM_POL_AVG, only together with both TMM_POL_S and TMM_POL_P (pol_mask 7),
@@ -412,13 +428,16 @@ TMM_API tmm_status tmm_surrogate_load(tmm_surrogate *s, const char *path);
  * GPU which loads it keeps until exit; nothing is allocated or freed.
  *   cfg      may be NULL; persistent is forced on; max_items_per_block must be 0
  *            (there is no workspace to report a timeout through).
+ *   prec     TMM_F64, TMM_F32 or TMM_F32D; TMM_F64X returns TMM_ERR_UNSUPPORTED
+ *            (the double-float kernel has no persistent form).
  *   Limit    the problem's persistent workspace (tmm_workspace_size with
  *            persistent = 1: about 4 * (S + 2 * (L_max + 2)) bytes plus
  *            headers) must fit in 1 MiB, i.e. up to ~261,000 stacks for small
  *            L_max; larger problems return TMM_ERR_NOMEM before any launch.
  *   The first call on a device looks up the array's device address (once per
  *   device, with that device current); make that first call before any stream
- *   capture.  Every call shares the one array: calls whose work overlaps on the
+ *   capture.  The address is kept for the life of the process: do not call
+ *   this entry point after cudaDeviceReset of a device it has run on.  Every call shares the one array: calls whose work overlaps on the
  *   GPU (several streams, several host threads) race and must be serialised
  *   by the caller.  Each call zeroes what must start at zero itself.
  */

@@ -28,6 +28,7 @@ TMM_ERR_NOMEM = -5
 TMM_F64 = 0
 TMM_F32 = 1
 TMM_F64X = 2
+TMM_F32D = 3
 TMM_POL_S = 1
 TMM_POL_P = 2
 TMM_POL_AVG = 4
@@ -209,7 +210,8 @@ class DeviceProblem:
 
     @property
     def real_dtype(self):
-        return torch.float32 if self.prec == TMM_F32 else torch.float64
+        """dtype of the outputs (float for TMM_F32 and TMM_F32D)."""
+        return torch.float32 if self.prec in (TMM_F32, TMM_F32D) else torch.float64
 
     @property
     def S(self):
@@ -254,8 +256,9 @@ def pol_mask_of(pols: str) -> int:
 
 
 def to_device(w, prec="f64", device="cuda", pols=None) -> DeviceProblem:
-    """Upload a ``workloads.Workload`` (numpy arrays) as a DeviceProblem."""
-    pr = {"f64": TMM_F64, "f32": TMM_F32, "f64x": TMM_F64X}.get(prec, prec)
+    """Upload a ``workloads.Workload`` (numpy arrays) as a DeviceProblem.
+    prec: "f64", "f32", "f64x" or "f32d" (FP32 arithmetic on double inputs)."""
+    pr = {"f64": TMM_F64, "f32": TMM_F32, "f64x": TMM_F64X, "f32d": TMM_F32D}.get(prec, prec)
     rd = torch.float32 if pr == TMM_F32 else torch.float64
     cd = torch.complex64 if pr == TMM_F32 else torch.complex128
     t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a)).to(device=device, dtype=dt).contiguous()

@@ -82,7 +82,7 @@ tmm_status ensure_dynamic_smem(const void *fn, size_t bytes)
 
 int npol(uint32_t pol_mask) { return (int)(pol_mask & 1u) + (int)((pol_mask >> 1) & 1u); }
 
-size_t real_size(int prec) { return prec == TMM_F32 ? sizeof(float) : sizeof(double); }
+size_t real_size(int prec) { return (prec == TMM_F32 || prec == TMM_F32D) ? sizeof(float) : sizeof(double); }
 
 tmm_status validate_problem(const tmm_problem *p)
 {
@@ -90,7 +90,8 @@ tmm_status validate_problem(const tmm_problem *p)
     if (p->S < 0 || p->L_max < 0 || p->n_lambda < 0 || p->n_theta < 0) return TMM_ERR_INVALID_ARG;
     if (p->pol_mask == 0 || p->pol_mask > 7u) return TMM_ERR_INVALID_ARG;
     if ((p->pol_mask & TMM_POL_AVG) && (p->pol_mask & 3u) != 3u) return TMM_ERR_INVALID_ARG;
-    if (p->prec != TMM_F64 && p->prec != TMM_F32 && p->prec != TMM_F64X) return TMM_ERR_INVALID_ARG;
+    if (p->prec != TMM_F64 && p->prec != TMM_F32 && p->prec != TMM_F64X && p->prec != TMM_F32D)
+        return TMM_ERR_INVALID_ARG;
     if (p->n_direct_per_lambda != 0 && p->n_direct_per_lambda != 1) return TMM_ERR_INVALID_ARG;
     // an empty batch reads no array, so its pointers are not checked
     if ((long long)p->S * p->n_lambda * p->n_theta == 0) return TMM_OK;
@@ -165,7 +166,7 @@ tmm_status tmm_coh_grad(const tmm_problem *p, const void *R_target, void *merit,
     if (p->S == 0) return TMM_OK;
     if (p->n_lambda == 0 || p->n_theta == 0) return TMM_ERR_INVALID_ARG;
     if (!R_target || !merit || (p->L_max > 0 && !dm_dd)) return TMM_ERR_INVALID_ARG;
-    if (p->prec == TMM_F64X || (p->pol_mask & TMM_POL_AVG)) return TMM_ERR_UNSUPPORTED;
+    if ((p->prec != TMM_F64 && p->prec != TMM_F32) || (p->pol_mask & TMM_POL_AVG)) return TMM_ERR_UNSUPPORTED;
     return launch_grad(p, R_target, merit, dm_dd, dm_dn, workspace, workspace_bytes,
                        static_cast<cudaStream_t>(stream));
 }
@@ -175,7 +176,7 @@ tmm_status tmm_reward_workspace_size(const tmm_problem *p, const tmm_launch_cfg 
     if (!bytes) return TMM_ERR_INVALID_ARG;
     tmm_status s = validate_problem(p);
     if (s != TMM_OK) return s;
-    if (p->prec == TMM_F64X) return TMM_ERR_UNSUPPORTED;
+    if (p->prec != TMM_F64 && p->prec != TMM_F32) return TMM_ERR_UNSUPPORTED;
     if (p->S == 0 || p->n_lambda == 0 || p->n_theta == 0) {
         *bytes = 0;
         return TMM_OK;
@@ -191,7 +192,7 @@ tmm_status tmm_coh_reward(const tmm_problem *p, const tmm_launch_cfg *cfg, const
     TraceRange trace("tmm_coh_reward");
     tmm_status s = validate_problem(p);
     if (s != TMM_OK) return s;
-    if (p->prec == TMM_F64X) return TMM_ERR_UNSUPPORTED;
+    if (p->prec != TMM_F64 && p->prec != TMM_F32) return TMM_ERR_UNSUPPORTED;
     if (cfg && (cfg->persistent < 0 || cfg->persistent > 1 || cfg->max_items_per_block != 0))
         return TMM_ERR_INVALID_ARG;
     if (p->S == 0) return TMM_OK;

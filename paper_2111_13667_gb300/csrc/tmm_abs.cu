@@ -291,7 +291,7 @@ extern "C" TMM_API tmm_status tmm_absorption_batched(const tmm_problem *p, void 
     TraceRange trace("tmm_absorption_batched");
     tmm_status s = validate_problem(p);
     if (s != TMM_OK) return s;
-    if (p->prec == TMM_F64X) return TMM_ERR_UNSUPPORTED;
+    if (p->prec != TMM_F64 && p->prec != TMM_F32) return TMM_ERR_UNSUPPORTED;
     if (p->L_max > kAbsMaxLayers) return TMM_ERR_UNSUPPORTED;
     const long long pts = (long long)p->S * p->n_lambda * p->n_theta;
     if (pts == 0) return TMM_OK;

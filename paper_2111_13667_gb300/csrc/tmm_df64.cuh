@@ -161,4 +161,97 @@ __device__ __forceinline__ void interface_pair(cdd k, cdd kn, cdd &x0, cdd &x1)
 }
 
 }  // namespace df
+
+// ---------------------------------------------------------------- shared by the FP32 and double-float kernels
+constexpr double kPi = 3.14159265358979323846264338327950288;
+
+// A double constant as a float pair (the conversions fold at compile time).
+__device__ __forceinline__ df::dd dconst(double v)
+{
+    const float h = (float)v;
+    return df::dd{h, (float)(v - (double)h)};
+}
+
+// {sin hi, sin lo, cos hi, cos lo} of 2 pi k / 256, k = 0..63, built on the host
+// in double precision and passed to the kernels by value.
+struct SinCosTable {
+    float4 sc[64];
+};
+
+// sin and cos of 2 pi f in double-float: f = j/256 + r, |r| <= 1/512; Taylor
+// series of sin, cos (2 pi r) to x^5 / x^6 (remainder below 2^-56), combined
+// with the table entry of j by the angle-addition formulas.
+__device__ __forceinline__ void sincos_turn_dd(df::dd f, const float4 *tab, df::dd *s, df::dd *c)
+{
+    using df::dd;
+    const float jf = rintf(__fmul_rn(f.hi, 256.0f));
+    const int j = (int)jf;
+    const dd r = df::add_f(f, -__fmul_rn(jf, 1.0f / 256.0f));
+    const dd x = df::mul(r, dconst(2.0 * kPi));
+    const dd x2 = df::sqr(x);
+    // sin x = x (1 - x^2/6 + x^4/120), cos x = 1 - x^2/2 + (x^4/24 - x^6/720)
+    const dd t = df::mul(x2, dconst(1.0 / 6.0));
+    const float x4 = __fmul_rn(x2.hi, x2.hi);
+    const dd p = df::add_f(df::sub(df::make(1.0f), t), __fmul_rn(x4, 1.0f / 120.0f));
+    const dd sx = df::mul(x, p);
+    const float h4 = __fsub_rn(__fmul_rn(x4, 1.0f / 24.0f), __fmul_rn(__fmul_rn(x4, x2.hi), 1.0f / 720.0f));
+    const dd cx = df::add_f(df::sub(df::make(1.0f), df::scale2(x2, 0.5f)), h4);
+    const int jj = j & 255, quad = jj >> 6, k = jj & 63;
+    const float4 e = tab[k];
+    const dd sk{e.x, e.y}, ck{e.z, e.w};
+    dd sj, cj;
+    if (quad == 0) { sj = sk; cj = ck; }
+    else if (quad == 1) { sj = ck; cj = df::neg(sk); }
+    else if (quad == 2) { sj = df::neg(sk); cj = df::neg(ck); }
+    else { sj = df::neg(ck); cj = sk; }
+    *s = df::dot2(sj, cx, cj, sx, 1.0f);
+    *c = df::dot2(cj, cx, sj, sx, -1.0f);
+}
+
+// An FP64 value as a float pair hi + lo by integer operations only (no work on
+// the FP64 pipe, which executes ~2 operations per clock per SM on this part):
+// hi keeps the sign, the exponent and the leading 23 stored mantissa bits
+// (truncated), lo the remaining 29 bits rounded to a float, so hi + lo equals
+// x to about 2^-47 relative.  |x| below 2^-126 gives (+-0, 0); |x| at or above
+// 2^128 gives +-inf; NaN stays NaN.  lo is dropped below |x| = 2^-74.
+__host__ __device__ __forceinline__ df::dd split_f64(double x)
+{
+#ifdef __CUDA_ARCH__
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+#else
+    unsigned long long b;
+    __builtin_memcpy(&b, &x, sizeof b);
+#endif
+    const unsigned hi32 = (unsigned)(b >> 32);
+    const unsigned sign = hi32 & 0x80000000u;
+    const int e = (int)((hi32 >> 20) & 0x7ffu);
+    const unsigned mtop = (unsigned)((b >> 29) & 0x7fffffu);
+    const unsigned mlow = (unsigned)(b & 0x1fffffffu);
+    unsigned hb, lb = 0u;
+    if (e == 0x7ff) {  // inf or NaN
+        hb = sign | 0x7f800000u | (((b & 0xfffffffffffffull) != 0ull) ? 0x00400000u : 0u);
+    } else if (e - 896 >= 255) {
+        hb = sign | 0x7f800000u;
+    } else if (e - 896 <= 0) {
+        hb = sign;
+    } else {
+        hb = sign | ((unsigned)(e - 896) << 23) | mtop;
+        if (e >= 949 && mlow != 0u) {
+            // mlow * 2^(e - 1075): the float of mlow times an exact power of two
+            const float m = (float)mlow;
+            const unsigned pb = (unsigned)(e - 948) << 23;
+            float p2;
+            __builtin_memcpy(&p2, &pb, sizeof p2);
+            float l = m * p2;
+            unsigned l_bits;
+            __builtin_memcpy(&l_bits, &l, sizeof l_bits);
+            lb = l_bits | sign;
+        }
+    }
+    float h, l;
+    __builtin_memcpy(&h, &hb, sizeof h);
+    __builtin_memcpy(&l, &lb, sizeof l);
+    return df::dd{h, l};
+}
+
 }  // namespace tmm

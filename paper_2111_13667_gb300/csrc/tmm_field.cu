@@ -600,7 +600,7 @@ extern "C" TMM_API tmm_status tmm_field_profile(const tmm_problem *p, int32_t n_
     TraceRange trace("tmm_field_profile");
     tmm_status s = validate_problem(p);
     if (s != TMM_OK) return s;
-    if (p->prec == TMM_F64X) return TMM_ERR_UNSUPPORTED;
+    if (p->prec != TMM_F64 && p->prec != TMM_F32) return TMM_ERR_UNSUPPORTED;
     if (n_z < 1) return TMM_ERR_INVALID_ARG;
     const long long pts = (long long)p->S * p->n_lambda * p->n_theta;
     if (pts == 0 || p->L_max == 0) return TMM_OK;

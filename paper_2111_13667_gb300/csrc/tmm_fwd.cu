@@ -21,10 +21,12 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <mutex>
 #include <type_traits>
 #include <vector>
 
+#include "tmm_df64.cuh"
 #include "tmm_device.cuh"
 #include "tmm_internal.h"
 
@@ -275,12 +277,260 @@ __device__ __forceinline__ void run_item(const tmm_problem &p, int s, int lt, in
     __syncthreads();
 }
 
+// ---------------------------------------------------------------- FP32 stage and layer phase
+// The FP32 kernels stage, per (medium j, wavelength):
+//   StageA  {n_j^2 - n_0^2, Im n_j^2, 1/n_j^2}, the first rounded once from
+//           double-float arithmetic on the inputs;
+//   StageP  {d_j / lambda, f_j, m_j} with m_j = +-n_j (below) and f_j the
+//           fraction of (d_j / lambda) Re m_j, from a double-float product;
+//   |1/n_j^2|^2;
+// per wavelength the injection index n_0 and per angle of the tile sin and
+// cos of theta, each as a float pair.  Inputs are float (TMM_F32) or double
+// (TMM_F32D, split into float pairs by integer operations).
+//
+// Layer phase.  A float product (d/lambda) Re q carries the roundings of
+// d/lambda, of q and of the product on the whole phase -- several turns in a
+// thick high-index layer, which near grazing incidence a resonant stack turns
+// into errors of 1e-4 in R.  The kernels instead split the phase in turns as
+//   (d/lambda) Re q = f + (d/lambda) Re(q - m),
+//   Re(q - m) = Re((q^2 - m^2) / (q + m)) = -beta^2 Re(1 / (q + m)),
+// using q^2 = n^2 - beta^2 (Snell's law, beta = n_0 sin theta), where m = +-n
+// is the root of n^2 that the interior root of q reaches at normal incidence
+// (Im m >= 0; Re m >= 0 for a real index) and f the fraction of
+// (d/lambda) Re m.  As beta grows, z = n^2 - beta^2 moves parallel to the real
+// axis and q stays in m's quadrant, so |q + m| >= |m|.  f is staged exactly;
+// the second term, computed in float, is small wherever the phase is large:
+// the float roundings act only on the part of the phase that depends on the
+// angle.  Where the wave in the layer is (nearly) evanescent, |Re q| < |Re m|/2,
+// the two terms would cancel, and the plain product (d/lambda) Re q, then
+// small, is used instead (exactly 0 for a lossless evanescent layer).
+struct __align__(16) StageP {
+    float dl, fr, mx, my;  // d/lambda, frac((d/lambda) Re m), m
+};
+
+// Shared-memory layout of an FP32 work item: byte offsets of its arrays.
+struct Stage32Layout {
+    size_t sp, ain2, n0, th, total;
+};
+__host__ __device__ __forceinline__ size_t align16(size_t v) { return (v + 15) / 16 * 16; }
+__host__ __device__ __forceinline__ Stage32Layout stage32_layout(int L_max, int TL, int TT)
+{
+    const size_t m = (size_t)(L_max + 2) * TL;
+    Stage32Layout g;
+    g.sp = m * sizeof(float4);
+    g.ain2 = 2 * m * sizeof(float4);
+    g.n0 = align16(g.ain2 + m * sizeof(float));
+    g.th = align16(g.n0 + (size_t)TL * sizeof(float2));
+    g.total = g.th + (size_t)TT * sizeof(float4);
+    return g;
+}
+
+struct Stage32 {
+    StageA<float> *sa;
+    StageP *sp;
+    float *ain2;
+    float2 *n0;  // (hi, lo); NaN if the injection medium is complex
+    float4 *th;  // {sin hi, sin lo, cos hi, cos lo} of the tile's angles
+};
+
+__device__ __forceinline__ Stage32 stage32_at(unsigned char *smem, int L_max, int TL, int TT)
+{
+    const Stage32Layout g = stage32_layout(L_max, TL, TT);
+    return Stage32{reinterpret_cast<StageA<float> *>(smem), reinterpret_cast<StageP *>(smem + g.sp),
+                   reinterpret_cast<float *>(smem + g.ain2), reinterpret_cast<float2 *>(smem + g.n0),
+                   reinterpret_cast<float4 *>(smem + g.th)};
+}
+
+template <typename In> __device__ __forceinline__ df::dd in_dd(In v);
+template <> __device__ __forceinline__ df::dd in_dd<float>(float v) { return df::dd{v, 0.f}; }
+template <> __device__ __forceinline__ df::dd in_dd<double>(double v)
+{
+    const df::dd t = split_f64(v);
+    return df::fast_two_sum(t.hi, t.lo);  // hi = v rounded to float
+}
+
+// Fill the FP32 stage for media 0..L+1 of stack s, wavelengths l0..l0+TL-1 and
+// angles t0..t0+TT-1.
+template <typename In>
+__device__ __forceinline__ void fill_stage32(const tmm_problem &p, int s, int L, int l0, int TL, int t0, int TT,
+                                             const float4 *tab, const Stage32 &g, int tid, int nthr)
+{
+    const In *lam = (const In *)p.lambda;
+    const In *d = (const In *)p.d;
+    const int total = (L + 2) * TL;
+    for (int idx = tid; idx < total; idx += nthr) {
+        const int j = idx / TL, tl = idx - j * TL;
+        const int l = min(l0 + tl, p.n_lambda - 1);
+        const Cx<In> n = index_of<In>(p, s, j, l);
+        const In n0v = j == 0 ? n.x : index_of<In>(p, s, 0, l).x;
+        const df::dd nx = in_dd<In>(n.x), ny = in_dd<In>(n.y), n0 = in_dd<In>(n0v);
+        // n^2 - n_0^2 = (n' - n_0)(n' + n_0) - n''^2
+        const df::dd d2 = df::sub(df::mul(df::sub(nx, n0), df::add(nx, n0)), df::sqr(ny));
+        const Cx<float> nf = {nx.hi, ny.hi};
+        // Im n^2 with +0 for a real index: the interior root then takes Re q >= 0
+        const Cx<float> n2 = {fmaf(nf.x, nf.x, -nf.y * nf.y), nf.y == 0.f ? 0.f : 2.f * nf.x * nf.y};
+        const float ia = 1.f / abs2(n2);
+        // m = +-n, the interior root of n^2 (Im m >= 0, Re m >= 0 if Im m = 0)
+        const bool flip = nf.y < 0.f || (nf.y == 0.f && nf.x < 0.f);
+        StageA<float> A;
+        A.d2x = d2.hi;
+        A.n2y = n2.y;
+        A.in2x = n2.x * ia;
+        A.in2y = -n2.y * ia;
+        StageP P;
+        P.dl = 0.f;
+        P.fr = 0.f;
+        if (j >= 1 && j <= L) {
+            const df::dd dl = df::div(in_dd<In>(d[(long long)s * p.L_max + (j - 1)]), in_dd<In>(lam[l]));
+            const df::dd ph = df::mul(dl, flip ? df::neg(nx) : nx);
+            const float k = rintf(ph.hi);
+            P.dl = dl.hi;
+            P.fr = __fadd_rn(__fsub_rn(ph.hi, k), ph.lo);
+        }
+        P.mx = flip ? -nf.x : nf.x;
+        P.my = flip ? -nf.y : nf.y;
+        g.sa[idx] = A;
+        g.sp[idx] = P;
+        g.ain2[idx] = ia;
+        if (j == 0) g.n0[tl] = (n.y == In(0)) ? make_float2(n0.hi, n0.lo) : make_float2(nan_w<float>(), 0.f);
+    }
+    const In *th = (const In *)p.theta;
+    for (int i = tid; i < TT; i += nthr) {
+        const int a = min(t0 + i, p.n_theta - 1);
+        const df::dd f = df::mul(in_dd<In>(th[a]), dconst(1.0 / (2.0 * kPi)));
+        df::dd sv, cv;
+        sincos_turn_dd(df::add_f(f, -rintf(f.hi)), tab, &sv, &cv);
+        g.th[i] = make_float4(sv.hi, sv.lo, cv.hi, cv.lo);
+    }
+}
+
+// Per-angle terms of one point from the staged sin, cos (float pairs) and n_0:
+// beta = n_0 sin theta, c0 = n_0 cos theta, q0sq = c0^2, nb2 = -beta^2.
+struct Angle32 {
+    float beta, c0, q0sq, nb2;
+};
+__device__ __forceinline__ Angle32 angle_terms(float4 t, float2 n0v)
+{
+    const df::dd n0{n0v.x, n0v.y};
+    const df::dd b = df::mul(df::dd{t.x, t.y}, n0);
+    const df::dd c = df::mul(df::dd{t.z, t.w}, n0);
+    return Angle32{b.hi, c.hi, df::sqr(c).hi, -df::sqr(b).hi};
+}
+
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// Layer phase Re(delta) / (2 pi) reduced to [-1/2, 1/2] (see above).
+__device__ __forceinline__ float phase_turns(Cx<float> q, const StageP &P, float nb2)
+{
+    const float sx = q.x + P.mx, sy = q.y + P.my;
+    const float rs = rcp_approx(fmaf(sx, sx, sy * sy));
+    const float fm = fmaf(P.dl, nb2 * sx * rs, P.fr);
+    const float f = fabsf(q.x) >= 0.5f * fabsf(P.mx) ? fm : P.dl * q.x;
+    return f - rintf(f);
+}
+
+// phase_turns for the two lanes of a thread (paired instructions).
+__device__ __forceinline__ float2 phase_turns2(Cx<float> qa, Cx<float> qb, const StageP &P, float2 nb2)
+{
+    const float2 qx = f2(qa.x, qb.x);
+    const float2 sx = add2(qx, bc2(P.mx)), sy = add2(f2(qa.y, qb.y), bc2(P.my));
+    const float2 s2 = fma2(sx, sx, mul2(sy, sy));
+    const float2 rs = f2(rcp_approx(s2.x), rcp_approx(s2.y));
+    const float2 fm = fma2(bc2(P.dl), mul2(mul2(nb2, sx), rs), bc2(P.fr));
+    const float2 fd = mul2(bc2(P.dl), qx);
+    const float h = 0.5f * fabsf(P.mx);
+    const float2 f = f2(fabsf(qa.x) >= h ? fm.x : fd.x, fabsf(qb.x) >= h ? fm.y : fd.y);
+    return f2(f.x - rintf(f.x), f.y - rintf(f.y));
+}
+
+// ---------------------------------------------------------------- FP32: one angle per thread
+template <int POL>
+__device__ __forceinline__ void layer_step_f(const Stage32 &g, int TL, int tl, int j, float q0sq, float nb2,
+                                             float yi_max, Sweep<float> &w)
+{
+    const StageA<float> A = g.sa[j * TL + tl];
+    const StageP P = g.sp[j * TL + tl];
+    float absz;
+    const Cx<float> q = inner_root(Cx<float>{A.d2x + q0sq, A.n2y}, &absz);
+    w.Ps *= absz;
+    const float yi = fminf(P.dl * q.y, yi_max);
+    w.Y += yi;
+    float sn, cs;
+    sincos_turn(phase_turns(q, P, nb2), &sn, &cs);
+    const float E2 = exp_m2_turn(yi);
+    const Cx<float> emi = {cs, -sn};
+    const Cx<float> epi = {E2 * cs, E2 * sn};
+    if (POL & 1) {
+        interface_pair(q, w.q_nx, w.s0, w.s1);
+        w.s0 = cmul(emi, w.s0);
+        w.s1 = cmul(epi, w.s1);
+    }
+    if (POL & 2) {
+        w.Pp *= g.ain2[j * TL + tl];
+        const Cx<float> gq = cmul(q, Cx<float>{A.in2x, A.in2y});
+        interface_pair(gq, w.g_nx, w.p0, w.p1);
+        w.p0 = cmul(emi, w.p0);
+        w.p1 = cmul(epi, w.p1);
+        w.g_nx = gq;
+    }
+    w.q_nx = q;
+}
+
+template <int POL>
+__device__ __forceinline__ void eval_point_f(const Stage32 &g, int TL, int tl, int L, float n0, const Angle32 &an,
+                                             float out[4])
+{
+    constexpr int RN = RenormEvery<float>::value;
+    const float yi_max = float(kImDeltaMax / kTwoPi);
+    const StageA<float> A = g.sa[(L + 1) * TL + tl];
+    float absz;
+    Sweep<float> w;
+    w.q_nx = forward_root(Cx<float>{A.d2x + an.q0sq, A.n2y}, &absz);
+    const Cx<float> q_out = w.q_nx, n2_out = {A.d2x + n0 * n0, A.n2y};
+    w.g_nx = cmul(w.q_nx, Cx<float>{A.in2x, A.in2y});
+    w.Ps = 1.f, w.Y = 0.f;
+    int eP = 0;
+    w.Pp = (POL & 2) ? g.ain2[(L + 1) * TL + tl] : 1.f;
+    int ePp = 0;
+    w.s0 = {1.f, 0.f}, w.s1 = {0.f, 0.f}, w.p0 = {1.f, 0.f}, w.p1 = {0.f, 0.f};
+    int es = 0, ep = 0;
+    int j = L;
+    for (; j >= 2 * RN; j -= 2 * RN) {
+#pragma unroll
+        for (int k = 0; k < RN; ++k) layer_step_f<POL>(g, TL, tl, j - k, an.q0sq, an.nb2, yi_max, w);
+        if (POL & 1) renorm_pair(w.s0, w.s1, es);
+        if (POL & 2) renorm_pair(w.p0, w.p1, ep);
+#pragma unroll
+        for (int k = RN; k < 2 * RN; ++k) layer_step_f<POL>(g, TL, tl, j - k, an.q0sq, an.nb2, yi_max, w);
+        renorm_scalar(w.Ps, eP);
+        if (POL & 2) renorm_scalar(w.Pp, ePp);
+        if (POL & 1) renorm_pair(w.s0, w.s1, es);
+        if (POL & 2) renorm_pair(w.p0, w.p1, ep);
+    }
+    for (; j >= RN; j -= RN) {
+#pragma unroll
+        for (int k = 0; k < RN; ++k) layer_step_f<POL>(g, TL, tl, j - k, an.q0sq, an.nb2, yi_max, w);
+        renorm_scalar(w.Ps, eP);
+        if (POL & 2) renorm_scalar(w.Pp, ePp);
+        if (POL & 1) renorm_pair(w.s0, w.s1, es);
+        if (POL & 2) renorm_pair(w.p0, w.p1, ep);
+    }
+    for (; j >= 1; --j) layer_step_f<POL>(g, TL, tl, j, an.q0sq, an.nb2, yi_max, w);
+    finish_point<float, POL>(g.sa[tl], q_out, n2_out, w.q_nx, w.g_nx, w.s0, w.s1, w.p0, w.p1, w.Ps, w.Y, w.Pp, eP,
+                             ePp, es, ep, L, n0, an.beta, an.c0, out);
+}
+
 // ---------------------------------------------------------------- FP32: two angles per thread
 // An FP32 thread carries two angles of one wavelength on the two lanes of the
 // paired instructions: the amplitude pairs, |q|^2 products and phase sums are
 // float2 per component; the stage (per medium and wavelength) and the p index
 // product are shared.  Roots, sin/cos and exp2 stay per lane (one MUFU each).
-// The arithmetic is the scalar path's up to the order of two additions per
+// The arithmetic is the one-angle path's up to the order of two additions per
 // interface and the branch of q inside the stack, which R and T do not see.
 struct Sweep2 {
     C2 q_nx, g_nx;        // q and q / n^2 of the medium to the right
@@ -291,21 +541,21 @@ struct Sweep2 {
 };
 
 template <int POL>
-__device__ __forceinline__ void layer_step2(const StageA<float> *__restrict__ sa, const StageB<float> *__restrict__ sb,
-                                            int TL, int tl, int j, float2 q0sq, float yi_max, Sweep2 &w)
+__device__ __forceinline__ void layer_step2(const Stage32 &g, int TL, int tl, int j, float2 q0sq, float2 nb2,
+                                            float yi_max, Sweep2 &w)
 {
-    const StageA<float> A = sa[j * TL + tl];
-    const StageB<float> B = sb[j * TL + tl];
+    const StageA<float> A = g.sa[j * TL + tl];
+    const StageP P = g.sp[j * TL + tl];
     float absa, absb;
     const Cx<float> qa = inner_root(Cx<float>{A.d2x + q0sq.x, A.n2y}, &absa);
     const Cx<float> qb = inner_root(Cx<float>{A.d2x + q0sq.y, A.n2y}, &absb);
     w.Ps = mul2(w.Ps, f2(absa, absb));
-    const float yra = B.dl * qa.x, yrb = B.dl * qb.x;
-    const float2 yi = f2(fminf(B.dl * qa.y, yi_max), fminf(B.dl * qb.y, yi_max));
+    const float2 yi = f2(fminf(P.dl * qa.y, yi_max), fminf(P.dl * qb.y, yi_max));
     w.Y = add2(w.Y, yi);
+    const float2 f = phase_turns2(qa, qb, P, nb2);
     float2 sn, cs;
-    sincos_turn(yra - rintf(yra), &sn.x, &cs.x);
-    sincos_turn(yrb - rintf(yrb), &sn.y, &cs.y);
+    sincos_turn(f.x, &sn.x, &cs.x);
+    sincos_turn(f.y, &sn.y, &cs.y);
     const float2 E2 = f2(exp_m2_turn(yi.x), exp_m2_turn(yi.y));
     const float2 nsn = neg2(sn), ec = mul2(E2, cs), es = mul2(E2, sn), nes = neg2(es);
     if (POL & 1) {
@@ -317,29 +567,28 @@ __device__ __forceinline__ void layer_step2(const StageA<float> *__restrict__ sa
         w.nqy_nx = nqy;
     }
     if (POL & 2) {
-        w.Pp *= B.ain2;
+        w.Pp *= g.ain2[j * TL + tl];
         const Cx<float> in2 = {A.in2x, A.in2y};
-        const C2 g = pack2(cmul(qa, in2), cmul(qb, in2));
-        const float2 ngy = neg2(g.y);
-        interface_pair2(g, ngy, w.g_nx, w.ngy_nx, w.p0, w.p1);
+        const C2 gq = pack2(cmul(qa, in2), cmul(qb, in2));
+        const float2 ngy = neg2(gq.y);
+        interface_pair2(gq, ngy, w.g_nx, w.ngy_nx, w.p0, w.p1);
         phase2(cs, sn, nsn, ec, es, nes, w.p0, w.p1);
-        w.g_nx = g;
+        w.g_nx = gq;
         w.ngy_nx = ngy;
     }
 }
 
-// eval_point for the angles with (sin, cos) in the lanes of st, ct:
-// out[i] = {R_s, T_s, R_p, T_p} of lane i.
+// eval_point_f for the angles of the two lanes: out[i] = {R_s, T_s, R_p, T_p}
+// of lane i.
 template <int POL>
-__device__ __forceinline__ void eval_point2(const StageA<float> *__restrict__ sa, const StageB<float> *__restrict__ sb,
-                                            int TL, int tl, int L, float n0, float2 st, float2 ct, float out[2][4])
+__device__ __forceinline__ void eval_point2(const Stage32 &g, int TL, int tl, int L, float n0, const Angle32 an[2],
+                                            float out[2][4])
 {
     constexpr int RN = RenormEvery<float>::value;
-    const float2 beta = f2(n0 * st.x, n0 * st.y), c0 = f2(n0 * ct.x, n0 * ct.y);
-    const float2 q0sq = f2(c0.x * c0.x, c0.y * c0.y);
+    const float2 q0sq = f2(an[0].q0sq, an[1].q0sq), nb2 = f2(an[0].nb2, an[1].nb2);
     const float yi_max = float(kImDeltaMax / kTwoPi);
 
-    const StageA<float> A = sa[(L + 1) * TL + tl];
+    const StageA<float> A = g.sa[(L + 1) * TL + tl];
     float absz;
     const Cx<float> qoa = forward_root(Cx<float>{A.d2x + q0sq.x, A.n2y}, &absz);
     const Cx<float> qob = forward_root(Cx<float>{A.d2x + q0sq.y, A.n2y}, &absz);
@@ -352,7 +601,7 @@ __device__ __forceinline__ void eval_point2(const StageA<float> *__restrict__ sa
     w.ngy_nx = neg2(w.g_nx.y);
     w.Ps = bc2(1.f);
     w.Y = bc2(0.f);
-    w.Pp = (POL & 2) ? sb[(L + 1) * TL + tl].ain2 : 1.f;
+    w.Pp = (POL & 2) ? g.ain2[(L + 1) * TL + tl] : 1.f;
     int ePa = 0, ePb = 0, ePp = 0;
     w.s0 = C2{bc2(1.f), bc2(0.f)};
     w.s1 = C2{bc2(0.f), bc2(0.f)};
@@ -360,16 +609,16 @@ __device__ __forceinline__ void eval_point2(const StageA<float> *__restrict__ sa
     w.p1 = w.s1;
     int esa = 0, esb = 0, epa = 0, epb = 0;
 
-    // the scalar kernel's grouping: RN layers, rescale the pairs, RN more,
+    // the one-angle kernel's grouping: RN layers, rescale the pairs, RN more,
     // rescale the products and the pairs
     int j = L;
     for (; j >= 2 * RN; j -= 2 * RN) {
 #pragma unroll
-        for (int k = 0; k < RN; ++k) layer_step2<POL>(sa, sb, TL, tl, j - k, q0sq, yi_max, w);
+        for (int k = 0; k < RN; ++k) layer_step2<POL>(g, TL, tl, j - k, q0sq, nb2, yi_max, w);
         if (POL & 1) renorm_pair2(w.s0, w.s1, esa, esb);
         if (POL & 2) renorm_pair2(w.p0, w.p1, epa, epb);
 #pragma unroll
-        for (int k = RN; k < 2 * RN; ++k) layer_step2<POL>(sa, sb, TL, tl, j - k, q0sq, yi_max, w);
+        for (int k = RN; k < 2 * RN; ++k) layer_step2<POL>(g, TL, tl, j - k, q0sq, nb2, yi_max, w);
         renorm_scalar(w.Ps.x, ePa);
         renorm_scalar(w.Ps.y, ePb);
         if (POL & 2) renorm_scalar(w.Pp, ePp);
@@ -378,52 +627,54 @@ __device__ __forceinline__ void eval_point2(const StageA<float> *__restrict__ sa
     }
     for (; j >= RN; j -= RN) {
 #pragma unroll
-        for (int k = 0; k < RN; ++k) layer_step2<POL>(sa, sb, TL, tl, j - k, q0sq, yi_max, w);
+        for (int k = 0; k < RN; ++k) layer_step2<POL>(g, TL, tl, j - k, q0sq, nb2, yi_max, w);
         renorm_scalar(w.Ps.x, ePa);
         renorm_scalar(w.Ps.y, ePb);
         if (POL & 2) renorm_scalar(w.Pp, ePp);
         if (POL & 1) renorm_pair2(w.s0, w.s1, esa, esb);
         if (POL & 2) renorm_pair2(w.p0, w.p1, epa, epb);
     }
-    for (; j >= 1; --j) layer_step2<POL>(sa, sb, TL, tl, j, q0sq, yi_max, w);
-    finish_point<float, POL>(sa[tl], qoa, n2_out, lane(w.q_nx, 0), lane(w.g_nx, 0), lane(w.s0, 0), lane(w.s1, 0),
-                             lane(w.p0, 0), lane(w.p1, 0), w.Ps.x, w.Y.x, w.Pp, ePa, ePp, esa, epa, L, n0, beta.x,
-                             c0.x, out[0]);
-    finish_point<float, POL>(sa[tl], qob, n2_out, lane(w.q_nx, 1), lane(w.g_nx, 1), lane(w.s0, 1), lane(w.s1, 1),
-                             lane(w.p0, 1), lane(w.p1, 1), w.Ps.y, w.Y.y, w.Pp, ePb, ePp, esb, epb, L, n0, beta.y,
-                             c0.y, out[1]);
+    for (; j >= 1; --j) layer_step2<POL>(g, TL, tl, j, q0sq, nb2, yi_max, w);
+    finish_point<float, POL>(g.sa[tl], qoa, n2_out, lane(w.q_nx, 0), lane(w.g_nx, 0), lane(w.s0, 0), lane(w.s1, 0),
+                             lane(w.p0, 0), lane(w.p1, 0), w.Ps.x, w.Y.x, w.Pp, ePa, ePp, esa, epa, L, n0, an[0].beta,
+                             an[0].c0, out[0]);
+    finish_point<float, POL>(g.sa[tl], qob, n2_out, lane(w.q_nx, 1), lane(w.g_nx, 1), lane(w.s0, 1), lane(w.s1, 1),
+                             lane(w.p0, 1), lane(w.p1, 1), w.Ps.y, w.Y.y, w.Pp, ePb, ePp, esb, epb, L, n0, an[1].beta,
+                             an[1].c0, out[1]);
 }
 
-// run_item for FP32 with two angles per thread: the block is TL x ceil(TT/2)
-// threads, thread (x, y) taking angles t0 + 2y and t0 + 2y + 1.
-template <int POL, bool WITH_T, bool RED>
-__device__ __forceinline__ void run_item2(const tmm_problem &p, int s, int lt, int tt, int n_tt, int TL, int TT,
-                                          unsigned char *smem, float *__restrict__ Rout, float *__restrict__ Tout,
-                                          const Reduce<float> &red)
+// One FP32 work item: PAIR blocks are TL x ceil(TT / 2) threads, thread
+// (x, y) taking angles t0 + 2y and t0 + 2y + 1; otherwise TL x TT threads of
+// one angle each.  Inputs of type In (float, or double for TMM_F32D).
+template <typename In, int POL, bool WITH_T, bool RED, bool PAIR>
+__device__ __forceinline__ void run_item_f32(const tmm_problem &p, const float4 *tab, int s, int lt, int tt, int n_tt,
+                                             int TL, int TT, unsigned char *smem, float *__restrict__ Rout,
+                                             float *__restrict__ Tout, const Reduce<float> &red)
 {
-    StageA<float> *sa = reinterpret_cast<StageA<float> *>(smem);
-    StageB<float> *sb = reinterpret_cast<StageB<float> *>(sa + (size_t)(p.L_max + 2) * TL);
-    float *n0s = reinterpret_cast<float *>(sb + (size_t)(p.L_max + 2) * TL);
-
+    const Stage32 g = stage32_at(smem, p.L_max, TL, TT);
     const int tid = threadIdx.y * TL + threadIdx.x;
     const int nthr = TL * (int)blockDim.y;
     const int L = layers_of(p, s);
     const int l0 = lt * TL, t0 = tt * TT;
-    if (L >= 0) fill_stage<float>(p, s, L, l0, TL, sa, sb, n0s, tid, nthr);
+    if (L >= 0) fill_stage32<In>(p, s, L, l0, TL, t0, TT, tab, g, tid, nthr);
     __syncthreads();
 
+    constexpr int NP = PAIR ? 2 : 1;
     const int tl = threadIdx.x, l = l0 + tl;
-    const int a0 = t0 + 2 * (int)threadIdx.y, t_end = min(t0 + TT, p.n_theta);
-    const bool v1 = a0 + 1 < t_end;
+    const int a0 = t0 + NP * (int)threadIdx.y, t_end = min(t0 + TT, p.n_theta);
+    const int np = (PAIR && a0 + 1 < t_end) ? 2 : 1;
     float contrib = 0.f;
     if (l < p.n_lambda && a0 < t_end) {
         float out[2][4];
         if (L >= 0) {
-            const float *th = (const float *)p.theta;
-            float2 st, ct;
-            sincos_w(th[a0], &st.x, &ct.x);
-            sincos_w(th[v1 ? a0 + 1 : a0], &st.y, &ct.y);
-            eval_point2<POL>(sa, sb, TL, tl, L, n0s[tl], st, ct, out);
+            const float2 n0 = g.n0[tl];
+            Angle32 an[2];
+            an[0] = angle_terms(g.th[a0 - t0], n0);
+            an[1] = PAIR ? angle_terms(g.th[a0 - t0 + np - 1], n0) : an[0];
+            if constexpr (PAIR)
+                eval_point2<POL>(g, TL, tl, L, n0.x, an, out);
+            else
+                eval_point_f<POL>(g, TL, tl, L, n0.x, an[0], out[0]);
         } else {
 #pragma unroll
             for (int i = 0; i < 2; ++i) out[i][0] = out[i][1] = out[i][2] = out[i][3] = nan_w<float>();
@@ -431,8 +682,8 @@ __device__ __forceinline__ void run_item2(const tmm_problem &p, int s, int lt, i
         const long long tplane = (long long)p.n_theta * p.n_lambda;
         const long long plane = (long long)p.S * tplane;
 #pragma unroll
-        for (int i = 0; i < 2; ++i) {
-            if (i == 1 && !v1) break;
+        for (int i = 0; i < NP; ++i) {
+            if (i == 1 && np < 2) break;
             const int a = a0 + i;
             if (RED) {
                 const long long ot = (long long)a * p.n_lambda + l;
@@ -478,38 +729,41 @@ __device__ __forceinline__ void run_item2(const tmm_problem &p, int s, int lt, i
     __syncthreads();
 }
 
-// The item evaluator of a kernel instance: paired lanes (FP32 only) or scalar.
-template <typename R, int POL, bool WITH_T, bool RED, bool PAIR>
-__device__ __forceinline__ void run_any(const tmm_problem &p, int s, int lt, int tt, int n_tt, int TL, int TT,
-                                        unsigned char *smem, R *__restrict__ Rout, R *__restrict__ Tout,
-                                        const Reduce<R> &red)
+// The item evaluator of a kernel instance: FP32 (float or double inputs,
+// paired lanes or one angle per thread) or FP64.
+template <typename R, typename In, int POL, bool WITH_T, bool RED, bool PAIR>
+__device__ __forceinline__ void run_any(const tmm_problem &p, const SinCosTable &tab, int s, int lt, int tt, int n_tt,
+                                        int TL, int TT, unsigned char *smem, R *__restrict__ Rout,
+                                        R *__restrict__ Tout, const Reduce<R> &red)
 {
-    if constexpr (PAIR)
-        run_item2<POL, WITH_T, RED>(p, s, lt, tt, n_tt, TL, TT, smem, Rout, Tout, red);
+    if constexpr (std::is_same<R, float>::value)
+        run_item_f32<In, POL, WITH_T, RED, PAIR>(p, tab.sc, s, lt, tt, n_tt, TL, TT, smem, Rout, Tout, red);
     else
         run_item<R, POL, WITH_T, RED>(p, s, lt, tt, n_tt, TL, TT, smem, Rout, Tout, red);
 }
 
-template <typename R, int POL, bool WITH_T, bool RED, bool PAIR>
-__global__ void __launch_bounds__(PAIR ? kPairThreads : kMaxThreads, PAIR ? kPairBlocks : 1) tmm_fwd_kernel(const tmm_problem p, int TL, int TT, int n_lt, int n_tt,
-                                                       R *__restrict__ Rout, R *__restrict__ Tout, const Reduce<R> red)
+template <typename R, typename In, int POL, bool WITH_T, bool RED, bool PAIR>
+__global__ void __launch_bounds__(PAIR ? kPairThreads : kMaxThreads, PAIR ? kPairBlocks : 1)
+    tmm_fwd_kernel(const tmm_problem p, const __grid_constant__ SinCosTable tab, int TL, int TT, int n_lt, int n_tt,
+                   R *__restrict__ Rout, R *__restrict__ Tout, const Reduce<R> red)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const long long item = blockIdx.x;
     const int per_stack = n_lt * n_tt;
     const int s = (int)(item / per_stack);
     const int r = (int)(item - (long long)s * per_stack);
-    run_any<R, POL, WITH_T, RED, PAIR>(p, s, r / n_tt, r % n_tt, n_tt, TL, TT, smem, Rout, Tout, red);
+    run_any<R, In, POL, WITH_T, RED, PAIR>(p, tab, s, r / n_tt, r % n_tt, n_tt, TL, TT, smem, Rout, Tout, red);
 }
 
 // Persistent variant: blocks pull work items from `counter`; item k belongs to
-// stack order[k / per_stack] (longest stacks first), tile k % per_stack.
-template <typename R, int POL, bool WITH_T, bool RED, bool PAIR>
-__global__ void __launch_bounds__(PAIR ? kPairThreads : kMaxThreads, PAIR ? kPairBlocks : 1) tmm_fwd_persistent(const tmm_problem p, int TL, int TT, int n_lt, int n_tt,
-                                                           const int *__restrict__ order, unsigned int *counter,
-                                                           int *err, unsigned int n_items, int max_items,
-                                                           R *__restrict__ Rout, R *__restrict__ Tout,
-                                                           const Reduce<R> red)
+// stack order[k / per_stack] (longest stacks first), tile k % per_stack.  The
+// host keeps n_items + grid below 2^32, so the one increment past n_items that
+// each block makes before it leaves cannot wrap the counter.
+template <typename R, typename In, int POL, bool WITH_T, bool RED, bool PAIR>
+__global__ void __launch_bounds__(PAIR ? kPairThreads : kMaxThreads, PAIR ? kPairBlocks : 1)
+    tmm_fwd_persistent(const tmm_problem p, const __grid_constant__ SinCosTable tab, int TL, int TT, int n_lt,
+                       int n_tt, const int *__restrict__ order, unsigned int *counter, int *err, unsigned int n_items,
+                       int max_items, R *__restrict__ Rout, R *__restrict__ Tout, const Reduce<R> red)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ unsigned int item_sh;
@@ -527,7 +781,8 @@ __global__ void __launch_bounds__(PAIR ? kPairThreads : kMaxThreads, PAIR ? kPai
         }
         const int k = (int)(item / per_stack);
         const int r = (int)(item - (unsigned int)k * per_stack);
-        run_any<R, POL, WITH_T, RED, PAIR>(p, order[k], r / n_tt, r % n_tt, n_tt, TL, TT, smem, Rout, Tout, red);
+        run_any<R, In, POL, WITH_T, RED, PAIR>(p, tab, order[k], r / n_tt, r % n_tt, n_tt, TL, TT, smem, Rout, Tout,
+                                               red);
     }
 }
 
@@ -582,14 +837,32 @@ PersistentWs persistent_ws_layout(const tmm_problem *p)
     return w;
 }
 
-static size_t stage_bytes(const tmm_problem *p, int TL)
+static bool fp32_family(const tmm_problem *p) { return p->prec == TMM_F32 || p->prec == TMM_F32D; }
+
+static size_t stage_bytes(const tmm_problem *p, int TL, int TT)
 {
+    if (fp32_family(p)) return stage32_layout(p->L_max, TL, TT).total;
     const size_t r = real_size(p->prec);
     return (size_t)(p->L_max + 2) * TL * (6 * r) + (size_t)TL * r;
 }
 
 // FP32 tiles of two or more angles run two angles per thread (paired lanes).
-static bool paired(const tmm_problem *p, int TT) { return p->prec == TMM_F32 && TT >= 2; }
+static bool paired(const tmm_problem *p, int TT) { return fp32_family(p) && TT >= 2; }
+
+const SinCosTable &sincos_table()
+{
+    static SinCosTable t;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        for (int k = 0; k < 64; ++k) {
+            const double a = 2.0 * kPi * k / 256.0;
+            const double sv = std::sin(a), cv = std::cos(a);
+            const float sh = (float)sv, ch = (float)cv;
+            t.sc[k] = make_float4(sh, (float)(sv - sh), ch, (float)(cv - ch));
+        }
+    });
+    return t;
+}
 
 static int tile_threads(const tmm_problem *p, int TL, int TT) { return TL * (paired(p, TT) ? (TT + 1) / 2 : TT); }
 static int max_threads(const tmm_problem *p, int TT) { return paired(p, TT) ? kPairThreads : kMaxThreads; }
@@ -606,7 +879,7 @@ tmm_status choose_tile(const tmm_problem *p, const tmm_launch_cfg *cfg, Tile *t)
         TL = 1;
         while (tile_threads(p, TL, TT) < 256 && tile_threads(p, 2 * TL, TT) <= max_threads(p, TT)) TL *= 2;
         while (TL > 1 && TL / 2 >= p->n_lambda) TL /= 2;
-        while (TL > 1 && stage_bytes(p, TL) > (size_t)di.max_smem_optin) TL /= 2;
+        while (TL > 1 && stage_bytes(p, TL, TT) > (size_t)di.max_smem_optin) TL /= 2;
     }
     if (TL < 1 || tile_threads(p, TL, TT) > max_threads(p, TT)) return TMM_ERR_INVALID_ARG;
     t->TL = TL;
@@ -614,7 +887,7 @@ tmm_status choose_tile(const tmm_problem *p, const tmm_launch_cfg *cfg, Tile *t)
     t->n_lt = (p->n_lambda + TL - 1) / TL;
     t->n_tt = (p->n_theta + TT - 1) / TT;
     t->n_items = (long long)p->S * t->n_lt * t->n_tt;
-    t->smem = stage_bytes(p, TL);
+    t->smem = stage_bytes(p, TL, TT);
     if (t->smem > (size_t)di.max_smem_optin) return TMM_ERR_UNSUPPORTED;
     return TMM_OK;
 }
@@ -660,7 +933,7 @@ static tmm_status prepare_kernel(Kernel k, int threads, size_t smem, bool need_o
     return TMM_OK;
 }
 
-template <typename R, int POL, bool WITH_T, bool RED, bool PAIR>
+template <typename R, typename In, int POL, bool WITH_T, bool RED, bool PAIR>
 static tmm_status launch_shaped(const tmm_problem *p, const tmm_launch_cfg *cfg, const Tile &t, void *ws,
                                 R *Rout, R *Tout, const Reduce<R> &red, cudaStream_t st)
 {
@@ -668,19 +941,27 @@ static tmm_status launch_shaped(const tmm_problem *p, const tmm_launch_cfg *cfg,
     const int threads = (int)(block.x * block.y);
     const bool persistent = cfg && cfg->persistent;
     if (!persistent) {
-        auto k = tmm_fwd_kernel<R, POL, WITH_T, RED, PAIR>;
+        auto k = tmm_fwd_kernel<R, In, POL, WITH_T, RED, PAIR>;
         tmm_status s = prepare_kernel(k, threads, t.smem, false, nullptr);
         if (s != TMM_OK) return s;
         if (t.n_items > 0x7fffffffLL) return TMM_ERR_UNSUPPORTED;
         if (t.n_items == 0) return TMM_OK;
-        k<<<(unsigned)t.n_items, block, t.smem, st>>>(*p, t.TL, t.TT, t.n_lt, t.n_tt, Rout, Tout, red);
+        k<<<(unsigned)t.n_items, block, t.smem, st>>>(*p, sincos_table(), t.TL, t.TT, t.n_lt, t.n_tt, Rout, Tout,
+                                                     red);
         return check_launch();
     }
-    auto k = tmm_fwd_persistent<R, POL, WITH_T, RED, PAIR>;
+    auto k = tmm_fwd_persistent<R, In, POL, WITH_T, RED, PAIR>;
     int occ = 0;
     tmm_status s = prepare_kernel(k, threads, t.smem, true, &occ);
     if (s != TMM_OK) return s;
-    if (t.n_items > 0xffffffffLL) return TMM_ERR_UNSUPPORTED;
+    DeviceInfo di;
+    s = device_info(&di);
+    if (s != TMM_OK) return s;
+    const int per_sm = cfg->blocks_per_sm > 0 ? cfg->blocks_per_sm : occ;
+    const long long grid = std::min((long long)per_sm * di.sms, t.n_items);
+    // each block takes one item number past n_items before it leaves: keep the
+    // 32-bit counter from wrapping
+    if (t.n_items + grid > 0xffffffffLL) return TMM_ERR_UNSUPPORTED;
     const PersistentWs w = persistent_ws_layout(p);
     unsigned char *base = static_cast<unsigned char *>(ws);
     cudaError_t e = cudaMemsetAsync(base, 0, w.order, st);  // counter, err, counts, offsets
@@ -701,50 +982,49 @@ static tmm_status launch_shaped(const tmm_problem *p, const tmm_launch_cfg *cfg,
         if (cs != TMM_OK) return cs;
     }
     if (t.n_items == 0) return TMM_OK;
-    DeviceInfo di;
-    s = device_info(&di);
-    if (s != TMM_OK) return s;
-    const int per_sm = cfg->blocks_per_sm > 0 ? cfg->blocks_per_sm : occ;
-    long long grid = (long long)per_sm * di.sms;
-    grid = std::min(grid, t.n_items);
-    k<<<(unsigned)grid, block, t.smem, st>>>(*p, t.TL, t.TT, t.n_lt, t.n_tt, order,
+    k<<<(unsigned)grid, block, t.smem, st>>>(*p, sincos_table(), t.TL, t.TT, t.n_lt, t.n_tt, order,
                                              reinterpret_cast<unsigned int *>(base + w.counter),
                                              reinterpret_cast<int *>(base + w.err), (unsigned)t.n_items,
                                              cfg->max_items_per_block, Rout, Tout, red);
     return check_launch();
 }
 
-template <typename R, int POL, bool WITH_T, bool RED>
+template <typename R, typename In, int POL, bool WITH_T, bool RED>
 static tmm_status launch_typed(const tmm_problem *p, const tmm_launch_cfg *cfg, const Tile &t, void *ws,
                                R *Rout, R *Tout, const Reduce<R> &red, cudaStream_t st)
 {
     if constexpr (std::is_same<R, float>::value) {
-        if (paired(p, t.TT)) return launch_shaped<R, POL, WITH_T, RED, true>(p, cfg, t, ws, Rout, Tout, red, st);
+        if (paired(p, t.TT))
+            return launch_shaped<R, In, POL, WITH_T, RED, true>(p, cfg, t, ws, Rout, Tout, red, st);
     }
-    return launch_shaped<R, POL, WITH_T, RED, false>(p, cfg, t, ws, Rout, Tout, red, st);
+    return launch_shaped<R, In, POL, WITH_T, RED, false>(p, cfg, t, ws, Rout, Tout, red, st);
 }
 
-template <typename R>
+template <typename R, typename In>
 static tmm_status launch_prec(const tmm_problem *p, const tmm_launch_cfg *cfg, const Tile &t, void *ws, void *R_,
                               void *T_, const Reduce<R> &red, cudaStream_t st)
 {
     R *Ro = static_cast<R *>(R_);
     R *To = static_cast<R *>(T_);
-    if (red.Rt) {  // reduction mode: no R, T output
-        switch (p->pol_mask) {
-        case 1: return launch_typed<R, 1, false, true>(p, cfg, t, ws, Ro, To, red, st);
-        case 2: return launch_typed<R, 2, false, true>(p, cfg, t, ws, Ro, To, red, st);
-        case 3: return launch_typed<R, 3, false, true>(p, cfg, t, ws, Ro, To, red, st);
-        case 7: return launch_typed<R, 7, false, true>(p, cfg, t, ws, Ro, To, red, st);
-        default: return TMM_ERR_INVALID_ARG;
+    if (red.Rt) {  // reduction mode: no R, T output (inputs of the working type only)
+        if constexpr (std::is_same<R, In>::value) {
+            switch (p->pol_mask) {
+            case 1: return launch_typed<R, In, 1, false, true>(p, cfg, t, ws, Ro, To, red, st);
+            case 2: return launch_typed<R, In, 2, false, true>(p, cfg, t, ws, Ro, To, red, st);
+            case 3: return launch_typed<R, In, 3, false, true>(p, cfg, t, ws, Ro, To, red, st);
+            case 7: return launch_typed<R, In, 7, false, true>(p, cfg, t, ws, Ro, To, red, st);
+            default: return TMM_ERR_INVALID_ARG;
+            }
+        } else {
+            return TMM_ERR_UNSUPPORTED;
         }
     }
     const bool wt = To != nullptr;
     switch (p->pol_mask) {
-    case 1: return wt ? launch_typed<R, 1, true, false>(p, cfg, t, ws, Ro, To, red, st) : launch_typed<R, 1, false, false>(p, cfg, t, ws, Ro, To, red, st);
-    case 2: return wt ? launch_typed<R, 2, true, false>(p, cfg, t, ws, Ro, To, red, st) : launch_typed<R, 2, false, false>(p, cfg, t, ws, Ro, To, red, st);
-    case 3: return wt ? launch_typed<R, 3, true, false>(p, cfg, t, ws, Ro, To, red, st) : launch_typed<R, 3, false, false>(p, cfg, t, ws, Ro, To, red, st);
-    case 7: return wt ? launch_typed<R, 7, true, false>(p, cfg, t, ws, Ro, To, red, st) : launch_typed<R, 7, false, false>(p, cfg, t, ws, Ro, To, red, st);
+    case 1: return wt ? launch_typed<R, In, 1, true, false>(p, cfg, t, ws, Ro, To, red, st) : launch_typed<R, In, 1, false, false>(p, cfg, t, ws, Ro, To, red, st);
+    case 2: return wt ? launch_typed<R, In, 2, true, false>(p, cfg, t, ws, Ro, To, red, st) : launch_typed<R, In, 2, false, false>(p, cfg, t, ws, Ro, To, red, st);
+    case 3: return wt ? launch_typed<R, In, 3, true, false>(p, cfg, t, ws, Ro, To, red, st) : launch_typed<R, In, 3, false, false>(p, cfg, t, ws, Ro, To, red, st);
+    case 7: return wt ? launch_typed<R, In, 7, true, false>(p, cfg, t, ws, Ro, To, red, st) : launch_typed<R, In, 7, false, false>(p, cfg, t, ws, Ro, To, red, st);
     default: return TMM_ERR_INVALID_ARG;
     }
 }
@@ -761,8 +1041,11 @@ tmm_status launch_forward(const tmm_problem *p, const tmm_launch_cfg *cfg, void 
         if (ws_bytes < persistent_ws_layout(p).total) return TMM_ERR_NOMEM;
         if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return TMM_ERR_INVALID_ARG;
     }
-    return p->prec == TMM_F64 ? launch_prec<double>(p, cfg, t, ws, R, T, Reduce<double>{nullptr, nullptr, 0}, st)
-                              : launch_prec<float>(p, cfg, t, ws, R, T, Reduce<float>{nullptr, nullptr, 0}, st);
+    if (p->prec == TMM_F64)
+        return launch_prec<double, double>(p, cfg, t, ws, R, T, Reduce<double>{nullptr, nullptr, 0}, st);
+    if (p->prec == TMM_F32D)
+        return launch_prec<float, double>(p, cfg, t, ws, R, T, Reduce<float>{nullptr, nullptr, 0}, st);
+    return launch_prec<float, float>(p, cfg, t, ws, R, T, Reduce<float>{nullptr, nullptr, 0}, st);
 }
 
 // ---------------------------------------------------------------- reward
@@ -805,13 +1088,13 @@ tmm_status launch_reward(const tmm_problem *p, const tmm_launch_cfg *cfg, const 
     unsigned char *base = static_cast<unsigned char *>(ws);
     const int n_tiles = t.n_lt * t.n_tt;
     if (p->prec == TMM_F64) {
-        s = launch_prec<double>(p, cfg, t, base + part, nullptr, nullptr,
+        s = launch_prec<double, double>(p, cfg, t, base + part, nullptr, nullptr,
                                 Reduce<double>{static_cast<const double *>(R_target), reinterpret_cast<double *>(base), n_tiles}, st);
         if (s != TMM_OK) return s;
         reward_finalize<double><<<(p->S + 255) / 256, 256, 0, st>>>(p->S, n_tiles, reinterpret_cast<const double *>(base),
                                                                    static_cast<double *>(reward));
     } else {
-        s = launch_prec<float>(p, cfg, t, base + part, nullptr, nullptr,
+        s = launch_prec<float, float>(p, cfg, t, base + part, nullptr, nullptr,
                                Reduce<float>{static_cast<const float *>(R_target), reinterpret_cast<float *>(base), n_tiles}, st);
         if (s != TMM_OK) return s;
         reward_finalize<float><<<(p->S + 255) / 256, 256, 0, st>>>(p->S, n_tiles, reinterpret_cast<const float *>(base),

@@ -47,40 +47,6 @@ struct __align__(16) DStage {
     float dlh, dll, ain2h, ain2l;
 };
 
-__device__ __forceinline__ dd dconst(double v)
-{
-    const float h = (float)v;
-    return dd{h, (float)(v - (double)h)};
-}
-
-constexpr double kPi = 3.14159265358979323846264338327950288;
-
-__device__ __forceinline__ void sincos_turn_dd(dd f, const float4 *tab, dd *s, dd *c)
-{
-    const float jf = rintf(__fmul_rn(f.hi, 256.0f));
-    const int j = (int)jf;
-    const dd r = df::add_f(f, -__fmul_rn(jf, 1.0f / 256.0f));
-    const dd x = df::mul(r, dconst(2.0 * kPi));
-    const dd x2 = df::sqr(x);
-    // sin x = x (1 - x^2/6 + x^4/120), cos x = 1 - x^2/2 + (x^4/24 - x^6/720)
-    const dd t = df::mul(x2, dconst(1.0 / 6.0));
-    const float x4 = __fmul_rn(x2.hi, x2.hi);
-    const dd p = df::add_f(df::sub(df::make(1.0f), t), __fmul_rn(x4, 1.0f / 120.0f));
-    const dd sx = df::mul(x, p);
-    const float h4 = __fsub_rn(__fmul_rn(x4, 1.0f / 24.0f), __fmul_rn(__fmul_rn(x4, x2.hi), 1.0f / 720.0f));
-    const dd cx = df::add_f(df::sub(df::make(1.0f), df::scale2(x2, 0.5f)), h4);
-    const int jj = j & 255, quad = jj >> 6, k = jj & 63;
-    const float4 e = tab[k];
-    const dd sk{e.x, e.y}, ck{e.z, e.w};
-    dd sj, cj;
-    if (quad == 0) { sj = sk; cj = ck; }
-    else if (quad == 1) { sj = ck; cj = df::neg(sk); }
-    else if (quad == 2) { sj = df::neg(sk); cj = df::neg(ck); }
-    else { sj = df::neg(ck); cj = sk; }
-    *s = df::dot2(sj, cx, cj, sx, 1.0f);
-    *c = df::dot2(cj, cx, sj, sx, -1.0f);
-}
-
 // 2^v as m * 2^n with m a dd in [2^-0.5, 2^0.5]
 __device__ __forceinline__ dd exp2_dd(dd v, const float2 *tab, int *n_out)
 {
@@ -570,12 +536,8 @@ const DfTables &host_tables()
     static DfTables t;
     static std::once_flag once;
     std::call_once(once, [] {
-        for (int k = 0; k < 64; ++k) {
-            const double a = 2.0 * kPi * k / 256.0;
-            const double sv = std::sin(a), cv = std::cos(a);
-            const float sh = (float)sv, ch = (float)cv;
-            t.sc[k] = make_float4(sh, (float)(sv - sh), ch, (float)(cv - ch));
-        }
+        const SinCosTable &sc = sincos_table();
+        for (int k = 0; k < 64; ++k) t.sc[k] = sc.sc[k];
         for (int i = -32; i <= 32; ++i) {
             const double v = std::exp2(i / 64.0);
             const float h = (float)v;

@@ -494,7 +494,7 @@ extern "C" TMM_API tmm_status tmm_inc_batched(const tmm_problem *p, const uint8_
     TraceRange trace("tmm_inc_batched");
     tmm_status s = validate_problem(p);
     if (s != TMM_OK) return s;
-    if (p->prec == TMM_F64X) return TMM_ERR_UNSUPPORTED;
+    if (p->prec != TMM_F64 && p->prec != TMM_F32) return TMM_ERR_UNSUPPORTED;
     const long long pts = (long long)p->S * p->n_lambda * p->n_theta;
     if (pts == 0) return TMM_OK;
     if (!R) return TMM_ERR_INVALID_ARG;

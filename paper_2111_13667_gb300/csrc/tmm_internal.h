@@ -49,6 +49,7 @@ constexpr size_t kSmemBlockCeiling = 227 * 1024;
 tmm_status ensure_dynamic_smem(const void *fn, size_t bytes);
 
 int npol(uint32_t pol_mask);
+// Bytes of the working real type of the outputs (float for TMM_F32 and TMM_F32D).
 size_t real_size(int prec);
 
 // Host-side validation of a problem (sizes, pointers, modes).
@@ -70,6 +71,10 @@ tmm_status reward_layout(const tmm_problem *p, const tmm_launch_cfg *cfg, Tile *
                          size_t *total);
 tmm_status launch_reward(const tmm_problem *p, const tmm_launch_cfg *cfg, const void *R_target, void *reward,
                          void *ws, size_t ws_bytes, cudaStream_t st);
+// {sin, cos} of 2 pi k / 256 as float pairs (host-built, passed to kernels by value).
+struct SinCosTable;
+const SinCosTable &sincos_table();
+
 tmm_status launch_forward_df64(const tmm_problem *p, const tmm_launch_cfg *cfg, void *R, void *T, cudaStream_t st);
 
 // Adjoint / merit.

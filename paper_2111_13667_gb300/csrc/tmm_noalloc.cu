@@ -23,6 +23,9 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratch
 
 // Device address of g_noalloc_scratch for the current device, looked up once
 // per device (host code cannot use the symbol itself as a device pointer).
+// The cached address belongs to the device's primary context: after
+// cudaDeviceReset the module is loaded anew and the address may change, so
+// the entry point must not be used after a reset of a device it ran on.
 static tmm_status noalloc_scratch(void **out)
 {
     static std::mutex mu;
@@ -49,9 +52,11 @@ using namespace tmm;
 extern "C" TMM_API tmm_status tmm_coh_batched_noalloc(const tmm_problem *p, const tmm_launch_cfg *cfg, void *R,
                                                       void *T, void *stream)
 {
+    TraceRange trace("tmm_coh_batched_noalloc");
     tmm_status s = validate_problem(p);
     if (s != TMM_OK) return s;
     if ((long long)p->S * p->n_lambda * p->n_theta == 0) return TMM_OK;
+    if (p->prec == TMM_F64X) return TMM_ERR_UNSUPPORTED;  // the double-float kernel has no persistent form
     if (!R) return TMM_ERR_INVALID_ARG;
     tmm_launch_cfg c = cfg ? *cfg : tmm_launch_cfg{};
     if (c.tile_lambda < 0 || c.tile_theta < 0 || c.blocks_per_sm < 0 || c.max_items_per_block != 0)

@@ -84,7 +84,7 @@ extern "C" TMM_API tmm_status tmm_optimize_workspace_size(const tmm_problem *p, 
     if (!bytes) return TMM_ERR_INVALID_ARG;
     tmm_status s = validate_problem(p);
     if (s != TMM_OK) return s;
-    if (p->prec == TMM_F64X || (p->pol_mask & TMM_POL_AVG)) return TMM_ERR_UNSUPPORTED;
+    if ((p->prec != TMM_F64 && p->prec != TMM_F32) || (p->pol_mask & TMM_POL_AVG)) return TMM_ERR_UNSUPPORTED;
     *bytes = p->S == 0 ? 0 : opt_layout(p).total;
     return TMM_OK;
 }
@@ -96,7 +96,7 @@ extern "C" TMM_API tmm_status tmm_optimize_adam(const tmm_problem *p, const void
     TraceRange trace("tmm_optimize_adam");
     tmm_status s = validate_problem(p);
     if (s != TMM_OK) return s;
-    if (p->prec == TMM_F64X || (p->pol_mask & TMM_POL_AVG)) return TMM_ERR_UNSUPPORTED;
+    if ((p->prec != TMM_F64 && p->prec != TMM_F32) || (p->pol_mask & TMM_POL_AVG)) return TMM_ERR_UNSUPPORTED;
     if (!cfg || steps < 0 || cfg->step0 < 0) return TMM_ERR_INVALID_ARG;
     if (!(cfg->lr > 0.0) || !(cfg->beta1 >= 0.0 && cfg->beta1 < 1.0) || !(cfg->beta2 >= 0.0 && cfg->beta2 < 1.0) ||
         !(cfg->eps > 0.0) || !(cfg->d_min <= cfg->d_max))

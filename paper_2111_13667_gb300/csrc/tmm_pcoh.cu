@@ -674,7 +674,7 @@ extern "C" TMM_API tmm_status tmm_pcoh_batched(const tmm_problem *p, const int32
     TraceRange trace("tmm_pcoh_batched");
     tmm_status s = validate_problem(p);
     if (s != TMM_OK) return s;
-    if (p->prec == TMM_F64X) return TMM_ERR_UNSUPPORTED;
+    if (p->prec != TMM_F64 && p->prec != TMM_F32) return TMM_ERR_UNSUPPORTED;
     if (n_nodes < 1 || n_nodes > kPcMaxNodes) return TMM_ERR_INVALID_ARG;
     const long long pts = (long long)p->S * p->n_lambda * p->n_theta;
     if (pts == 0) return TMM_OK;

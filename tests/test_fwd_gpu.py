@@ -1,7 +1,10 @@
 """GPU parity of the forward path (tmm_coh_batched) against the FP64 oracle.
 
-Tolerances: FP64 path within 1e-10 absolute in R and T, FP32 path within
-1e-4 absolute, element by element on the same seeded inputs.
+Tolerances: FP64 paths (f64, f64x) within 1e-10 absolute in R and T, FP32
+paths within 1e-4 absolute, element by element on the same seeded inputs.
+"f32" takes its inputs as float (rounded from the seeded doubles), "f32d" as
+double; both compute in FP32 and are held to 1e-4 against the oracle on the
+double inputs.
 """
 from dataclasses import replace
 
@@ -15,7 +18,8 @@ from tests.helpers import oracle_index, oracle_RT
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"f64": 1e-10, "f32": 1e-4, "f64x": 1e-10}
+TOL = {"f64": 1e-10, "f32": 1e-4, "f64x": 1e-10, "f32d": 1e-4}
+ALL = ["f64", "f32", "f64x", "f32d"]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -39,7 +43,7 @@ def assert_close(got, ref, tol, what=""):
     assert err <= tol, f"{what}: max |err| = {err:.3e} > {tol:.0e}"
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32", "f64x"])
+@pytest.mark.parametrize("prec", ALL)
 def test_plain_fp64_workload_full(prec):
     w = W.plain_fp64()
     Ro, To = oracle_RT(w)
@@ -48,7 +52,7 @@ def test_plain_fp64_workload_full(prec):
     assert_close(T, To, TOL[prec], "T")
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32", "f64x"])
+@pytest.mark.parametrize("prec", ALL)
 def test_dispersive_small_ragged_tail(prec):
     # several lambda / theta tiles with a partial last tile, gathered index
     w = W.dispersive(seed=11, S=37, L=24, n_lambda=203, n_theta=13)
@@ -58,7 +62,7 @@ def test_dispersive_small_ragged_tail(prec):
     assert_close(T, To, TOL[prec], "T")
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32", "f64x"])
+@pytest.mark.parametrize("prec", ALL)
 def test_direct_per_lambda_index(prec):
     w = W.dispersive(seed=12, S=9, L=10, n_lambda=40, n_theta=5)
     w.n_direct = oracle_index(w)  # same indices given directly, [S][L+2][N_lambda]
@@ -69,7 +73,7 @@ def test_direct_per_lambda_index(prec):
     assert_close(T, To, TOL[prec], "T")
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32", "f64x"])
+@pytest.mark.parametrize("prec", ALL)
 @pytest.mark.parametrize("pols", ["s", "p"])
 def test_single_polarisation_and_R_only(prec, pols):
     w = W.plain_fp64(seed=13, S=5, L=7)
@@ -78,7 +82,7 @@ def test_single_polarisation_and_R_only(prec, pols):
     assert_close(R, Ro, TOL[prec], "R")
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32", "f64x"])
+@pytest.mark.parametrize("prec", ALL)
 def test_unpolarised_average_mode(prec):
     # pol_mask 7: one plane of (R_s + R_p) / 2 and (T_s + T_p) / 2, as the paper
     # averages s and p for unpolarised light
@@ -91,12 +95,12 @@ def test_unpolarised_average_mode(prec):
     # the same as averaging the two planes of the s+p launch, to rounding of a
     # separately compiled kernel
     Rsp, Tsp = gpu_RT(w, prec)
-    same = 1e-12 if prec != "f32" else 2e-6
+    same = 1e-12 if prec in ("f64", "f64x") else 2e-6
     assert_close(R[0], 0.5 * (Rsp[0] + Rsp[1]), same, "R vs s+p launch")
     assert_close(T[0], 0.5 * (Tsp[0] + Tsp[1]), same, "T vs s+p launch")
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32", "f64x"])
+@pytest.mark.parametrize("prec", ALL)
 def test_total_internal_reflection_and_grazing(prec):
     # injection index 2 into air, interior indices up to 4.6, theta up to
     # exactly 90 deg (the paper's reflectivity-map shape)
@@ -115,70 +119,35 @@ def test_total_internal_reflection_and_grazing(prec):
     assert (~below).sum() > 100  # the map reaches far into total internal reflection
 
 
-def rounded_to_f32(w):
-    """The workload with every input rounded to FP32 (what the FP32 path is given)."""
-    r = lambda a: a.astype(np.float32).astype(np.float64)
-    nd = None if w.n_direct is None else r(w.n_direct.real) + 1j * r(w.n_direct.imag)
-    return replace(w, d=r(w.d), theta=r(w.theta), lam=r(w.lam), n_direct=nd)
-
-
-def assert_f32_conditioned(w, R, T, Ro, To, what):
-    """The FP32 tolerance read per angle: 1e-4, or six times the movement of
-    the exact R, T when only the inputs are rounded to FP32, where that is
-    larger.  Returns the largest error per angle."""
-    Rr, Tr = oracle_RT(rounded_to_f32(w))
-    floor = np.maximum(np.abs(Rr - Ro), np.abs(Tr - To)).max(axis=(0, 1, 3))
-    err = np.maximum(np.abs(R - Ro), np.abs(T - To)).max(axis=(0, 1, 3))
-    bound = np.maximum(TOL["f32"], 6.0 * floor)
-    assert np.all(np.isfinite(R)) and np.all(np.isfinite(T)), what
-    assert np.all(err <= bound), (what, [(round(float(np.rad2deg(t)), 1), float(e), float(b))
-                                         for t, e, b in zip(w.theta, err, bound)])
-    return err
-
-
-@pytest.mark.parametrize("prec", ["f64", "f32", "f64x"])
-def test_timing_shape_to_grazing_and_input_conditioning(prec):
-    # Sec. 4 timing run: 19 layers of real index up to 5 between air, theta
-    # 0-90 deg.  The FP64 forms meet 1e-10 at every angle.  For FP32 the
-    # reading is per angle: 1e-4 wherever rounding the inputs alone to FP32
-    # moves the exact R, T by at most 1e-4 / 6, and otherwise at most six times
-    # that movement -- each layer's phase takes about six roundings (n^2 - n0^2,
-    # + (n0 cos)^2, sqrt, d / lambda, the product, sin/cos) of the size of one
-    # input rounding.  Near grazing incidence this stack amplifies them: at
-    # 85.3 deg input rounding alone moves R by 4.4e-5.
+@pytest.mark.parametrize("prec", ALL)
+def test_timing_shape_to_grazing(prec):
+    # Sec. 4 timing run: 19 layers of real index 1.2-5 between air, theta
+    # 0-90 deg.  Near grazing incidence (85.3 deg) this resonant stack turns a
+    # phase error of 1e-6 rad per layer into 1e-4 in R: the FP32 kernels hold
+    # the plain tolerance because the large, angle-independent part of every
+    # layer phase is staged in double-float arithmetic.
     w = W.speedup_x1()
     Ro, To = oracle_RT(w)
     R, T = gpu_RT(w, prec)
-    if prec != "f32":
-        assert_close(R, Ro, TOL[prec], "R")
-        assert_close(T, To, TOL[prec], "T")
-        return
-    err = assert_f32_conditioned(w, R, T, Ro, To, "timing shape")
-    # the plain FP32 tolerance holds at every angle up to 81 deg; only the most
-    # grazing finite angle (85.3 deg) needs the relaxed bound
-    below = np.rad2deg(w.theta) <= 81.0
-    assert below.sum() == 18 and np.all(err[below] <= TOL["f32"]), err[below].max()
+    assert_close(R, Ro, TOL[prec], "R")
+    assert_close(T, To, TOL[prec], "T")
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32", "f64x"])
+@pytest.mark.parametrize("prec", ALL)
 def test_alternating_shared_memory_sizes(prec):
     # One kernel launched for a deeper, a shallower and again the deeper stack;
     # all three stage more than the 48 KiB default of shared memory, so the
     # limit granted for the first launch must still hold for the third.  These
-    # stacks reflect up to 0.9996, where FP32 meets the per-angle reading of
-    # its tolerance rather than 1e-4 at every angle.
+    # stacks (71 and 97 layers of index 1.3-2.5) reflect up to 0.9996.
     for L in (97, 71, 97):
         w = W.plain_fp64(seed=40 + L, S=3, L=L)
         Ro, To = oracle_RT(w)
         R, T = gpu_RT(w, prec)
-        if prec == "f32":
-            assert_f32_conditioned(w, R, T, Ro, To, f"L={L}")
-        else:
-            assert_close(R, Ro, TOL[prec], f"R L={L}")
-            assert_close(T, To, TOL[prec], f"T L={L}")
+        assert_close(R, Ro, TOL[prec], f"R L={L}")
+        assert_close(T, To, TOL[prec], f"T L={L}")
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32", "f64x"])
+@pytest.mark.parametrize("prec", ALL)
 def test_single_interface_and_opaque_layers(prec):
     lam = np.linspace(400, 800, 33)
     th = np.deg2rad(np.linspace(0, 70, 6))
@@ -197,7 +166,8 @@ def test_single_interface_and_opaque_layers(prec):
         assert_close(T, To, TOL[prec], f"T {media[:3]}")
 
 
-@pytest.mark.parametrize("prec,persistent", [("f64", 0), ("f64", 1), ("f32", 0), ("f32", 1), ("f64x", 0)])
+@pytest.mark.parametrize("prec,persistent", [("f64", 0), ("f64", 1), ("f32", 0), ("f32", 1), ("f64x", 0),
+                                             ("f32d", 0), ("f32d", 1)])
 def test_ragged_layer_counts(prec, persistent):
     w = W.ragged(seed=14, S=301, L_max=60, n_lambda=45, n_theta=7)
     Ro, To = oracle_RT(w)
@@ -262,10 +232,33 @@ def test_workspace_checks():
     assert e.value.status == abi.TMM_ERR_NOMEM
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32", "f64x"])
+def max_abs_diff(a, b, chunk=1 << 26):
+    """max |a - b| over two equally shaped device tensors, in FP64, chunk by chunk."""
+    a, b = a.reshape(-1), b.reshape(-1)
+    m = 0.0
+    for i in range(0, a.numel(), chunk):
+        m = max(m, float((a[i:i + chunk].double() - b[i:i + chunk].double()).abs().max()))
+    return m
+
+
+_full_f64x = {}
+
+
+def full_dispersive_f64x():
+    """The full dispersive workload in double-float (held to 1e-10 on its
+    oracle samples), the reference for whole-tensor checks of the FP32 paths."""
+    if not _full_f64x:
+        R, T = abi.coh_tmm(abi.to_device(W.dispersive(), "f64x"))
+        _full_f64x["RT"] = (R, T)
+    return _full_f64x["RT"]
+
+
+@pytest.mark.parametrize("prec", ALL)
 def test_dispersive_full_size_sampled(prec):
     """The full 16384 x 24 x 512 x 32 problem in the launch the benchmark
-    times; a seeded sample of stacks is checked against the oracle."""
+    times.  A seeded sample of stacks is checked against the oracle; the FP32
+    paths are also checked element by element on the whole output against
+    the double-float launch, which meets 1e-10 on its own oracle sample."""
     w = W.dispersive()
     prob = abi.to_device(w, prec)
     R, T = abi.coh_tmm(prob)
@@ -278,12 +271,19 @@ def test_dispersive_full_size_sampled(prec):
     Tg = T[:, it].double().cpu().numpy()
     assert_close(Rg, Ro, TOL[prec], "R")
     assert_close(Tg, To, TOL[prec], "T")
-    # properties that hold everywhere: finite, 0 <= R, T and R + T <= 1
-    Rall = R.double()
-    Tall = T.double()
-    assert bool(torch.isfinite(Rall).all()) and bool(torch.isfinite(Tall).all())
-    assert float(Rall.min()) >= -TOL[prec] and float(Tall.min()) >= -TOL[prec]
-    assert float((Rall + Tall).max()) <= 1 + TOL[prec]
+    assert bool(torch.isfinite(R).all()) and bool(torch.isfinite(T).all())
+    if prec in ("f32", "f32d"):
+        Rx, Tx = full_dispersive_f64x()
+        eR, eT = max_abs_diff(R, Rx), max_abs_diff(T, Tx)
+        assert eR <= TOL[prec] and eT <= TOL[prec], (eR, eT)
+    else:
+        # properties that hold everywhere: 0 <= R, T and R + T <= 1
+        assert float(R.min()) >= -TOL[prec] and float(T.min()) >= -TOL[prec]
+        assert float((R + T).max()) <= 1 + TOL[prec]
+    del R, T
+    if prec == "f32d":
+        _full_f64x.clear()
+        torch.cuda.empty_cache()
 
 
 def test_empty_batch():

@@ -76,7 +76,14 @@ def test_full_size_ragged_sampled():
     assert np.max(np.abs(np_(R[:, it]) - Ro)) <= TOL["f32"]
     assert np.max(np.abs(np_(T[:, it]) - To)) <= TOL["f32"]
     assert bool(torch.isfinite(R).all()) and bool(torch.isfinite(T).all())
-    # padded launch of the same arrays agrees everywhere
+    # every element against the double-float launch of the same ragged problem
+    # (held to 1e-10 on its own oracle samples), then the padded FP32 launch
+    R64, T64 = abi.coh_tmm(abi.to_device(w, "f64x"))
+    assert float((R.double() - R64).abs().max()) <= TOL["f32"]
+    assert float((T.double() - T64).abs().max()) <= TOL["f32"]
+    R64s, T64s = R64[:, it].cpu().numpy(), T64[:, it].cpu().numpy()
+    assert np.max(np.abs(R64s - Ro)) <= 1e-10 and np.max(np.abs(T64s - To)) <= 1e-10
+    del R64, T64
     padded = abi.DeviceProblem(prob.prec, prob.pol_mask, prob.theta, prob.lam, prob.d, table=prob.table,
                                mat_idx=prob.mat_idx)
     Rp, Tp = abi.coh_tmm(padded)
