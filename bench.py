@@ -5,8 +5,10 @@ One step = one call of tmm_coh_batched over the whole dispersive workload
 (16384 stacks x 24 layers, 8 Cauchy materials, 512 lambda in 300-1200 nm x
 32 theta in 0-85 deg, s and p, R and T), inputs resident in HBM.  The metric is
 evaluations per second, one evaluation being one (stack, lambda, theta, pol)
-R, T pair.  The headline runs in FP32; the FP64 path is measured the same way
-and reported beside it.
+R, T pair.  The headline is the FP64-accurate path at the paper's precision
+(complex128): double-float arithmetic (TMM_F64X, FP64 inputs and outputs,
+held to 1e-10 against the FP64 oracle).  FP32 (float and double inputs) and
+native FP64 are measured the same way and reported beside it.
 
 Prints ONE JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
 oracle instead, on a bounded sample of the same workload.
@@ -37,32 +39,34 @@ FLUSH_BYTES = 512 * 1024 * 1024
 # shared) and the vector update (6 complex products + 2 adds): 88 per layer,
 # about 2.2 kflop per eval over the 25 interfaces of the dispersive workload.
 FLOPS_PER_EVAL_INTERFACE = 88.0
-# What the kernels execute per (eval, interface) with unnormalised interfaces
-# (no complex division), both polarisations sharing root and phase.  FP32
-# (two angles per thread on paired lanes): shared 21 (n^2 - beta^2, root,
-# phase arguments and factors, |q|^2 product, two sign flips), s 39 (a sign
-# flip, interface 24, phase 12, rescaling 2), p 45.5 (q / n^2 6, the p index
-# product 0.5, the rest as s) -> 105.5 / 2 pols.  FP64 and double-float (one
-# point per thread, tolerance-band root): shared 21, s 44, p 51 -> 116 / 2.
-EXECUTED_FLOPS_PER_EVAL_INTERFACE = {"f32": 52.75, "f64": 58.0, "f64x": 58.0}
 # Unit-count peaks (152 SMs, max SM clock 2070 MHz): FP32 128 FMA lanes / SM;
 # FP64 from the nominal 1.25 TFLOP/s of the part.
 SMS = 152
 MAX_SM_MHZ = 2070.0
 PEAK_F32_FLOPS = SMS * 128 * 2 * MAX_SM_MHZ * 1e6
 PEAK_F64_FLOPS = 1.25e12
-DOMINANT_KERNEL_SOURCES = ["paper_2111_13667_gb300/csrc/tmm_fwd.cu", "paper_2111_13667_gb300/csrc/tmm_device.cuh"]
+_CSRC = "paper_2111_13667_gb300/csrc/"
+KERNEL_SOURCES = {
+    "fwd": [_CSRC + "tmm_fwd.cu", _CSRC + "tmm_device.cuh", _CSRC + "tmm_df64.cuh"],
+    "df64": [_CSRC + "tmm_fwd_df64.cu", _CSRC + "tmm_device.cuh", _CSRC + "tmm_df64.cuh", _CSRC + "tmm_df64x2.cuh"],
+}
+KERNELS = {
+    "f32": ("tmm_fwd_kernel<float,float,3,true,false,true>", "fwd"),
+    "f32d": ("tmm_fwd_kernel<float,double,3,true,false,true>", "fwd"),
+    "f64": ("tmm_fwd_kernel<double,double,3,true,false,false>", "fwd"),
+    "f64x": ("tmm_fwd_df64_kernel<3,true,true>", "df64"),
+}
 
 
-def kernel_hash():
+def kernel_hash(group="fwd"):
     h = hashlib.sha256()
-    for f in DOMINANT_KERNEL_SOURCES:
+    for f in KERNEL_SOURCES[group]:
         with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def stored_profile(kernel_key, field):
+def stored_profile(kernel_key, field, group="fwd"):
     """A figure of the committed ncu summary (profiles/traffic.json), if it
     still describes the current kernel source (else None)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
@@ -71,14 +75,14 @@ def stored_profile(kernel_key, field):
     with open(p) as fh:
         data = json.load(fh)
     ent = data.get(kernel_key)
-    if not ent or ent.get("source_hash") != kernel_hash():
+    if not ent or ent.get("source_hash") != kernel_hash(group):
         return None
     return ent.get(field)
 
 
-def stored_traffic(kernel_key):
+def stored_traffic(kernel_key, group="fwd"):
     """DRAM bytes per launch from the committed ncu summary (or None)."""
-    return stored_profile(kernel_key, "dram_bytes_per_launch")
+    return stored_profile(kernel_key, "dram_bytes_per_launch", group)
 
 
 def measured_peaks():
@@ -169,6 +173,47 @@ def time_steps(fn, steps, warmup, torch, flush):
     return [a.elapsed_time(b) for a, b in evs]
 
 
+def roofline(prec, evals, interfaces, ms, abi):
+    """Roofline object of one precision's forward kernel on this launch.
+
+    f32, f32d, f64: the standard algorithmic count (FLOPS_PER_EVAL_INTERFACE
+    per eval and interface) against the FP32 / FP64 unit-count peak.
+    f64x: double-float arithmetic runs on the FP32 pipes, so its FP32 flops as
+    executed (ncu counts of FADD, FMUL, FFMA and their paired forms, per eval
+    and interface, from profiles/traffic.json) against the FP32 peak; null
+    while the committed counts do not describe the current source."""
+    key, group = KERNELS[prec]
+    peak = PEAK_F64_FLOPS if prec == "f64" else PEAK_F32_FLOPS
+    work = FLOPS_PER_EVAL_INTERFACE * interfaces * evals
+    r = {"bound": "alu", "unit": "TFLOP/s", "peak": peak / 1e12, "kernel": key,
+         "traffic": stored_traffic(key, group), "issue_frac": stored_profile(key, "issue_active_frac", group),
+         "fma_pipe_frac": stored_profile(key, "fma_pipe_active_frac", group),
+         "peak_source": ("unit count: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz" if prec != "f64"
+                         else "nominal FP64 1.25 TFLOP/s of the part")}
+    if prec == "f64x":
+        ex = stored_profile(key, "executed_fp32_flops_per_eval_interface", group)
+        r["work"] = ("FP32 flops executed by the double-float kernel (ncu: fadd + fmul + 2 ffma + 2 fadd2 + "
+                     "2 fmul2 + 4 ffma2 thread instructions) per eval-interface x interfaces x evals")
+        r["executed_fp32_flops_per_eval_interface"] = ex
+        r["achieved"] = None if ex is None else ex * interfaces * evals / (ms * 1e-3) / 1e12
+        r["frac"] = None if ex is None else r["achieved"] / r["peak"]
+        r["fp64_equivalent_TFLOPs"] = work / (ms * 1e-3) / 1e12
+    else:
+        r["work"] = (f"{FLOPS_PER_EVAL_INTERFACE:g} flop per eval-interface x {interfaces} interfaces x {evals} "
+                     f"evals (standard count of the vector-sweep method)")
+        r["achieved"] = work / (ms * 1e-3) / 1e12
+        r["frac"] = r["achieved"] / r["peak"]
+        ex = stored_profile(key, "executed_fp32_flops_per_eval_interface", group)
+        if ex is not None:
+            r["executed_frac"] = ex * interfaces * evals / (ms * 1e-3) / peak
+    try:
+        f, _ = abi.tmm_probe_fma_rate(abi.TMM_F64 if prec == "f64" else abi.TMM_F32)
+        r["probe_peak"] = f / 1e12
+    except Exception as e:  # the probe is optional context
+        r["probe_peak"] = f"probe failed: {e}"
+    return r
+
+
 def gpu_arm(args):
     import torch
     import torch.distributed as dist
@@ -198,16 +243,17 @@ def gpu_arm(args):
     def max_over_ranks(v):
         return D.max_over_ranks(v, dev)
 
-    for prec, steps, warmup in (("f32", args.steps, args.warmup), ("f64", args.f64_steps, 3),
-                                ("f64x", max(3, args.f64_steps), 3)):
-        if prec != "f32" and args.skip_f64:
+    runs = [("f64x", args.steps, args.warmup), ("f32", args.steps, args.warmup),
+            ("f32d", max(3, args.steps // 2), 3), ("f64", args.f64_steps, 3)]
+    for prec, steps, warmup in runs:
+        if prec in ("f64", "f32d") and args.skip_f64:
             continue
         prob = abi.to_device(w, prec, device=dev)
         R = prob.empty_out()
         T = prob.empty_out()
         step = lambda: abi.tmm_coh_batched(prob, R, T)
         barrier()
-        sampler = ClockSampler(local) if prec == "f32" else None
+        sampler = ClockSampler(local) if prec in ("f64x", "f32") else None
         wall0 = time.perf_counter()
         if sampler:
             sampler.__enter__()
@@ -219,36 +265,17 @@ def gpu_arm(args):
         barrier()
         wall = time.perf_counter() - wall0
         ms = max_over_ranks(sum(times) / len(times))
-        value = evals * world / (ms * 1e-3)
-        flops = FLOPS_PER_EVAL_INTERFACE * interfaces * evals
-        achieved = flops / (ms * 1e-3)
-        peak = PEAK_F32_FLOPS if prec == "f32" else PEAK_F64_FLOPS
-        key = {"f32": "tmm_fwd_kernel<float,3,true,false,true>", "f64": "tmm_fwd_kernel<double,3,true,false,false>",
-               "f64x": "tmm_fwd_df64_kernel<3,true>"}[prec]
-        entry = {"value": value, "ms_per_step": ms, "steps": steps, "warmup": warmup, "wall_s": wall,
-                 "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
-                              "unit": "TFLOP/s", "frac": achieved / peak, "traffic": stored_traffic(key),
-                              "issue_frac": stored_profile(key, "issue_active_frac"),
-                              "kernel": key,
-                              "work": f"{FLOPS_PER_EVAL_INTERFACE:g} flop per eval-interface x {interfaces} "
-                                      f"interfaces x {evals} evals (standard count of the vector-sweep "
-                                      f"method)",
-                              "executed_frac": achieved / peak * EXECUTED_FLOPS_PER_EVAL_INTERFACE[prec]
-                              / FLOPS_PER_EVAL_INTERFACE}}
-        try:
-            f, pms = abi.tmm_probe_fma_rate(abi.TMM_F64 if prec == "f64" else abi.TMM_F32)
-            entry["roofline"]["probe_peak"] = f / 1e12
-        except Exception as e:  # the probe is optional context
-            entry["roofline"]["probe_peak"] = f"probe failed: {e}"
-        if prec == "f64x":
-            entry["roofline"]["note"] = ("double-float arithmetic on the FP32 pipes; achieved counts the same "
-                                         "algorithmic flops as the FP64 path, peak is the FP64 peak it replaces, "
-                                         "probe_peak the FP32 FMA probe")
-            entry["dtype"] = "f32x2 (double-float), f64 inputs and outputs"
+        entry = {"value": evals * world / (ms * 1e-3), "ms_per_step": ms, "steps": steps, "warmup": warmup,
+                 "wall_s": wall, "roofline": roofline(prec, evals, interfaces, ms, abi)}
+        entry["dtype"] = {"f64x": "f64x: double-float (float pairs, ~48 bits) on the FP32 pipes, f64 inputs and "
+                                  "outputs, held to 1e-10 against the FP64 oracle",
+                          "f32": "f32 arithmetic, f32 inputs and outputs, held to 1e-4",
+                          "f32d": "f32 arithmetic, f64 inputs, f32 outputs, held to 1e-4",
+                          "f64": "native f64 arithmetic"}[prec]
         if sampler:
             entry["clocks"] = sampler.summary()
         # end to end through the C ABI from pinned host buffers
-        if not args.skip_e2e and (prec == "f32" or not args.skip_e2e_f64):
+        if not args.skip_e2e and prec in ("f64x", "f32"):
             from paper_2111_13667_gb300.pipeline import HostPipeline
             h_in = {k: getattr(prob, k).cpu().pin_memory() for k in ("theta", "lam", "d", "table", "mat_idx")}
             hR = torch.empty(R.shape, dtype=R.dtype).pin_memory()
@@ -267,6 +294,7 @@ def gpu_arm(args):
             d2h = (hR.numel() * hR.element_size()) * 2
             entry["e2e"] = {"value": evals * world / (ems * 1e-3), "unit": "evals/s", "ms_per_step": ems,
                             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": e_steps}
+            del pipe, hR, hT, h_in
         out[prec] = entry
         R = T = None
         del prob
@@ -291,21 +319,22 @@ def gpu_arm(args):
         if "surrogate" in sections and not args.skip_surrogate:
             out["surrogate"] = bench_surrogate(args, torch, abi, W, flush, world, max_over_ranks)
 
-    head = out["f32"]
+    head = out["f64x"]
     line = {
         "metric": "TMM evals/s (stack x lambda x theta x pol), dispersive 16384x24, 512 lambda x 32 theta, s+p",
         "value": head["value"], "unit": "evals/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded)",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64x", "dtype_note": head["dtype"],
+        "data": "synthetic (seeded)",
         "config": {"workload": w.name, "stacks_per_gpu": w.S, "layers": w.L_max, "n_lambda": w.n_lambda,
                    "n_theta": w.n_theta, "pols": "s+p", "outputs": "R,T",
                    "l2": f"flushed ({FLUSH_BYTES >> 20} MiB memset) before every timed step; "
-                         f"outputs {R_bytes(w, 4) >> 20} MiB per step also exceed L2",
+                         f"outputs {R_bytes(w, 8) >> 20} MiB per step also exceed L2",
                    "parallelism": f"replicas x{world} (independent stacks, no collective)"},
         "roofline": head["roofline"], "clocks": head.get("clocks"), "e2e": head.get("e2e"),
         "gpu_launches": args.steps,
     }
-    for k in ("f64", "f64x", "ragged", "adjoint", "optimize", "incoherent", "partial", "absorption", "paper_shapes",
+    for k in ("f32", "f32d", "f64", "ragged", "adjoint", "optimize", "incoherent", "partial", "absorption", "paper_shapes",
               "surrogate"):
         if k in out:
             line[k] = out[k]
@@ -584,7 +613,7 @@ def bench_paper_shapes(args, torch, abi, W, flush):
         if pols:
             ent["output"] = "one plane of (R_s + R_p) / 2 and (T_s + T_p) / 2 (pol_mask 7)"
         R64 = T64 = None
-        for prec in ("f64", "f64x", "f32"):
+        for prec in ("f64", "f64x", "f32", "f32d"):
             prob = abi.to_device(w, prec, pols=pols)
             R, T = prob.empty_out(), prob.empty_out()
             t = time_steps(lambda: abi.tmm_coh_batched(prob, R, T), 5, 3, torch, flush)

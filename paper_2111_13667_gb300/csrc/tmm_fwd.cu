@@ -278,15 +278,18 @@ __device__ __forceinline__ void run_item(const tmm_problem &p, int s, int lt, in
 }
 
 // ---------------------------------------------------------------- FP32 stage and layer phase
-// The FP32 kernels stage, per (medium j, wavelength):
-//   StageA  {n_j^2 - n_0^2, Im n_j^2, 1/n_j^2}, the first rounded once from
-//           double-float arithmetic on the inputs;
-//   StageP  {d_j / lambda, f_j, m_j} with m_j = +-n_j (below) and f_j the
-//           fraction of (d_j / lambda) Re m_j, from a double-float product;
-//   |1/n_j^2|^2;
+// The FP32 kernels stage, per (medium j, wavelength), 28 bytes:
+//   StageQ  {n_j^2 - n_0^2 (rounded once from double-float arithmetic on the
+//           inputs), d_j / lambda, f_j, Re m_j} with m_j = +-n_j (below) and
+//           f_j the fraction of (d_j / lambda) Re m_j from a double-float
+//           product;
+//   1 / n_j^2 (complex) and Im m_j;
 // per wavelength the injection index n_0 and per angle of the tile sin and
-// cos of theta, each as a float pair.  Inputs are float (TMM_F32) or double
-// (TMM_F32D, split into float pairs by integer operations).
+// cos of theta, each as a float pair.  Im n_j^2 = 2 Re m_j Im m_j and
+// |1/n_j^2|^2 are formed where they are used, which keeps a 120-layer stage
+// of 32 wavelengths within half of an SM's shared memory.  Inputs are float
+// (TMM_F32) or double (TMM_F32D, split into float pairs by integer
+// operations).
 //
 // Layer phase.  A float product (d/lambda) Re q carries the roundings of
 // d/lambda, of q and of the product on the whole phase -- several turns in a
@@ -304,41 +307,54 @@ __device__ __forceinline__ void run_item(const tmm_problem &p, int s, int lt, in
 // angle.  Where the wave in the layer is (nearly) evanescent, |Re q| < |Re m|/2,
 // the two terms would cancel, and the plain product (d/lambda) Re q, then
 // small, is used instead (exactly 0 for a lossless evanescent layer).
-struct __align__(16) StageP {
-    float dl, fr, mx, my;  // d/lambda, frac((d/lambda) Re m), m
+struct __align__(16) StageQ {
+    float d2x, dl, fr, mx;
 };
 
 // Shared-memory layout of an FP32 work item: byte offsets of its arrays.
 struct Stage32Layout {
-    size_t sp, ain2, n0, th, total;
+    size_t in2, my, n0, th, total;
 };
 __host__ __device__ __forceinline__ size_t align16(size_t v) { return (v + 15) / 16 * 16; }
 __host__ __device__ __forceinline__ Stage32Layout stage32_layout(int L_max, int TL, int TT)
 {
     const size_t m = (size_t)(L_max + 2) * TL;
     Stage32Layout g;
-    g.sp = m * sizeof(float4);
-    g.ain2 = 2 * m * sizeof(float4);
-    g.n0 = align16(g.ain2 + m * sizeof(float));
+    g.in2 = m * sizeof(float4);
+    g.my = g.in2 + m * sizeof(float2);
+    g.n0 = align16(g.my + m * sizeof(float));
     g.th = align16(g.n0 + (size_t)TL * sizeof(float2));
     g.total = g.th + (size_t)TT * sizeof(float4);
     return g;
 }
 
 struct Stage32 {
-    StageA<float> *sa;
-    StageP *sp;
-    float *ain2;
-    float2 *n0;  // (hi, lo); NaN if the injection medium is complex
-    float4 *th;  // {sin hi, sin lo, cos hi, cos lo} of the tile's angles
+    StageQ *q;
+    float2 *in2;  // 1 / n^2
+    float *my;    // Im m
+    float2 *n0;   // (hi, lo); NaN if the injection medium is complex
+    float4 *th;   // {sin hi, sin lo, cos hi, cos lo} of the tile's angles
 };
 
 __device__ __forceinline__ Stage32 stage32_at(unsigned char *smem, int L_max, int TL, int TT)
 {
     const Stage32Layout g = stage32_layout(L_max, TL, TT);
-    return Stage32{reinterpret_cast<StageA<float> *>(smem), reinterpret_cast<StageP *>(smem + g.sp),
-                   reinterpret_cast<float *>(smem + g.ain2), reinterpret_cast<float2 *>(smem + g.n0),
+    return Stage32{reinterpret_cast<StageQ *>(smem), reinterpret_cast<float2 *>(smem + g.in2),
+                   reinterpret_cast<float *>(smem + g.my), reinterpret_cast<float2 *>(smem + g.n0),
                    reinterpret_cast<float4 *>(smem + g.th)};
+}
+
+// One medium's staged data as the sweep uses it.
+struct Medium32 {
+    float d2x, n2y, dl, fr, mx, my;
+    Cx<float> in2;
+};
+__device__ __forceinline__ Medium32 medium_at(const Stage32 &g, int idx)
+{
+    const StageQ Q = g.q[idx];
+    const float2 i2 = g.in2[idx];
+    const float my = g.my[idx];
+    return Medium32{Q.d2x, 2.f * Q.mx * my, Q.dl, Q.fr, Q.mx, my, Cx<float>{i2.x, i2.y}};
 }
 
 template <typename In> __device__ __forceinline__ df::dd in_dd(In v);
@@ -350,7 +366,9 @@ template <> __device__ __forceinline__ df::dd in_dd<double>(double v)
 }
 
 // Fill the FP32 stage for media 0..L+1 of stack s, wavelengths l0..l0+TL-1 and
-// angles t0..t0+TT-1.
+// angles t0..t0+TT-1.  Only the phase reference needs more than float
+// precision: d/lambda as q1 + q2 (float quotient plus the exact remainder
+// divided once more) and its product with Re m by a two-product.
 template <typename In>
 __device__ __forceinline__ void fill_stage32(const tmm_problem &p, int s, int L, int l0, int TL, int t0, int TT,
                                              const float4 *tab, const Stage32 &g, int tid, int nthr)
@@ -364,34 +382,51 @@ __device__ __forceinline__ void fill_stage32(const tmm_problem &p, int s, int L,
         const Cx<In> n = index_of<In>(p, s, j, l);
         const In n0v = j == 0 ? n.x : index_of<In>(p, s, 0, l).x;
         const df::dd nx = in_dd<In>(n.x), ny = in_dd<In>(n.y), n0 = in_dd<In>(n0v);
-        // n^2 - n_0^2 = (n' - n_0)(n' + n_0) - n''^2
-        const df::dd d2 = df::sub(df::mul(df::sub(nx, n0), df::add(nx, n0)), df::sqr(ny));
-        const Cx<float> nf = {nx.hi, ny.hi};
-        // Im n^2 with +0 for a real index: the interior root then takes Re q >= 0
-        const Cx<float> n2 = {fmaf(nf.x, nf.x, -nf.y * nf.y), nf.y == 0.f ? 0.f : 2.f * nf.x * nf.y};
-        const float ia = 1.f / abs2(n2);
-        // m = +-n, the interior root of n^2 (Im m >= 0, Re m >= 0 if Im m = 0)
-        const bool flip = nf.y < 0.f || (nf.y == 0.f && nf.x < 0.f);
-        StageA<float> A;
-        A.d2x = d2.hi;
-        A.n2y = n2.y;
-        A.in2x = n2.x * ia;
-        A.in2y = -n2.y * ia;
-        StageP P;
-        P.dl = 0.f;
-        P.fr = 0.f;
-        if (j >= 1 && j <= L) {
-            const df::dd dl = df::div(in_dd<In>(d[(long long)s * p.L_max + (j - 1)]), in_dd<In>(lam[l]));
-            const df::dd ph = df::mul(dl, flip ? df::neg(nx) : nx);
-            const float k = rintf(ph.hi);
-            P.dl = dl.hi;
-            P.fr = __fadd_rn(__fsub_rn(ph.hi, k), ph.lo);
+        // n^2 - n_0^2 = (n' - n_0)(n' + n_0) - n''^2, rounded once: both factors
+        // and n''^2 as exact float pairs (TwoSum, two-product), then one
+        // rounding of the leading difference plus the collected low parts
+        df::dd a = df::two_sum(nx.hi, -n0.hi), b = df::two_sum(nx.hi, n0.hi);
+        float yl2 = 0.f;
+        if constexpr (std::is_same<In, double>::value) {
+            a.lo = __fadd_rn(a.lo, __fsub_rn(nx.lo, n0.lo));
+            b.lo = __fadd_rn(b.lo, __fadd_rn(nx.lo, n0.lo));
+            yl2 = __fmul_rn(2.f * ny.hi, ny.lo);
         }
-        P.mx = flip ? -nf.x : nf.x;
-        P.my = flip ? -nf.y : nf.y;
-        g.sa[idx] = A;
-        g.sp[idx] = P;
-        g.ain2[idx] = ia;
+        const df::dd pab = df::two_prod(a.hi, b.hi), y2 = df::two_prod(ny.hi, ny.hi);
+        const float lo = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, __fsub_rn(pab.lo, __fadd_rn(y2.lo, yl2))));
+        const float d2 = __fadd_rn(__fsub_rn(pab.hi, y2.hi), lo);
+        const Cx<float> nf = {nx.hi, ny.hi};
+        const Cx<float> n2 = {fmaf(nf.x, nf.x, -nf.y * nf.y), 2.f * nf.x * nf.y};
+        const float ia = 1.f / abs2(n2);
+        // m = +-n, the interior root of n^2 (Im m >= 0, Re m >= 0 if Im m = 0);
+        // Im m is stored as +0 for a real index, so that Im n^2 = 2 Re m Im m
+        // is +0 and the interior root takes Re q >= 0 there too
+        const bool flip = nf.y < 0.f || (nf.y == 0.f && nf.x < 0.f);
+        const float mh = flip ? -nx.hi : nx.hi, ml = flip ? -nx.lo : nx.lo;
+        StageQ Q;
+        Q.d2x = d2;
+        Q.dl = 0.f;
+        Q.fr = 0.f;
+        if (j >= 1 && j <= L) {
+            const df::dd dv = in_dd<In>(d[(long long)s * p.L_max + (j - 1)]), lv = in_dd<In>(lam[l]);
+            const float q1 = dv.hi / lv.hi;
+            float r = fmaf(-q1, lv.hi, dv.hi);  // exact remainder of the float quotient
+            if constexpr (std::is_same<In, double>::value) r += fmaf(-q1, lv.lo, dv.lo);
+            const float q2 = r / lv.hi;
+            // (q1 + q2) (mh + ml) = ph + e, ph = q1 mh rounded, e its error and the cross terms
+            const float ph = __fmul_rn(q1, mh);
+            float e = fmaf(q1, mh, -ph);
+            e = fmaf(q1, ml, e);
+            e = fmaf(q2, mh, e);
+            const float k = rintf(ph);
+            Q.dl = q1;
+            Q.fr = __fadd_rn(__fsub_rn(ph, k), e);
+        }
+        Q.mx = mh;
+        const float my = flip ? -nf.y : nf.y;
+        g.q[idx] = Q;
+        g.in2[idx] = make_float2(n2.x * ia, -n2.y * ia);
+        g.my[idx] = my == 0.f ? 0.f : my;
         if (j == 0) g.n0[tl] = (n.y == In(0)) ? make_float2(n0.hi, n0.lo) : make_float2(nan_w<float>(), 0.f);
     }
     const In *th = (const In *)p.theta;
@@ -402,6 +437,13 @@ __device__ __forceinline__ void fill_stage32(const tmm_problem &p, int s, int L,
         sincos_turn_dd(df::add_f(f, -rintf(f.hi)), tab, &sv, &cv);
         g.th[i] = make_float4(sv.hi, sv.lo, cv.hi, cv.lo);
     }
+}
+
+// The injection medium's 1 / n_0^2 in the StageA form finish_point takes.
+__device__ __forceinline__ StageA<float> in2_stage(const Stage32 &g, int tl)
+{
+    const float2 i2 = g.in2[tl];
+    return StageA<float>{0.f, 0.f, i2.x, i2.y};
 }
 
 // Per-angle terms of one point from the staged sin, cos (float pairs) and n_0:
@@ -425,7 +467,7 @@ __device__ __forceinline__ float rcp_approx(float x)
 }
 
 // Layer phase Re(delta) / (2 pi) reduced to [-1/2, 1/2] (see above).
-__device__ __forceinline__ float phase_turns(Cx<float> q, const StageP &P, float nb2)
+__device__ __forceinline__ float phase_turns(Cx<float> q, const Medium32 &P, float nb2)
 {
     const float sx = q.x + P.mx, sy = q.y + P.my;
     const float rs = rcp_approx(fmaf(sx, sx, sy * sy));
@@ -435,7 +477,7 @@ __device__ __forceinline__ float phase_turns(Cx<float> q, const StageP &P, float
 }
 
 // phase_turns for the two lanes of a thread (paired instructions).
-__device__ __forceinline__ float2 phase_turns2(Cx<float> qa, Cx<float> qb, const StageP &P, float2 nb2)
+__device__ __forceinline__ float2 phase_turns2(Cx<float> qa, Cx<float> qb, const Medium32 &P, float2 nb2)
 {
     const float2 qx = f2(qa.x, qb.x);
     const float2 sx = add2(qx, bc2(P.mx)), sy = add2(f2(qa.y, qb.y), bc2(P.my));
@@ -453,10 +495,9 @@ template <int POL>
 __device__ __forceinline__ void layer_step_f(const Stage32 &g, int TL, int tl, int j, float q0sq, float nb2,
                                              float yi_max, Sweep<float> &w)
 {
-    const StageA<float> A = g.sa[j * TL + tl];
-    const StageP P = g.sp[j * TL + tl];
+    const Medium32 P = medium_at(g, j * TL + tl);
     float absz;
-    const Cx<float> q = inner_root(Cx<float>{A.d2x + q0sq, A.n2y}, &absz);
+    const Cx<float> q = inner_root(Cx<float>{P.d2x + q0sq, P.n2y}, &absz);
     w.Ps *= absz;
     const float yi = fminf(P.dl * q.y, yi_max);
     w.Y += yi;
@@ -471,8 +512,8 @@ __device__ __forceinline__ void layer_step_f(const Stage32 &g, int TL, int tl, i
         w.s1 = cmul(epi, w.s1);
     }
     if (POL & 2) {
-        w.Pp *= g.ain2[j * TL + tl];
-        const Cx<float> gq = cmul(q, Cx<float>{A.in2x, A.in2y});
+        w.Pp *= abs2(P.in2);
+        const Cx<float> gq = cmul(q, P.in2);
         interface_pair(gq, w.g_nx, w.p0, w.p1);
         w.p0 = cmul(emi, w.p0);
         w.p1 = cmul(epi, w.p1);
@@ -487,15 +528,15 @@ __device__ __forceinline__ void eval_point_f(const Stage32 &g, int TL, int tl, i
 {
     constexpr int RN = RenormEvery<float>::value;
     const float yi_max = float(kImDeltaMax / kTwoPi);
-    const StageA<float> A = g.sa[(L + 1) * TL + tl];
+    const Medium32 A = medium_at(g, (L + 1) * TL + tl);
     float absz;
     Sweep<float> w;
     w.q_nx = forward_root(Cx<float>{A.d2x + an.q0sq, A.n2y}, &absz);
     const Cx<float> q_out = w.q_nx, n2_out = {A.d2x + n0 * n0, A.n2y};
-    w.g_nx = cmul(w.q_nx, Cx<float>{A.in2x, A.in2y});
+    w.g_nx = cmul(w.q_nx, A.in2);
     w.Ps = 1.f, w.Y = 0.f;
     int eP = 0;
-    w.Pp = (POL & 2) ? g.ain2[(L + 1) * TL + tl] : 1.f;
+    w.Pp = (POL & 2) ? abs2(A.in2) : 1.f;
     int ePp = 0;
     w.s0 = {1.f, 0.f}, w.s1 = {0.f, 0.f}, w.p0 = {1.f, 0.f}, w.p1 = {0.f, 0.f};
     int es = 0, ep = 0;
@@ -521,8 +562,8 @@ __device__ __forceinline__ void eval_point_f(const Stage32 &g, int TL, int tl, i
         if (POL & 2) renorm_pair(w.p0, w.p1, ep);
     }
     for (; j >= 1; --j) layer_step_f<POL>(g, TL, tl, j, an.q0sq, an.nb2, yi_max, w);
-    finish_point<float, POL>(g.sa[tl], q_out, n2_out, w.q_nx, w.g_nx, w.s0, w.s1, w.p0, w.p1, w.Ps, w.Y, w.Pp, eP,
-                             ePp, es, ep, L, n0, an.beta, an.c0, out);
+    finish_point<float, POL>(in2_stage(g, tl), q_out, n2_out, w.q_nx, w.g_nx, w.s0, w.s1, w.p0, w.p1, w.Ps, w.Y,
+                             w.Pp, eP, ePp, es, ep, L, n0, an.beta, an.c0, out);
 }
 
 // ---------------------------------------------------------------- FP32: two angles per thread
@@ -544,11 +585,10 @@ template <int POL>
 __device__ __forceinline__ void layer_step2(const Stage32 &g, int TL, int tl, int j, float2 q0sq, float2 nb2,
                                             float yi_max, Sweep2 &w)
 {
-    const StageA<float> A = g.sa[j * TL + tl];
-    const StageP P = g.sp[j * TL + tl];
+    const Medium32 P = medium_at(g, j * TL + tl);
     float absa, absb;
-    const Cx<float> qa = inner_root(Cx<float>{A.d2x + q0sq.x, A.n2y}, &absa);
-    const Cx<float> qb = inner_root(Cx<float>{A.d2x + q0sq.y, A.n2y}, &absb);
+    const Cx<float> qa = inner_root(Cx<float>{P.d2x + q0sq.x, P.n2y}, &absa);
+    const Cx<float> qb = inner_root(Cx<float>{P.d2x + q0sq.y, P.n2y}, &absb);
     w.Ps = mul2(w.Ps, f2(absa, absb));
     const float2 yi = f2(fminf(P.dl * qa.y, yi_max), fminf(P.dl * qb.y, yi_max));
     w.Y = add2(w.Y, yi);
@@ -567,9 +607,8 @@ __device__ __forceinline__ void layer_step2(const Stage32 &g, int TL, int tl, in
         w.nqy_nx = nqy;
     }
     if (POL & 2) {
-        w.Pp *= g.ain2[j * TL + tl];
-        const Cx<float> in2 = {A.in2x, A.in2y};
-        const C2 gq = pack2(cmul(qa, in2), cmul(qb, in2));
+        w.Pp *= abs2(P.in2);
+        const C2 gq = pack2(cmul(qa, P.in2), cmul(qb, P.in2));
         const float2 ngy = neg2(gq.y);
         interface_pair2(gq, ngy, w.g_nx, w.ngy_nx, w.p0, w.p1);
         phase2(cs, sn, nsn, ec, es, nes, w.p0, w.p1);
@@ -588,12 +627,12 @@ __device__ __forceinline__ void eval_point2(const Stage32 &g, int TL, int tl, in
     const float2 q0sq = f2(an[0].q0sq, an[1].q0sq), nb2 = f2(an[0].nb2, an[1].nb2);
     const float yi_max = float(kImDeltaMax / kTwoPi);
 
-    const StageA<float> A = g.sa[(L + 1) * TL + tl];
+    const Medium32 A = medium_at(g, (L + 1) * TL + tl);
     float absz;
     const Cx<float> qoa = forward_root(Cx<float>{A.d2x + q0sq.x, A.n2y}, &absz);
     const Cx<float> qob = forward_root(Cx<float>{A.d2x + q0sq.y, A.n2y}, &absz);
     const Cx<float> n2_out = {A.d2x + n0 * n0, A.n2y};
-    const Cx<float> in2 = {A.in2x, A.in2y};
+    const Cx<float> in2 = A.in2;
     Sweep2 w;
     w.q_nx = pack2(qoa, qob);
     w.nqy_nx = neg2(w.q_nx.y);
@@ -601,7 +640,7 @@ __device__ __forceinline__ void eval_point2(const Stage32 &g, int TL, int tl, in
     w.ngy_nx = neg2(w.g_nx.y);
     w.Ps = bc2(1.f);
     w.Y = bc2(0.f);
-    w.Pp = (POL & 2) ? g.ain2[(L + 1) * TL + tl] : 1.f;
+    w.Pp = (POL & 2) ? abs2(in2) : 1.f;
     int ePa = 0, ePb = 0, ePp = 0;
     w.s0 = C2{bc2(1.f), bc2(0.f)};
     w.s1 = C2{bc2(0.f), bc2(0.f)};
@@ -635,10 +674,11 @@ __device__ __forceinline__ void eval_point2(const Stage32 &g, int TL, int tl, in
         if (POL & 2) renorm_pair2(w.p0, w.p1, epa, epb);
     }
     for (; j >= 1; --j) layer_step2<POL>(g, TL, tl, j, q0sq, nb2, yi_max, w);
-    finish_point<float, POL>(g.sa[tl], qoa, n2_out, lane(w.q_nx, 0), lane(w.g_nx, 0), lane(w.s0, 0), lane(w.s1, 0),
+    const StageA<float> A0 = in2_stage(g, tl);
+    finish_point<float, POL>(A0, qoa, n2_out, lane(w.q_nx, 0), lane(w.g_nx, 0), lane(w.s0, 0), lane(w.s1, 0),
                              lane(w.p0, 0), lane(w.p1, 0), w.Ps.x, w.Y.x, w.Pp, ePa, ePp, esa, epa, L, n0, an[0].beta,
                              an[0].c0, out[0]);
-    finish_point<float, POL>(g.sa[tl], qob, n2_out, lane(w.q_nx, 1), lane(w.g_nx, 1), lane(w.s0, 1), lane(w.s1, 1),
+    finish_point<float, POL>(A0, qob, n2_out, lane(w.q_nx, 1), lane(w.g_nx, 1), lane(w.s0, 1), lane(w.s1, 1),
                              lane(w.p0, 1), lane(w.p1, 1), w.Ps.y, w.Y.y, w.Pp, ePb, ePp, esb, epb, L, n0, an[1].beta,
                              an[1].c0, out[1]);
 }
