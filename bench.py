@@ -542,14 +542,35 @@ def bench_absorption(args, torch, abi, W, flush, world, max_over_ranks):
 
 def bench_surrogate(args, torch, abi, W, flush, world, max_over_ranks):
     """Learned surrogate (20 x 1.46/2.35 stack, 256 lambda x 8 theta x s+p = 4096
-    outputs, 6 x 1024 GELU MLP): trained here on GPU-generated spectra, then
-    inference on 65536 stacks vs the exact kernel on the same stacks."""
+    outputs, 6 x 1024 GELU MLP): trained here on GPU-generated spectra (Adam,
+    cosine learning rate from 1e-3, batches of 8192), with its learning curve on
+    8192 held-out stacks; then inference on 65536 stacks vs the exact kernel on
+    the same stacks, alone and judged (every 16th row, and every row) at
+    max |dR| <= 1e-3 with per-row fallback."""
     from paper_2111_13667_gb300.surrogate import Surrogate, make_dataset, random_thicknesses, train
     sur = Surrogate()
     t0 = time.perf_counter()
     d, R = make_dataset(sur, args.sur_train, seed=4)
     gen_s = time.perf_counter() - t0
-    rep = train(sur, d, R, steps=args.sur_steps, batch=8192, lr_max=1e-3, warmup=100)
+    d_test = random_thicknesses(8192, seed=45)
+    R_test = sur.generate(d_test)
+    tols = (1e-3, 1e-2, 5e-2, 1e-1)
+
+    def held_out():
+        y = sur.infer(d_test)
+        e = (y - R_test).abs()
+        rowmax = e.amax(dim=1)
+        return {"mse": float((e * e).mean()), "mean_abs_err": float(e.mean()),
+                "row_max_err_median": float(rowmax.median()),
+                "rows_within": {f"{t:g}": float((rowmax <= t).float().mean()) for t in tols}}
+
+    curve = []
+    t_train = time.perf_counter()
+    rep = train(sur, d, R, steps=args.sur_steps, batch=8192, lr_max=1e-3, warmup=200,
+                eval_every=max(1, args.sur_steps // 10),
+                on_eval=lambda k, loss: curve.append({"step": k, "seconds": time.perf_counter() - t_train,
+                                                     "train_loss": loss, **held_out()}))
+    mean_mse = float(((R_test - R.mean(dim=0)) ** 2).mean())  # the mean spectrum as predictor
     del d, R
     torch.cuda.empty_cache()
     B = 65536
@@ -559,18 +580,24 @@ def bench_surrogate(args, torch, abi, W, flush, world, max_over_ranks):
     torch.cuda.synchronize()
     err = (raw - exact).abs().amax(dim=1)
     mean_abs = float((raw - exact).abs().mean())
-    within = float((err <= 1e-3).float().mean())
+    within = {f"{t:g}": float((err <= t).float().mean()) for t in tols}
     outR = torch.empty_like(exact)
     stats = torch.zeros(2, dtype=torch.int32, device=dt.device)
     steps = max(3, args.steps // 2)
     t_exact = time_steps(lambda: sur.generate(dt, outR), steps, 3, torch, flush)
     t_net = time_steps(lambda: sur.infer(dt, out=outR), steps, 3, torch, flush)
-    t_judge = time_steps(lambda: sur.infer(dt, 1.0, 1e-3, out=outR, stats=stats), steps, 3, torch, flush)
-    n_fb = int(stats[0].item())
-    judged_err = float((outR - exact).abs().max())
+    judged = {}
+    for frac in (1.0 / 16, 1.0):
+        tj = time_steps(lambda: sur.infer(dt, frac, 1e-3, out=outR, stats=stats), steps, 3, torch, flush)
+        n_fb = int(stats[0].item())
+        rows = torch.arange(0, B, int(round(1 / frac)), device=dt.device)
+        ms_j = max_over_ranks(sum(tj) / len(tj))
+        judged[f"judge_fraction_{frac:g}"] = {
+            "value": B * world / (ms_j * 1e-3), "ms_per_step": ms_j, "judged_rows": int(rows.numel()),
+            "fallback_rows": n_fb, "max_abs_err_judged_rows_delivered": float((outR[rows] - exact[rows]).abs().max()),
+            "max_abs_err_all_rows_delivered": float((outR - exact).abs().max()), "tol": 1e-3}
     ms_e = max_over_ranks(sum(t_exact) / len(t_exact))
     ms_n = max_over_ranks(sum(t_net) / len(t_net))
-    ms_j = max_over_ranks(sum(t_judge) / len(t_judge))
     flops = 2.0 * B * sum(n * k for n, k in sur_shapes(sur))
     peaks = measured_peaks() or {}
     peak = peaks.get("bf16_tflops")
@@ -579,17 +606,20 @@ def bench_surrogate(args, torch, abi, W, flush, world, max_over_ranks):
     achieved = flops / (ms_n * 1e-3) / 1e12
     status = sur.status()
     sur.close()
+    full = judged["judge_fraction_1"]
     return {"unit": "spectra/s", "outputs_per_spectrum": int(exact.shape[1]), "batch": B,
             "parameters": sur.parameters, "dataset_spectra": args.sur_train, "dataset_gen_s": gen_s,
             "train": {"steps": rep.steps, "batch": rep.batch, "seconds": rep.seconds, "loss_first": rep.loss_first,
-                      "loss_last": rep.loss_last},
+                      "loss_last": rep.loss_last, "lr": "1e-3 peak, 200 warm-up steps, cosine to 1e-5",
+                      "held_out_mse_of_mean_spectrum": mean_mse, "learning_curve": curve},
             "exact_tmm": {"value": B * world / (ms_e * 1e-3), "ms_per_step": ms_e},
             "network_only": {"value": B * world / (ms_n * 1e-3), "ms_per_step": ms_n,
                              "max_abs_err": float(err.max()), "mean_abs_err": mean_abs,
-                             "rows_within_1e-3": within},
-            "judged_all_fallback": {"value": B * world / (ms_j * 1e-3), "ms_per_step": ms_j,
-                                    "fallback_rows": n_fb, "max_abs_err_delivered": judged_err, "tol": 1e-3},
-            "speedup_network_only": ms_e / ms_n, "speedup_at_max_err_1e-3": ms_e / ms_j,
+                             "rows_within_1e-3": within["0.001"], "rows_within": within},
+            "judged": judged,
+            "speedup_network_only": ms_e / ms_n,
+            "speedup_at_max_err_1e-3": ms_e / full["ms_per_step"],
+            "speedup_judge_fraction_1_16": ms_e / judged["judge_fraction_0.0625"]["ms_per_step"],
             "roofline": {"bound": "tensor", "kernel": "gemm_bf16_kernel (7 GEMMs of one inference)",
                          "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                          "peak_source": peak_src, "work": f"{flops / 1e12:.3f} TFLOP per 65536-spectrum batch"},
@@ -739,7 +769,7 @@ def main():
                     help="extra sections after the headline (comma list of ragged, adjoint, optimize, incoherent, "
                          "partial, absorption, paper, surrogate)")
     ap.add_argument("--sur-train", type=int, default=2_000_000, help="training spectra (GPU-generated)")
-    ap.add_argument("--sur-steps", type=int, default=2000, help="training steps of 8192 spectra")
+    ap.add_argument("--sur-steps", type=int, default=60000, help="training steps of 8192 spectra (about 85 s)")
     ap.add_argument("--stacks", type=int, default=0, help="shrink the workload (profiling runs only)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     args = ap.parse_args()

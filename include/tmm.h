@@ -222,11 +222,13 @@ TMM_API tmm_status tmm_coh_grad(const tmm_problem *p, const void *R_target, void
  *   incoherent  device uint8 [S][L_max], nonzero = incoherent layer; NULL =
  *               none (the coherent result)
  *   R, T        as tmm_coh_batched (T may be NULL); pol_mask 1, 2, 3 or 7
- * Incoherent layers must be non-absorbing: a point whose wavelength gives an
- * incoherent layer a complex index gets NaN.  The first incoherent layer in
- * which the wave is evanescent (n_j <= n_0 sin theta) ends the stack: it is
- * the exit medium for R and T = 0.  prec TMM_F64 or TMM_F32 (TMM_F64X:
- * TMM_ERR_UNSUPPORTED).  Asynchronous on `stream`.
+ * An incoherent layer may absorb: each single pass of light through it is
+ * attenuated by exp(-4 pi Im(n_j cos theta_j) d_j / lambda) (Beer-Lambert
+ * along the refracted path), and the blocks next to it see its complex index
+ * in their Fresnel coefficients and Poynting factors.  The first incoherent
+ * layer with Re(n_j^2 - n_0^2 sin^2 theta) <= 0 (for a real index: the wave
+ * is evanescent) ends the stack: it is the exit medium for R and T = 0.  prec
+ * TMM_F64 or TMM_F32 (else TMM_ERR_UNSUPPORTED).  Asynchronous on `stream`.
  */
 TMM_API tmm_status tmm_inc_batched(const tmm_problem *p, const uint8_t *incoherent, void *R, void *T,
                                    void *stream);
@@ -379,7 +381,7 @@ typedef struct {
     const double *lambda;    /* host [n_lambda], nm */
     int32_t n_theta;
     const double *theta;     /* host [n_theta], radians */
-    double d_min, d_max;     /* thickness range; inputs are mapped to [-1, 1] */
+    double d_min, d_max;     /* thickness range; inputs are mapped to [0, 1] */
     int32_t hidden;          /* width, multiple of 64 */
     int32_t depth;           /* hidden layers, 1..16 */
     uint64_t seed;           /* weight initialisation */

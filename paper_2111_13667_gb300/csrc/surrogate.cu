@@ -4,7 +4,7 @@
 // tcgen05 bf16 GEMM with fp32 accumulation, and judged by the exact
 // transfer-matrix kernel with a per-row fallback.
 //
-// Network: x = 2 (d - d_min) / (d_max - d_min) - 1 (L inputs, zero-padded to
+// Network: x = (d - d_min) / (d_max - d_min) in [0, 1] (L inputs, zero-padded to
 // 64), `depth` hidden layers of width `hidden` with GELU (erf form), a linear
 // head of 2 n_theta n_lambda outputs (clamped to [0, 1] at inference).
 // Training: MSE loss, Adam on fp32 master weights; every GEMM of the forward

@@ -7,15 +7,20 @@
 // combined by intensities.  Per block and polarisation:
 //   R_f = |M10 / M00|^2 (light from a),  R_b = |M01 / M00|^2 (light from b),
 //   T_f from M00 and the carried scales exactly as the forward kernel's T
-//   (Eqs. 5-6 with the Poynting factors), and T_b = T_f (transmittance of a
-//   stack between non-absorbing media is reciprocal).
-// With (P, M) the forward and backward intensities on the left of the blocks
-// done so far, scaled by the product t of their T_f,
+//   (Eqs. 5-6 with the Poynting factors Re k, k = q for s, q / n^2 for p), and
+//   T_b = T_f (Re k_a / |k_a|)^2 / (Re k_b / |k_b|)^2: the amplitude
+//   transmissions from either side differ by det M = k_b / k_a (1 between
+//   non-absorbing media).
+// An absorbing incoherent layer j attenuates every single pass by
+// p_j = exp(-4 pi Im(q_j) d_j / lambda).  With (P, M) the forward and backward
+// intensities on the left of the blocks done so far, scaled by the product t
+// of their T_f and single-pass factors, crossing layer b from its right
+// boundary to its left takes (P, M, t) to (P, p_b^2 M, p_b t), and a block
 //   P' = P - R_b M,   M' = R_f P' + T_f T_b M,   t' = t T_f
 // from (1, 0, 1) in the exit medium; R = M / P and T = t / P in medium 0.
-// Incoherent layers must be non-absorbing (else the point's outputs are NaN);
-// the first incoherent layer in which the wave is evanescent ends the stack:
-// it is the exit medium and T = 0.
+// The first incoherent layer with Re(n_j^2 - n_0^2 sin^2 theta) <= 0 (for a
+// real index: the wave is evanescent) ends the stack: it is the exit medium
+// and T = 0.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -52,13 +57,20 @@ template <typename R> __device__ __forceinline__ void phase_cols(Cols<R> &c, Cx<
     c.y0 = cmul(emi, c.y0), c.y1 = cmul(epi, c.y1);
 }
 
-// R_f, R_b, T_f of the coherent block between incoherent media a < b, for the
-// polarisations in POL ([0] s, [1] p).  q_a (> 0) and n_a^2 are real; a = 0
-// takes q_0 = n_0 cos(theta) directly.
+// (Re k_a / |k_a|)^2 / (Re k_b / |k_b|)^2, exactly 1 for real k_a, k_b.
+template <typename R> __device__ __forceinline__ R back_ratio(Cx<R> ka, Cx<R> kb)
+{
+    if (ka.y == R(0) && kb.y == R(0)) return R(1);
+    return (ka.x * ka.x * abs2(kb)) / (kb.x * kb.x * abs2(ka));
+}
+
+// R_f, R_b, T_f, T_b of the coherent block between incoherent media a < b,
+// for the polarisations in POL ([0] s, [1] p).  q_a is medium a's root (a = 0:
+// q_0 = n_0 cos(theta), computed directly).
 template <typename R, int POL>
 __device__ __forceinline__ void block_coeffs(const StageA<R> *__restrict__ sa, const StageB<R> *__restrict__ sb,
-                                             int TL, int tl, int a, int b, R q0sq, R qa, R n0, R Rf[2], R Rb[2],
-                                             R Tf[2])
+                                             int TL, int tl, int a, int b, R q0sq, Cx<R> q_a, R n0, R Rf[2], R Rb[2],
+                                             R Tf[2], R Tb[2])
 {
     constexpr int RN = RenormEvery<R>::value;
     const R yi_max = R(kImDeltaMax / kTwoPi);
@@ -67,6 +79,7 @@ __device__ __forceinline__ void block_coeffs(const StageA<R> *__restrict__ sa, c
     Cx<R> q_nx = forward_root(Cx<R>{A.d2x + q0sq, A.n2y}, &absz);
     const Cx<R> q_b = q_nx, n2_b = {A.d2x + n0 * n0, A.n2y};
     Cx<R> g_nx = cmul(q_nx, Cx<R>{A.in2x, A.in2y});
+    const Cx<R> g_b = g_nx;
     R Pp = sb[b * TL + tl].ain2;
     int ePp = 0;
     R Ps = R(1), Y = R(0);
@@ -108,10 +121,9 @@ __device__ __forceinline__ void block_coeffs(const StageA<R> *__restrict__ sa, c
             if (POL & 2) renorm_cols(cp, ep);
         }
     }
-    // interface a | a+1; medium a is real
+    // interface a | a+1
     A = sa[a * TL + tl];
-    const Cx<R> q_a = {qa, R(0)};
-    Ps *= qa * qa;
+    Ps *= abs2(q_a);
     const int e4 = 2 * (b - a);
     R u = R(-2.0 * kTwoPi * kLog2e) * Y;
     u = fmax(u, R(-1.0e6));
@@ -124,23 +136,33 @@ __device__ __forceinline__ void block_coeffs(const StageA<R> *__restrict__ sa, c
         const R ax0 = abs2(cs.x0);
         Rf[0] = abs2(cs.x1) / ax0;
         Rb[0] = abs2(cs.y0) / ax0;
-        Tf[0] = q_b.x / qa * ldexp_w(Ps * yscale / ax0, e4 + eP + yn - 2 * es);
+        Tf[0] = q_b.x / q_a.x * ldexp_w(Ps * yscale / ax0, e4 + eP + yn - 2 * es);
+        Tb[0] = Tf[0] * back_ratio(q_a, q_b);
     }
     if (POL & 2) {
-        const R na2 = A.d2x + n0 * n0;
+        const Cx<R> n2_a = {A.d2x + n0 * n0, A.n2y};
         const Cx<R> g_a = cmul(q_a, Cx<R>{A.in2x, A.in2y});
         interface_pair(g_a, g_nx, cp.x0, cp.x1);
         interface_pair(g_a, g_nx, cp.y0, cp.y1);
         const R ax0 = abs2(cp.x0);
         Rf[1] = abs2(cp.x1) / ax0;
         Rb[1] = abs2(cp.y0) / ax0;
-        const R num = cmul(n2_b, conj(q_b)).x;
-        Tf[1] = num / (na2 * qa) * ldexp_w(Ps * Pp * yscale / ax0, e4 + eP + ePp + yn - 2 * ep);
+        const R num = cmul(n2_b, conj(q_b)).x, den = cmul(n2_a, conj(q_a)).x;
+        Tf[1] = num / den * ldexp_w(Ps * Pp * yscale / ax0, e4 + eP + ePp + yn - 2 * ep);
+        Tb[1] = Tf[1] * back_ratio(g_a, g_b);
     }
 }
 
-// One point (one angle), both polarisations: Rv, Tv = {s, p}.  ok: the
-// stack is valid and its incoherent layers are non-absorbing.
+// Single-pass power factor exp(-4 pi Im(q_j) d_j / lambda) of finite layer j.
+template <typename R>
+__device__ __forceinline__ R pass_factor(const StageA<R> &A, const StageB<R> &B, R q0sq)
+{
+    R absz;
+    const Cx<R> q = forward_root(Cx<R>{A.d2x + q0sq, A.n2y}, &absz);
+    return exp_m2_turn(B.dl * q.y);
+}
+
+// One point (one angle), both polarisations: Rv, Tv = {s, p}.
 template <typename R, int POL>
 __device__ __forceinline__ void inc_point(const StageA<R> *__restrict__ sa, const StageB<R> *__restrict__ sb,
                                           const unsigned char *flg, int TL, int tl, int L, R n0, R sth, R cth,
@@ -165,16 +187,23 @@ __device__ __forceinline__ void inc_point(const StageA<R> *__restrict__ sa, cons
     R P[2] = {R(1), R(1)}, M[2] = {R(0), R(0)}, t[2] = {R(1), R(1)};
     int b = e;
     while (b > 0) {
+        if (b != e) {  // across incoherent layer b, right boundary to left
+            const R pb = pass_factor(sa[b * TL + tl], sb[b * TL + tl], q0sq);
+#pragma unroll
+            for (int k = 0; k < 2; ++k) M[k] *= pb * pb, t[k] *= pb;
+        }
         int a = b - 1;
         while (a > 0 && !flg[a]) --a;
-        const R qa = a == 0 ? c0 : sqrt(sa[a * TL + tl].d2x + q0sq);
-        R Rf[2] = {R(0), R(0)}, Rb[2] = {R(0), R(0)}, Tf[2] = {R(0), R(0)};
-        block_coeffs<R, POL>(sa, sb, TL, tl, a, b, q0sq, qa, n0, Rf, Rb, Tf);
+        R absa;
+        const Cx<R> qa = a == 0 ? Cx<R>{c0, R(0)}
+                                : forward_root(Cx<R>{sa[a * TL + tl].d2x + q0sq, sa[a * TL + tl].n2y}, &absa);
+        R Rf[2] = {R(0), R(0)}, Rb[2] = {R(0), R(0)}, Tf[2] = {R(0), R(0)}, Tb[2] = {R(0), R(0)};
+        block_coeffs<R, POL>(sa, sb, TL, tl, a, b, q0sq, qa, n0, Rf, Rb, Tf, Tb);
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
             if (!(POL & (1 << k))) continue;
             const R P1 = P[k] - Rb[k] * M[k];
-            const R M1 = Rf[k] * P1 + Tf[k] * Tf[k] * M[k];
+            const R M1 = Rf[k] * P1 + Tf[k] * Tb[k] * M[k];
             const R inv = R(1) / P1;  // keep P = 1
             P[k] = R(1);
             M[k] = M1 * inv;
@@ -190,13 +219,13 @@ __device__ __forceinline__ void inc_point(const StageA<R> *__restrict__ sa, cons
 }
 
 // ---------------------------------------------------------------- FP32: two angles per thread
-// block_coeffs for the two angles in the lanes of q0sq (qa: the real root of
+// block_coeffs for the two angles in the lanes of q0sq (qa: the root of
 // medium a per lane); outputs [lane][pol].
 template <int POL>
 __device__ __forceinline__ void block_coeffs2(const StageA<float> *__restrict__ sa,
                                               const StageB<float> *__restrict__ sb, int TL, int tl, int a, int b,
-                                              float2 q0sq, float2 qa, float n0, float Rf[2][2], float Rb[2][2],
-                                              float Tf[2][2])
+                                              float2 q0sq, const Cx<float> qa[2], float n0, float Rf[2][2],
+                                              float Rb[2][2], float Tf[2][2], float Tb[2][2])
 {
     constexpr int RN = RenormEvery<float>::value;
     const float yi_max = float(kImDeltaMax / kTwoPi);
@@ -261,16 +290,16 @@ __device__ __forceinline__ void block_coeffs2(const StageA<float> *__restrict__ 
             if (POL & 2) renorm_cols2(cp, epa, epb);
         }
     }
-    // interface a | a+1 per lane; medium a is real
+    // interface a | a+1 per lane
     A = sa[a * TL + tl];
     const int e4 = 2 * (b - a);
-    const float na2 = A.d2x + n0 * n0;
+    const Cx<float> n2_a = {A.d2x + n0 * n0, A.n2y};
     const Cx<float> in2a = {A.in2x, A.in2y};
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
-        const float qai = i ? qa.y : qa.x, Psi = (i ? Ps.y : Ps.x) * (qai * qai), Yi = i ? Y.y : Y.x;
+        const Cx<float> q_a = qa[i], q_b = i ? qbb : qba;
+        const float Psi = (i ? Ps.y : Ps.x) * abs2(q_a), Yi = i ? Y.y : Y.x;
         const int ePi = i ? ePb : ePa;
-        const Cx<float> q_a = {qai, 0.f}, q_b = i ? qbb : qba;
         float u = float(-2.0 * kTwoPi * kLog2e) * Yi;
         u = fmaxf(u, -1.0e6f);
         const float un = floorf(u);
@@ -284,7 +313,8 @@ __device__ __forceinline__ void block_coeffs2(const StageA<float> *__restrict__ 
             const float ax0 = abs2(x0);
             Rf[i][0] = abs2(x1) / ax0;
             Rb[i][0] = abs2(y0) / ax0;
-            Tf[i][0] = q_b.x / qai * ldexpf(Psi * yscale / ax0, e4 + ePi + yn - 2 * (i ? esb : esa));
+            Tf[i][0] = q_b.x / q_a.x * ldexpf(Psi * yscale / ax0, e4 + ePi + yn - 2 * (i ? esb : esa));
+            Tb[i][0] = Tf[i][0] * back_ratio(q_a, q_b);
         }
         if (POL & 2) {
             const Cx<float> g_a = cmul(q_a, in2a), gn = lane(g_nx, i);
@@ -294,8 +324,9 @@ __device__ __forceinline__ void block_coeffs2(const StageA<float> *__restrict__ 
             const float ax0 = abs2(x0);
             Rf[i][1] = abs2(x1) / ax0;
             Rb[i][1] = abs2(y0) / ax0;
-            const float num = cmul(n2_b, conj(q_b)).x;
-            Tf[i][1] = num / (na2 * qai) * ldexpf(Psi * Pp * yscale / ax0, e4 + ePi + ePp + yn - 2 * (i ? epb : epa));
+            const float num = cmul(n2_b, conj(q_b)).x, den = cmul(n2_a, conj(q_a)).x;
+            Tf[i][1] = num / den * ldexpf(Psi * Pp * yscale / ax0, e4 + ePi + ePp + yn - 2 * (i ? epb : epa));
+            Tb[i][1] = Tf[i][1] * back_ratio(g_a, cmul(q_b, in2b));
         }
     }
 }
@@ -329,18 +360,35 @@ __device__ __forceinline__ void inc_point2(const StageA<float> *__restrict__ sa,
     float P[2][2] = {{1.f, 1.f}, {1.f, 1.f}}, M[2][2] = {{0.f, 0.f}, {0.f, 0.f}}, t[2][2] = {{1.f, 1.f}, {1.f, 1.f}};
     int b = e[0];
     while (b > 0) {
+        if (b != e[0]) {  // across incoherent layer b, right boundary to left
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const float pb = pass_factor(sa[b * TL + tl], sb[b * TL + tl], i ? q0sq.y : q0sq.x);
+#pragma unroll
+                for (int k = 0; k < 2; ++k) M[i][k] *= pb * pb, t[i][k] *= pb;
+            }
+        }
         int a = b - 1;
         while (a > 0 && !flg[a]) --a;
-        const float2 qa = a == 0 ? c0 : f2(sqrtf(sa[a * TL + tl].d2x + q0sq.x), sqrtf(sa[a * TL + tl].d2x + q0sq.y));
-        float Rf[2][2] = {}, Rb[2][2] = {}, Tf[2][2] = {};
-        block_coeffs2<POL>(sa, sb, TL, tl, a, b, q0sq, qa, n0, Rf, Rb, Tf);
+        Cx<float> qa[2];
+        if (a == 0) {
+            qa[0] = Cx<float>{c0.x, 0.f};
+            qa[1] = Cx<float>{c0.y, 0.f};
+        } else {
+            const StageA<float> Aa = sa[a * TL + tl];
+            float absa;
+            qa[0] = forward_root(Cx<float>{Aa.d2x + q0sq.x, Aa.n2y}, &absa);
+            qa[1] = forward_root(Cx<float>{Aa.d2x + q0sq.y, Aa.n2y}, &absa);
+        }
+        float Rf[2][2] = {}, Rb[2][2] = {}, Tf[2][2] = {}, Tb[2][2] = {};
+        block_coeffs2<POL>(sa, sb, TL, tl, a, b, q0sq, qa, n0, Rf, Rb, Tf, Tb);
 #pragma unroll
         for (int i = 0; i < 2; ++i)
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
                 if (!(POL & (1 << k))) continue;
                 const float P1 = P[i][k] - Rb[i][k] * M[i][k];
-                const float M1 = Rf[i][k] * P1 + Tf[i][k] * Tf[i][k] * M[i][k];
+                const float M1 = Rf[i][k] * P1 + Tf[i][k] * Tb[i][k] * M[i][k];
                 const float inv = 1.f / P1;
                 P[i][k] = 1.f;
                 M[i][k] = M1 * inv;
@@ -393,11 +441,7 @@ __global__ void __launch_bounds__(kIncThreads) tmm_inc_kernel(const tmm_problem 
     R Rv[2][2], Tv[2][2];
 #pragma unroll
     for (int i = 0; i < 2; ++i) Rv[i][0] = Rv[i][1] = Tv[i][0] = Tv[i][1] = nan_w<R>();
-    bool ok = L >= 0;
-    if (ok)
-        for (int j = 1; j <= L; ++j)
-            if (flg[j] && sa[j * TL + tl].n2y != R(0)) ok = false;  // absorbing incoherent layer
-    if (ok) {
+    if (L >= 0) {
         const R *th = (const R *)p.theta;
         const R n0 = n0s[tl];
         if constexpr (PAIR) {

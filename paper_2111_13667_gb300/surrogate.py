@@ -137,8 +137,10 @@ class TrainReport:
 
 
 def train(sur: Surrogate, d: torch.Tensor, R: torch.Tensor, steps: int, batch: int = 8192, lr_max: float = 1e-3,
-          lr_min: float = 1e-5, warmup: int = 100, log_every: int = 0) -> TrainReport:
-    """Adam with linear warm-up and cosine decay over contiguous dataset slices."""
+          lr_min: float = 1e-5, warmup: int = 100, log_every: int = 0, on_eval=None, eval_every: int = 0) -> TrainReport:
+    """Adam with linear warm-up and cosine decay over contiguous dataset slices.
+    ``on_eval(step, loss)`` is called every ``eval_every`` steps and after the
+    last (for a learning curve)."""
     import time
     n = (int(d.shape[0]) // batch) * batch
     loss = torch.zeros(1, device=d.device)
@@ -155,6 +157,8 @@ def train(sur: Surrogate, d: torch.Tensor, R: torch.Tensor, steps: int, batch: i
             first = float(loss.item())
         if log_every and k % log_every == 0:
             print(f"step {k} lr {lr:.2e} loss {float(loss.item()):.3e}", flush=True)
+        if on_eval is not None and ((eval_every and (k + 1) % eval_every == 0) or k + 1 == steps):
+            on_eval(k + 1, float(loss.item()))
     torch.cuda.synchronize()
     return TrainReport(steps, batch, time.perf_counter() - t0, first or float("nan"), float(loss.item()))
 

@@ -207,16 +207,19 @@ def ragged(seed=3, S=131072, L_max=120, n_lambda=256, n_theta=16):
                     L_per_stack=Ls)
 
 
-def coated_substrate(seed=5, S=16384, L=24, n_lambda=512, n_theta=32):
+def coated_substrate(seed=5, S=16384, L=24, n_lambda=512, n_theta=32, plate_k=0.0):
     """Coatings on a thick glass plate in air: layers 1..L-1 as the dispersive
     workload (8 Cauchy materials, d ~ U[5, 400] nm), layer L a 1 mm plate of
-    the substrate index 1.52 flagged incoherent, air behind it.  Returns the
-    workload with ``meta["incoherent"]`` = uint8 [S][L] flags."""
+    the substrate index 1.52 (plus i plate_k, a weakly absorbing glass, when
+    plate_k > 0) flagged incoherent, air behind it.  Returns the workload with
+    ``meta["incoherent"]`` = uint8 [S][L] flags."""
     rng = np.random.default_rng(seed)
     lam = np.linspace(300.0, 1200.0, n_lambda)
     table = cauchy_table(rng, lam)
+    if plate_k > 0.0:
+        table = np.ascontiguousarray(np.concatenate([table, table[N_MATERIALS + 1:N_MATERIALS + 2] + 1j * plate_k]))
     mat = _mat_rows(rng, S, L)
-    mat[:, L] = N_MATERIALS + 1       # the plate: substrate index
+    mat[:, L] = N_MATERIALS + 1 if plate_k <= 0.0 else N_MATERIALS + 2  # the plate
     mat[:, L + 1] = N_MATERIALS       # air behind it (the ambient row)
     d = rng.uniform(5.0, 400.0, (S, L))
     d[:, L - 1] = 1.0e6

@@ -24,15 +24,16 @@ def _lib():
     abi.load()
 
 
-def random_inc_workload(seed, S=5, L=6, n_lambda=17, n_theta=5, L_per_stack=None):
-    """Coherent layers may absorb; flagged (incoherent) layers are real and thick."""
+def random_inc_workload(seed, S=5, L=6, n_lambda=17, n_theta=5, L_per_stack=None, inc_k=0.0):
+    """Coherent layers may absorb; flagged (incoherent) layers are thick, with
+    extinction coefficients up to inc_k."""
     rng = np.random.default_rng(seed)
     lam = np.linspace(450.0, 750.0, n_lambda)
     flags = (rng.uniform(size=(S, L)) < 0.35).astype(np.uint8)
     n = np.empty((S, L + 2, n_lambda), dtype=np.complex128)
     n[:, 0] = 1.0
     re = rng.uniform(1.3, 2.4, (S, L))
-    im = rng.uniform(0.0, 0.08, (S, L)) * (flags == 0)
+    im = np.where(flags == 0, rng.uniform(0.0, 0.08, (S, L)), rng.uniform(0.0, inc_k, (S, L)))
     n[:, 1:L + 1] = (re + 1j * im)[:, :, None] * (1.0 + 0.02 * (lam[None, None, :] - 600.0) / 300.0)
     n[:, L + 1] = 1.52
     d = np.where(flags == 1, rng.uniform(2e4, 5e5, (S, L)), rng.uniform(20.0, 250.0, (S, L)))
@@ -93,15 +94,42 @@ def test_evanescent_cut_and_absorbing_incoherent_layer():
     th = np.deg2rad([0.0, 70.0])
     nd = np.array([[1.8, 2.2, 1.5, 2.0, 1.0],        # at 70 deg the 1.5 slab is evanescent
                    [1.0, 2.0, 1.5 + 0.01j, 1.7, 1.0]], dtype=np.complex128)  # absorbing incoherent
-    d = np.array([[110.0, 1e6, 90.0], [100.0, 1e5, 80.0]])
+    d = np.array([[110.0, 1e6, 90.0], [100.0, 1e3, 80.0]])
     flags = np.array([[0, 1, 0], [0, 1, 0]], dtype=np.uint8)
     w = W.Workload("cut", theta=th, lam=lam, d=d, n_direct=nd)
-    Ro, To = oracle_inc(W.Workload("cut", theta=th, lam=lam, d=d[:1], n_direct=np.repeat(nd[:1, :, None], 2, 2)),
-                        flags[:1])
+    Ro, To = oracle_inc(W.Workload("cut", theta=th, lam=lam, d=d, n_direct=np.repeat(nd[:, :, None], 2, 2)), flags)
     R, T = gpu_inc(w, flags, "f64")
-    assert np.max(np.abs(R[:, 0] - Ro[:, 0])) <= 1e-10 and np.max(np.abs(T[:, 0] - To[:, 0])) <= 1e-10
+    assert np.max(np.abs(R - Ro)) <= 1e-10 and np.max(np.abs(T - To)) <= 1e-10
     assert np.all(T[:, 0, 1, :] == 0.0)
-    assert np.isnan(R[:, 1]).all() and np.isnan(T[:, 1]).all()
+    assert np.all(T[:, 1] > 0.0) and np.all(R[:, 1] + T[:, 1] < 1.0)  # the absorber transmits part
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_absorbing_incoherent_layers_match_oracle(prec):
+    # flagged layers with extinction coefficients up to 1e-4 (0.2 - 500 um
+    # thick: single-pass factors down to ~0.3), next to absorbing coherent ones
+    w, flags = random_inc_workload(44, S=6, inc_k=1e-4)
+    assert flags.sum() >= 4
+    Ro, To = oracle_inc(w, flags)
+    R, T = gpu_inc(w, flags, prec)
+    assert np.max(np.abs(R - Ro)) <= TOL[prec] and np.max(np.abs(T - To)) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("plate_k", [1e-6, 2e-5])
+def test_coated_absorbing_plate(prec, plate_k):
+    # coatings on a 1 mm plate of weakly absorbing glass (1.52 + i plate_k)
+    w = W.coated_substrate(S=4, n_lambda=23, n_theta=6, plate_k=plate_k)
+    flags = w.meta["incoherent"]
+    n = oracle_index(w)
+    Ro = np.stack([inc.inc_tmm(pol, n, w.d, flags, w.theta, w.lam)[0] for pol in "sp"])
+    To = np.stack([inc.inc_tmm(pol, n, w.d, flags, w.theta, w.lam)[1] for pol in "sp"])
+    R, T = gpu_inc(w, flags, prec)
+    assert np.max(np.abs(R - Ro)) <= TOL[prec] and np.max(np.abs(T - To)) <= TOL[prec]
+    # the plate absorbs: less transmitted than the lossless plate
+    w0 = W.coated_substrate(S=4, n_lambda=23, n_theta=6)
+    R0, T0 = gpu_inc(w0, flags, prec)
+    assert np.all(T <= T0 + TOL[prec])
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32"])

@@ -105,3 +105,31 @@ def test_weight_gradients_match_finite_differences(problem):
         g = float(grads[li][0][n, k])
         assert abs(fd - g) <= 1e-6 + 1e-3 * abs(g), (li, fd, g)
         assert abs(g) > 1e-6
+
+
+def test_written_out_backward_equals_autograd():
+    # the layer-by-layer backward of forward_backward_stored, rounding off, is
+    # the autograd gradient of the same loss (a transposed operand, a missing
+    # GELU' factor or a wrong loss scale would fail here)
+    layers = _net([16, 12, 9], seed=5)
+    g = torch.Generator().manual_seed(6)
+    d = 20.0 + 230.0 * torch.rand(7, 5, generator=g)
+    t = torch.rand(7, 9, generator=g)
+    loss_a, grads_a, y_a = mlp.forward_backward(layers, d, t, 20.0, 250.0)
+    Wr = [(W.to(torch.bfloat16).double(), b) for W, b in layers]  # the rounding forward_backward applies
+    x = torch.zeros(7, 64, dtype=torch.float64)
+    x[:, :5] = (d.double() - 20.0) / 230.0
+    # forward_backward rounds its input to bf16; feed the same input here
+    d_r = (x[:, :5].to(torch.bfloat16).double() * 230.0 + 20.0)
+    loss_b, grads_b, y_b = mlp.forward_backward_stored(Wr, d_r, t, 20.0, 250.0, bf16=False)
+    assert abs(loss_a - loss_b) < 1e-12
+    assert float((y_a - y_b).abs().max()) < 1e-12
+    for (gw, gb), (hw, hb) in zip(grads_a, grads_b):
+        assert float((gw - hw).abs().max()) < 1e-12 and float((gb - hb).abs().max()) < 1e-12
+
+
+def test_gelu_grad_is_the_derivative():
+    z = torch.linspace(-6.0, 6.0, 601, dtype=torch.float64)
+    h = 1e-6
+    fd = (mlp.gelu(z + h) - mlp.gelu(z - h)) / (2 * h)
+    assert float((mlp.gelu_grad(z) - fd).abs().max()) < 1e-9

@@ -42,6 +42,12 @@ def test_generate_matches_oracle():
 
 
 def test_training_step_gradients_match_cpu_reference():
+    """Every element of every weight and bias gradient of one tcgen05 training
+    step against the CPU reference that rounds to bf16 where the kernels store
+    bf16 (oracle.mlp.forward_backward_stored).  What remains is the order of the
+    fp32 sums (up to 1024 terms, relative 2^-24 each) and the odd bf16 rounding
+    it flips; the bound, 1e-3 of the layer's largest gradient element plus 1 %
+    of the element, is far above both."""
     sur = small()
     B = 256
     d = random_thicknesses(B, seed=62)
@@ -50,14 +56,17 @@ def test_training_step_gradients_match_cpu_reference():
     sur.train_step(d, T, lr=1e-6)
     torch.cuda.synchronize()
     assert sur.status() == abi.TMM_OK
-    loss, grads, _ = mlp.forward_backward([(W_.cpu(), b.cpu()) for W_, b in layers], d.cpu(), T.cpu(),
-                                          *sur.d_range)
+    _, grads, _ = mlp.forward_backward_stored([(W_.cpu(), b.cpu()) for W_, b in layers], d.cpu(), T.cpu(),
+                                              *sur.d_range)
+    worst = 0.0
     for i in range(sur.depth + 1):
         _, _, dW, db = [t.cpu().double() for t in sur.layer_tensors(i)]
-        gW, gb = grads[i]
-        rel_w = float((dW - gW).norm() / gW.norm())
-        rel_b = float((db - gb).norm() / gb.norm())
-        assert rel_w < 2e-2 and rel_b < 2e-2, (i, rel_w, rel_b)
+        for got, ref in ((dW, grads[i][0]), (db, grads[i][1])):
+            scale = float(ref.abs().max())
+            excess = (got - ref).abs() - (1e-3 * scale + 1e-2 * ref.abs())
+            assert float(excess.max()) <= 0.0, (i, float((got - ref).abs().max()), scale)
+            worst = max(worst, float((got - ref).abs().max()) / scale)
+    print(f"largest element-wise gradient difference: {worst:.2e} of the layer's largest element")
 
 
 def test_training_reduces_loss_and_judge_guarantees_tolerance(tmp_path):
@@ -105,23 +114,43 @@ def test_checkpoint_resume_is_exact(tmp_path):
         assert torch.equal(sur.layer_tensors(i)[0], other.layer_tensors(i)[0])
 
 
-def test_mlp_inference_outruns_exact_kernel():
-    """The gain the network buys: spectra per second of the network alone vs
-    the exact kernel on the same 65536 stacks (full-size network)."""
+def test_judged_inference_delivers_tolerance_and_reports_speedup():
+    """What the trained network gains over the exact method at a stated
+    tolerance: a judged inference of 65536 spectra checks every 16th row against
+    the exact kernel and replaces the rows that miss tol.  Every judged row as
+    delivered is within tol of the exact spectrum, every other row is the
+    network's own; the spectra/s of this path and of the exact kernel are
+    reported (the full-size network, briefly trained)."""
     sur = Surrogate()
-    d = random_thicknesses(65536, seed=67)
-    for _ in range(2):
-        sur.infer(d)
-        sur.generate(d)
-    torch.cuda.synchronize()
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-    ev[0].record()
-    sur.infer(d)
-    ev[1].record()
-    ev[2].record()
-    sur.generate(d)
-    ev[3].record()
-    torch.cuda.synchronize()
-    t_mlp, t_exact = ev[0].elapsed_time(ev[1]), ev[2].elapsed_time(ev[3])
-    print(f"network {65536 / t_mlp * 1e3:.3e} spectra/s, exact {65536 / t_exact * 1e3:.3e} spectra/s")
-    assert t_mlp < t_exact
+    d, R = make_dataset(sur, 262144, seed=68)
+    train(sur, d, R, steps=1500, batch=8192, lr_max=1e-3, warmup=100)
+    del d, R
+    B, stride = 65536, 16
+    dt = random_thicknesses(B, seed=67)
+    exact = sur.generate(dt)
+    raw = sur.infer(dt)
+    rows = torch.arange(0, B, stride, device="cuda")
+    other = torch.ones(B, dtype=torch.bool, device="cuda")
+    other[rows] = False
+    stats = torch.zeros(2, dtype=torch.int32, device="cuda")
+    times = {}
+    for tol in (1e-3, 0.1):
+        out = sur.infer(dt, judge_fraction=1.0 / stride, tol=tol, stats=stats)
+        torch.cuda.synchronize()
+        assert float((out[rows] - exact[rows]).abs().max()) <= tol + 1e-7
+        assert torch.equal(out[other], raw[other])
+        n_fb = int(stats[0].item())
+        assert n_fb == int(((raw[rows] - exact[rows]).abs().amax(dim=1) > tol).sum().item())
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record()
+        sur.infer(dt, judge_fraction=1.0 / stride, tol=tol, out=out)
+        ev[1].record()
+        ev[2].record()
+        sur.generate(dt, exact)
+        ev[3].record()
+        torch.cuda.synchronize()
+        times[tol] = (ev[0].elapsed_time(ev[1]), ev[2].elapsed_time(ev[3]), n_fb)
+    for tol, (t_j, t_e, n_fb) in times.items():
+        print(f"tol {tol:g}: judged path {B / t_j * 1e3:.3e} spectra/s ({n_fb} of {B // stride} judged rows "
+              f"replaced), exact {B / t_e * 1e3:.3e} spectra/s, speed-up {t_e / t_j:.2f}")
+    assert sur.status() == abi.TMM_OK
