@@ -57,11 +57,13 @@ template <typename R> __device__ __forceinline__ void phase_cols(Cols<R> &c, Cx<
     c.y0 = cmul(emi, c.y0), c.y1 = cmul(epi, c.y1);
 }
 
-// (Re k_a / |k_a|)^2 / (Re k_b / |k_b|)^2, exactly 1 for real k_a, k_b.
+// (Re k_a / |k_a|)^2 / (Re k_b / |k_b|)^2, exactly 1 for real k_a, k_b; 0 when
+// medium b carries no flux (Re k_b = 0: evanescent), where nothing returns.
 template <typename R> __device__ __forceinline__ R back_ratio(Cx<R> ka, Cx<R> kb)
 {
     if (ka.y == R(0) && kb.y == R(0)) return R(1);
-    return (ka.x * ka.x * abs2(kb)) / (kb.x * kb.x * abs2(ka));
+    const R den = kb.x * kb.x * abs2(ka);
+    return den > R(0) ? (ka.x * ka.x * abs2(kb)) / den : R(0);
 }
 
 // R_f, R_b, T_f, T_b of the coherent block between incoherent media a < b,
@@ -199,6 +201,7 @@ __device__ __forceinline__ void inc_point(const StageA<R> *__restrict__ sa, cons
                                 : forward_root(Cx<R>{sa[a * TL + tl].d2x + q0sq, sa[a * TL + tl].n2y}, &absa);
         R Rf[2] = {R(0), R(0)}, Rb[2] = {R(0), R(0)}, Tf[2] = {R(0), R(0)}, Tb[2] = {R(0), R(0)};
         block_coeffs<R, POL>(sa, sb, TL, tl, a, b, q0sq, qa, n0, Rf, Rb, Tf, Tb);
+        if (b == e) Rb[0] = Rb[1] = Tb[0] = Tb[1] = R(0);  // nothing returns from the exit medium
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
             if (!(POL & (1 << k))) continue;
@@ -382,6 +385,9 @@ __device__ __forceinline__ void inc_point2(const StageA<float> *__restrict__ sa,
         }
         float Rf[2][2] = {}, Rb[2][2] = {}, Tf[2][2] = {}, Tb[2][2] = {};
         block_coeffs2<POL>(sa, sb, TL, tl, a, b, q0sq, qa, n0, Rf, Rb, Tf, Tb);
+        if (b == e[0])  // nothing returns from the exit medium
+#pragma unroll
+            for (int i = 0; i < 2; ++i) Rb[i][0] = Rb[i][1] = Tb[i][0] = Tb[i][1] = 0.f;
 #pragma unroll
         for (int i = 0; i < 2; ++i)
 #pragma unroll

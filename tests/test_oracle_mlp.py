@@ -18,7 +18,10 @@ from oracle import mlp
 def test_gelu_is_z_times_normal_cdf():
     z = torch.linspace(-8.0, 8.0, 16001, dtype=torch.float64)
     exact = z * torch.as_tensor(ndtr(z.numpy()))
-    assert float((mlp.gelu(z) - exact).abs().max()) < 1e-14
+    # torch's erf is accurate to a few ulp; its vectorised and scalar paths
+    # (chosen by how a tensor is split over threads) differ by up to ~16 ulp
+    # of GELU values near 8
+    assert float(((mlp.gelu(z) - exact) / z.abs().clamp(min=1.0)).abs().max()) < 1e-14
 
 
 def test_gelu_odd_part_is_half_identity():
