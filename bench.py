@@ -48,6 +48,7 @@ PEAK_F64_FLOPS = 1.25e12
 _CSRC = "paper_2111_13667_gb300/csrc/"
 KERNEL_SOURCES = {
     "fwd": [_CSRC + "tmm_fwd.cu", _CSRC + "tmm_device.cuh", _CSRC + "tmm_df64.cuh"],
+    "grad": [_CSRC + "tmm_grad.cu", _CSRC + "tmm_device.cuh"],
     "df64": [_CSRC + "tmm_fwd_df64.cu", _CSRC + "tmm_device.cuh", _CSRC + "tmm_df64.cuh", _CSRC + "tmm_df64x2.cuh"],
 }
 KERNELS = {
@@ -414,8 +415,33 @@ def bench_adjoint(args, torch, abi, W, flush, world, max_over_ranks):
         ws = ag.grad_workspace(prob)
         t = time_steps(lambda: abi.tmm_coh_grad(prob, Rt, m, dd, dn, ws), steps, 3, torch, flush)
         ms = max_over_ranks(sum(t) / len(t))
-        res[prec] = {"value": w.evals * world / (ms * 1e-3), "ms_per_step": ms, "steps": steps}
+        res[prec] = {"value": w.evals * world / (ms * 1e-3), "ms_per_step": ms, "steps": steps,
+                     "roofline": adjoint_roofline(prec, w, ms)}
     return res
+
+
+ADJOINT_FLOPS_PER_EVAL_INTERFACE = 3 * FLOPS_PER_EVAL_INTERFACE
+
+
+def adjoint_roofline(prec, w, ms):
+    """Merit and both gradients: the reverse sweep's standard count, three
+    times the forward's per eval and interface (right sweep, cotangent sweep
+    and the per-layer derivative terms), against the FP32 / FP64 peak; DRAM
+    traffic and issue fraction from the committed ncu figures of the same
+    kernel source (null when they do not describe it)."""
+    key = {"f32": "tmm_grad_kernel<float,66,true>", "f64": "tmm_grad_kernel<double,66,true>"}[prec]
+    work = ADJOINT_FLOPS_PER_EVAL_INTERFACE * (w.L_max + 1) * w.evals
+    peak = PEAK_F64_FLOPS if prec == "f64" else PEAK_F32_FLOPS
+    inputs = w.S * (w.L_max + 2) * 4 + w.table.size * 16 + w.S * w.L_max * 8 + w.R_target.size * 8
+    outputs = w.S * (2 * w.L_max + 1) * (8 if prec == "f64" else 4)
+    return {"bound": "alu", "unit": "TFLOP/s", "kernel": key, "achieved": work / (ms * 1e-3) / 1e12,
+            "peak": peak / 1e12, "frac": work / (ms * 1e-3) / peak,
+            "work": f"{ADJOINT_FLOPS_PER_EVAL_INTERFACE:g} flop per eval-interface x {w.L_max + 1} interfaces x "
+                    f"{w.evals} evals (three times the forward count)",
+            "algorithmic_bytes_per_launch": inputs + outputs,
+            "traffic": stored_traffic(key, "grad"),
+            "issue_frac": stored_profile(key, "issue_active_frac", "grad"),
+            "fma_pipe_frac": stored_profile(key, "fma_pipe_active_frac", "grad")}
 
 
 def bench_optimize(args, torch, abi, W, flush, world, max_over_ranks):
