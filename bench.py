@@ -275,18 +275,20 @@ def gpu_arm(args):
                           "f64": "native f64 arithmetic"}[prec]
         if sampler:
             entry["clocks"] = sampler.summary()
-        # end to end through the C ABI from pinned host buffers
+        # end to end through the C ABI from pinned host buffers: tmm_coh_batched_host
+        # copies the inputs in, runs 32 chunks and copies R, T back behind the kernels
         if not args.skip_e2e and prec in ("f64x", "f32"):
-            from paper_2111_13667_gb300.pipeline import HostPipeline
             h_in = {k: getattr(prob, k).cpu().pin_memory() for k in ("theta", "lam", "d", "table", "mat_idx")}
             hR = torch.empty(R.shape, dtype=R.dtype).pin_memory()
             hT = torch.empty(T.shape, dtype=T.dtype).pin_memory()
             del R, T
             torch.cuda.empty_cache()
-            pipe = HostPipeline(prob)
+            hp = abi.host_problem(prob, h_in)
+            n_chunks = 32
+            hws = torch.empty(abi.tmm_host_workspace_size(hp, n_chunks), dtype=torch.uint8, device=dev)
 
             def e2e_step():
-                pipe.run(h_in, hR, hT)
+                abi.tmm_coh_batched_host(hp, n_chunks, hws, hR, hT)
 
             e_steps = max(2, min(steps, 5))
             et = time_steps(e2e_step, e_steps, 2, torch, flush)
@@ -294,8 +296,9 @@ def gpu_arm(args):
             h2d = sum(v.numel() * v.element_size() for v in h_in.values())
             d2h = (hR.numel() * hR.element_size()) * 2
             entry["e2e"] = {"value": evals * world / (ems * 1e-3), "unit": "evals/s", "ms_per_step": ems,
-                            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": e_steps}
-            del pipe, hR, hT, h_in
+                            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": e_steps,
+                            "call": "tmm_coh_batched_host (C ABI), 32 chunks, pinned host buffers"}
+            del hws, hR, hT, h_in
         out[prec] = entry
         R = T = None
         del prob

@@ -182,6 +182,29 @@ TMM_API tmm_status tmm_coh_batched_ex(const tmm_problem *p, const tmm_launch_cfg
                               void *workspace, size_t workspace_bytes, void *R, void *T,
                               void *stream);
 
+/*
+ * R and T (Sec. 2, Eqs. 1-6) for a problem whose arrays live in HOST memory:
+ * the call copies the inputs to the device, evaluates the stacks in n_chunks
+ * contiguous chunks on `stream`, and copies every chunk's R and T back while
+ * the next chunks run (three device slots of chunk outputs; the copies go on
+ * a stream of their own).  Only the last chunk's copy is exposed.
+ *   p          as for tmm_coh_batched, but every array pointer is host memory
+ *              (page-locked memory lets the copies overlap the kernels;
+ *              pageable memory works, serialised); prec TMM_F64, TMM_F32,
+ *              TMM_F32D or TMM_F64X
+ *   R, T       host [P][S][n_theta][n_lambda] of the output type (T may be NULL)
+ *   n_chunks   1 .. S (else TMM_ERR_INVALID_ARG)
+ *   workspace  device, >= tmm_host_workspace_size(p, n_chunks) bytes,
+ *              256-byte aligned: the inputs' device copies and the output slots
+ * Asynchronous on `stream` like the other entry points: the host inputs must
+ * stay unchanged, and R, T are complete, only once `stream` has synchronised.
+ * The call creates and releases one stream and a few events of its own.
+ * Calls that share a workspace must be serialised by the caller.
+ */
+TMM_API tmm_status tmm_host_workspace_size(const tmm_problem *p, int32_t n_chunks, size_t *bytes);
+TMM_API tmm_status tmm_coh_batched_host(const tmm_problem *p, int32_t n_chunks, void *workspace,
+                                        size_t workspace_bytes, void *R, void *T, void *stream);
+
 /* Workspace bytes tmm_coh_batched_ex / tmm_coh_grad need for this problem. */
 TMM_API tmm_status tmm_workspace_size(const tmm_problem *p, const tmm_launch_cfg *cfg,
                               size_t *bytes);

@@ -37,6 +37,7 @@ EXPORTED = ("tmm_coh_batched", "tmm_coh_batched_ex", "tmm_workspace_size", "tmm_
             "tmm_coh_grad", "tmm_status_string", "tmm_last_cuda_error", "tmm_version",
             "tmm_probe_fma_rate", "tmm_gemm_bf16", "tmm_gemm_bf16_t", "tmm_coh_batched_noalloc",
             "tmm_optimize_workspace_size", "tmm_optimize_adam", "tmm_reward_workspace_size", "tmm_coh_reward",
+            "tmm_host_workspace_size", "tmm_coh_batched_host",
             "tmm_inc_batched", "tmm_absorption_batched", "tmm_field_profile", "tmm_pcoh_batched", "tmm_surrogate_create", "tmm_surrogate_destroy", "tmm_surrogate_outputs", "tmm_surrogate_parameters",
             "tmm_surrogate_generate", "tmm_surrogate_train_step", "tmm_surrogate_infer", "tmm_surrogate_layer",
             "tmm_surrogate_status", "tmm_surrogate_save", "tmm_surrogate_load")
@@ -113,6 +114,8 @@ def load(path: Optional[str] = None):
         lib.tmm_coh_batched_ex.argtypes = [P, C, vp, sz, vp, vp, vp]
         lib.tmm_workspace_size.argtypes = [P, C, ctypes.POINTER(sz)]
         lib.tmm_workspace_status.argtypes = [vp, vp]
+        lib.tmm_host_workspace_size.argtypes = [P, ctypes.c_int32, ctypes.POINTER(sz)]
+        lib.tmm_coh_batched_host.argtypes = [P, ctypes.c_int32, vp, sz, vp, vp, vp]
         lib.tmm_coh_grad.argtypes = [P, vp, vp, vp, vp, vp, sz, vp]
         lib.tmm_status_string.argtypes = [ctypes.c_int]
         lib.tmm_status_string.restype = ctypes.c_char_p
@@ -304,6 +307,39 @@ def tmm_coh_batched_noalloc(prob: DeviceProblem, cfg: Optional[TmmLaunchCfg], R:
     s = prob.struct()
     _check("tmm_coh_batched_noalloc", load().tmm_coh_batched_noalloc(
         ctypes.byref(s), ctypes.byref(cfg) if cfg else None, _ptr(R), _ptr(T), _stream(stream)))
+
+
+def tmm_host_workspace_size(prob_struct: TmmProblem, n_chunks: int) -> int:
+    n = ctypes.c_size_t(0)
+    _check("tmm_host_workspace_size", load().tmm_host_workspace_size(ctypes.byref(prob_struct), int(n_chunks),
+                                                                     ctypes.byref(n)))
+    return int(n.value)
+
+
+def host_problem(prob: "DeviceProblem", host: dict) -> TmmProblem:
+    """The tmm_problem of ``prob`` with its arrays replaced by the (pinned) host
+    tensors in ``host`` (keys: the DeviceProblem field names)."""
+    p = prob.struct()
+    hp = lambda t: None if t is None else t.data_ptr()
+    if prob.n_direct is not None:
+        p.n_direct = hp(host["n_direct"])
+    else:
+        p.mat_table, p.mat_idx = hp(host["table"]), hp(host["mat_idx"])
+    p.d, p.theta, p.lambda_ = hp(host["d"]), hp(host["theta"]), hp(host["lam"])
+    p.L_per_stack = hp(host.get("L_per_stack"))
+    return p
+
+
+def tmm_coh_batched_host(prob_struct: TmmProblem, n_chunks: int, workspace: torch.Tensor, R: torch.Tensor,
+                         T: Optional[torch.Tensor] = None, stream=None):
+    """Host-memory problem and outputs (``prob_struct`` from ``host_problem``);
+    ``R``, ``T`` host tensors, ``workspace`` a device tensor."""
+    for t in (R, T):
+        if t is not None and (t.is_cuda or not t.is_contiguous()):
+            raise ValueError("R, T must be contiguous host tensors")
+    _check("tmm_coh_batched_host", load().tmm_coh_batched_host(
+        ctypes.byref(prob_struct), int(n_chunks), _ptr(workspace), workspace.numel() * workspace.element_size(),
+        R.data_ptr(), None if T is None else T.data_ptr(), _stream(stream)))
 
 
 def tmm_workspace_status(workspace: torch.Tensor, stream=None) -> int:

@@ -307,17 +307,46 @@ def test_f64x_rejects_persistent_and_grad():
     assert e.value.status == abi.TMM_ERR_UNSUPPORTED
 
 
+@pytest.mark.parametrize("prec", ["f32", "f64x", "f32d"])
 @pytest.mark.parametrize("n_chunks", [1, 3, 8])
-def test_host_pipeline_matches_device_launch(n_chunks):
-    from paper_2111_13667_gb300.pipeline import HostPipeline
+def test_host_entry_matches_device_launch(prec, n_chunks):
+    # tmm_coh_batched_host: host inputs and outputs, chunked, copies behind the
+    # kernels -- the same kernels on the same values, so bit for bit the device
+    # launch; twice in a row on one workspace, pinned and pageable host memory
     w = W.dispersive(seed=20, S=53, L=9, n_lambda=37, n_theta=6)
-    prob = abi.to_device(w, "f32")
+    prob = abi.to_device(w, prec)
     Rd, Td = abi.coh_tmm(prob)
-    h_in = {k: getattr(prob, k).cpu().pin_memory() for k in ("theta", "lam", "d", "table", "mat_idx")}
-    hR = torch.zeros(Rd.shape, dtype=Rd.dtype).pin_memory()
-    hT = torch.zeros(Td.shape, dtype=Td.dtype).pin_memory()
-    pipe = HostPipeline(abi.to_device(w, "f32"), n_chunks=n_chunks)
-    for _ in range(2):
-        pipe.run(h_in, hR, hT)
+    for pinned in (True, False):
+        pin = (lambda t: t.pin_memory()) if pinned else (lambda t: t)
+        h_in = {k: pin(getattr(prob, k).cpu()) for k in ("theta", "lam", "d", "table", "mat_idx")}
+        hR = pin(torch.zeros(Rd.shape, dtype=Rd.dtype))
+        hT = pin(torch.zeros(Td.shape, dtype=Td.dtype))
+        hp = abi.host_problem(prob, h_in)
+        ws = torch.empty(abi.tmm_host_workspace_size(hp, n_chunks), dtype=torch.uint8, device="cuda")
+        for _ in range(2):
+            abi.tmm_coh_batched_host(hp, n_chunks, ws, hR, hT)
+            torch.cuda.synchronize()
+            assert torch.equal(hR, Rd.cpu()) and torch.equal(hT, Td.cpu())
+
+
+def test_host_entry_ragged_direct_index_and_checks():
+    w = W.ragged(seed=21, S=40, L_max=12, n_lambda=19, n_theta=5)
+    w2 = W.plain_fp64(seed=22, S=17, L=6)
+    for ww in (w, w2):
+        prob = abi.to_device(ww, "f64")
+        Rd, _ = abi.coh_tmm(prob, with_T=False)
+        keys = [k for k in ("theta", "lam", "d", "table", "mat_idx", "n_direct", "L_per_stack")
+                if getattr(prob, k) is not None]
+        h_in = {k: getattr(prob, k).cpu() for k in keys}
+        hp = abi.host_problem(prob, h_in)
+        ws = torch.empty(abi.tmm_host_workspace_size(hp, 4), dtype=torch.uint8, device="cuda")
+        hR = torch.zeros(Rd.shape, dtype=Rd.dtype)
+        abi.tmm_coh_batched_host(hp, 4, ws, hR, None)
         torch.cuda.synchronize()
-        assert torch.equal(hR, Rd.cpu()) and torch.equal(hT, Td.cpu())
+        assert torch.equal(hR, Rd.cpu())
+        with pytest.raises(abi.TmmError) as e:  # workspace too small
+            abi.tmm_coh_batched_host(hp, 4, ws[:256], hR, None)
+        assert e.value.status == abi.TMM_ERR_NOMEM
+        with pytest.raises(abi.TmmError) as e:  # more chunks than stacks
+            abi.tmm_coh_batched_host(hp, ww.S + 1, ws, hR, None)
+        assert e.value.status == abi.TMM_ERR_INVALID_ARG
