@@ -12,9 +12,11 @@
 //   ML = F_0 P_1 F_1 ... P_{j-1} F_{j-1}: the block left of layer j, both
 //        columns carried through the same sweep from the identity;
 //   per node: x_0 = ML P_j(d_j + D_k) y, R_k = |x_0[1] / x_0[0]|^2 and T_k
-//        from the dropped scales exactly as the forward kernel's T; the
-//        products ML_ab y_b are formed once, so a node costs its phase
-//        factors, one complex product and one complex fma per row.
+//        from the dropped scales exactly as the forward kernel's T.  The
+//        products ML_ab y_b are formed once and reduced to quadratic forms
+//        of |x_0[a]|^2 in the node's (cos 2 Re delta, sin 2 Re delta,
+//        e^{-2 Im delta}); T's scale factor does not depend on the node and is
+//        applied to the node sum once; node pairs +-D_k share one sincos.
 // The nodes come from a Sturm-sequence bisection of the Hermite Jacobi matrix
 // on the host; they are symmetric, so the kernel takes the non-negative half.
 #include <cuda_runtime.h>
@@ -140,6 +142,31 @@ __device__ __forceinline__ void rt_of(Cx<R> x0, Cx<R> x1, R scale, int e, R kapp
     const R ax0 = abs2(x0);
     Rv = abs2(x1) / ax0;
     Tv = kappa_out / kappa_in * ldexp_w(scale / ax0, e);
+}
+
+// A node's |x|^2 with x = A e^{-i t} + E B e^{+i t} (t = Re delta, E = e^{-2 Im delta}):
+//   |x|^2 = |A|^2 + E^2 |B|^2 + 2 E Re(A conj(B) e^{-2 i t}) = a + E (E b + cx cos 2t + cy sin 2t),
+// a quadratic form whose coefficients do not depend on the node.
+template <typename R> struct Quad {
+    R a, b, cx, cy;
+};
+template <typename R> __device__ __forceinline__ Quad<R> quad_of(Cx<R> A, Cx<R> B)
+{
+    return Quad<R>{abs2(A), abs2(B), R(2) * fma(A.x, B.x, A.y * B.y), R(2) * fma(A.y, B.x, -A.x * B.y)};
+}
+template <typename R> __device__ __forceinline__ R quad_at(const Quad<R> &q, R c2, R s2, R E)
+{
+    return fma(E, fma(E, q.b, fma(q.cx, c2, q.cy * s2)), q.a);
+}
+
+// cos 2t, sin 2t and E = e^{-2 Im delta} of layer jp at thickness / lambda = dl
+// (Im delta / 2 pi clamped like every layer's).
+template <typename R>
+__device__ __forceinline__ void twice_phase(R dl, Cx<R> q, R yi_max, R &c2, R &s2, R &E)
+{
+    const R y2 = R(2) * dl * q.x;
+    sincos_turn(y2 - rint_w(y2), &s2, &c2);
+    E = exp_m2_turn(fmin(dl * q.y, yi_max));
 }
 
 template <typename R, int POL>
@@ -297,34 +324,82 @@ __device__ __forceinline__ void pc_point(const StageA<R> *__restrict__ sa, const
     Cx<R> sA = {R(0), R(0)}, sB = sA, sC = sA, sD = sA, pA = sA, pB = sA, pC = sA, pD = sA;
     if (POL & 1) sA = cmul(sc00, s0), sB = cmul(sc01, s1), sC = cmul(sc10, s0), sD = cmul(sc11, s1);
     if (POL & 2) pA = cmul(pc00, p0), pB = cmul(pc01, p1), pC = cmul(pc10, p0), pD = cmul(pc11, p1);
-    // the nodes: layer jp's phase at thickness d_jp + sqrt(2) sigma x_k
-    R acc[4] = {R(0), R(0), R(0), R(0)};
+    const Quad<R> fs0 = quad_of(sA, sB), fs1 = quad_of(sC, sD), fp0 = quad_of(pA, pB), fp1 = quad_of(pC, pD);
+    // the nodes: layer jp's phase at thickness d_jp +- sqrt(2) sigma x_k.  A node's
+    // R is |x_0[1]|^2 / |x_0[0]|^2; its T is a node-independent factor times
+    // E / |x_0[0]|^2, so the sums carry w E / |x_0[0]|^2 and the factor (with the
+    // dropped scales) is applied once.
+    R aRs = R(0), aTs = R(0), aRp = R(0), aTp = R(0);
+    auto node = [&](R c2, R s2, R E, R w) {
+        if (POL & 1) {
+            const R wr = w / quad_at(fs0, c2, s2, E);
+            aRs = fma(wr, quad_at(fs1, c2, s2, E), aRs);
+            aTs = fma(wr, E, aTs);
+        }
+        if (POL & 2) {
+            const R wr = w / quad_at(fp0, c2, s2, E);
+            aRp = fma(wr, quad_at(fp1, c2, s2, E), aRp);
+            aTp = fma(wr, E, aTp);
+        }
+    };
+    // While no node's thickness or Im(delta) is clamped, delta is linear in the
+    // thickness: the nodes d_jp +- D turn the base (cos 2t_0, sin 2t_0) by
+    // +-2 dt (angle addition, one sincos per pair) and scale E_0 by
+    // e^{-+2 Im d delta}; otherwise each node's phase is taken on its own.
+    const R dl0 = dj * inv_lam, dmax = sig * nd.off[0] * inv_lam;
+    const bool rotate = dj >= sig * nd.off[0] && (dl0 + dmax) * qj.y <= yi_max;
+    R C0, S0, E0;
+    twice_phase(dl0, qj, yi_max, C0, S0, E0);
     for (int i = 0; i < nd.n_half; ++i) {
-        const int nsign = (nd.odd && i == nd.n_half - 1) ? 1 : 2;
-        for (int sgn = 0; sgn < nsign; ++sgn) {
-            const R D = sig * (sgn ? -nd.off[i] : nd.off[i]);
-            const R dl = fmax(dj + D, R(0)) * inv_lam;
-            const Step<R> st = phase_of(dl, qj, yi_max);
-            Cx<R> xs0 = {R(0), R(0)}, xs1 = xs0, xp0 = xs0, xp1 = xs0;
-            if (POL & 1) {
-                xs0 = cfma(sB, st.epi, cmul(sA, st.emi));
-                xs1 = cfma(sD, st.epi, cmul(sC, st.emi));
+        const bool both = !(nd.odd && i == nd.n_half - 1);
+        const R D = sig * nd.off[i], w = nd.w[i];
+        if (rotate) {
+            const R dl = D * inv_lam, y2 = R(2) * dl * qj.x;
+            R sd, cd;
+            sincos_turn(y2 - rint_w(y2), &sd, &cd);
+            const R a = C0 * cd, b = S0 * sd, c = S0 * cd, d = C0 * sd;
+            R Ep = E0, Em = E0;
+            if (qj.y != R(0)) Ep *= exp_m2_turn(dl * qj.y), Em *= exp_m2_turn(-dl * qj.y);
+            node(a - b, c + d, Ep, w);
+            if (both) node(a + b, c - d, Em, w);
+        } else {
+            for (int sg = 0; sg < (both ? 2 : 1); ++sg) {
+                R c2, s2, E;
+                twice_phase(fmax(dj + (sg ? -D : D), R(0)) * inv_lam, qj, yi_max, c2, s2, E);
+                node(c2, s2, E, w);
             }
-            if (POL & 2) {
-                xp0 = cfma(pB, st.epi, cmul(pA, st.emi));
-                xp1 = cfma(pD, st.epi, cmul(pC, st.emi));
-            }
-            R res[4] = {R(0), R(0), R(0), R(0)};
-            finish(xs0, xs1, xp0, xp1, Y + st.yi, es + els, ep + elp, res);
-#pragma unroll
-            for (int c = 0; c < 4; ++c) acc[c] = fma(nd.w[i], res[c], acc[c]);
         }
     }
-#pragma unroll
-    for (int c = 0; c < 4; ++c) out[c] = acc[c];
+    // T's factor: Eqs. 5-6 with the dropped scales, exp(-2 Im) of the other layers
+    R u = R(-2.0 * kTwoPi * kLog2e) * Y;
+    u = fmax(u, R(-1.0e6));
+    const R un = floor_w(u);
+    const R ys = Ps * (q0.x * q0.x) * exp2_w(u - un);
+    const int yn = (int)un;
+    out[0] = aRs;
+    out[1] = q_out.x / q0.x * ldexp_w(ys * aTs, e4 + eP + yn - 2 * (es + els));
+    out[2] = aRp;
+    out[3] = kout_p / kin_p * ldexp_w(ys * Pp * aTp, e4 + eP + ePp + yn - 2 * (ep + elp));
+    if (grazing) out[0] = out[2] = R(1), out[1] = out[3] = R(0);
 }
 
 // ---------------------------------------------------------------- FP32: two angles per thread
+
+// Quad on the two lanes.
+struct Quad2 {
+    float2 a, b, cx, cy;
+};
+__device__ __forceinline__ Quad2 quad_of2(const C2 &A, const C2 &B)
+{
+    const float2 two = bc2(2.f);
+    return Quad2{fma2(A.x, A.x, mul2(A.y, A.y)), fma2(B.x, B.x, mul2(B.y, B.y)),
+                 mul2(two, fma2(A.x, B.x, mul2(A.y, B.y))), mul2(two, sub2(mul2(A.y, B.x), mul2(A.x, B.y)))};
+}
+__device__ __forceinline__ float2 quad_at2(const Quad2 &q, float2 c2, float2 s2, float2 E)
+{
+    return fma2(E, fma2(E, q.b, fma2(q.cx, c2, mul2(q.cy, s2))), q.a);
+}
+
 // pc_point for the two angles in the lanes of st, ct (see tmm_fwd.cu): the
 // sweeps and the node products on paired lanes; the nodes' thicknesses are
 // the same for both lanes.  out[lane][{R_s, T_s, R_p, T_p}].
@@ -489,55 +564,91 @@ __device__ __forceinline__ void pc_point2(const StageA<float> *__restrict__ sa,
         interface_pair2(G0, neg2(G0.y), gr, ngry, cp.x0, cp.x1);
         interface_pair2(G0, neg2(G0.y), gr, ngry, cp.y0, cp.y1);
     }
-    // node-independent products: row a of x_0 = (ML_a0 y0) e^{-i delta} + (ML_a1 y1) e^{+i delta}
-    C2 sA = zero, sB = zero, sC = zero, sD = zero, pA = zero, pB = zero, pC = zero, pD = zero;
+    // node-independent products: row a of x_0 = (ML_a0 y0) e^{-i delta} + (ML_a1 y1) e^{+i delta},
+    // reduced to the quadratic forms of |x_0[a]|^2 (see Quad)
+    Quad2 fs0{}, fs1{}, fp0{}, fp1{};
     if (POL & 1) {
         const float2 n0y = neg2(s0.y), n1y = neg2(s1.y);
-        sA = cmul2(cs.x0, s0, n0y), sB = cmul2(cs.y0, s1, n1y);
-        sC = cmul2(cs.x1, s0, n0y), sD = cmul2(cs.y1, s1, n1y);
+        const C2 sA = cmul2(cs.x0, s0, n0y), sB = cmul2(cs.y0, s1, n1y);
+        const C2 sC = cmul2(cs.x1, s0, n0y), sD = cmul2(cs.y1, s1, n1y);
+        fs0 = quad_of2(sA, sB), fs1 = quad_of2(sC, sD);
     }
     if (POL & 2) {
         const float2 n0y = neg2(p0.y), n1y = neg2(p1.y);
-        pA = cmul2(cp.x0, p0, n0y), pB = cmul2(cp.y0, p1, n1y);
-        pC = cmul2(cp.x1, p0, n0y), pD = cmul2(cp.y1, p1, n1y);
+        const C2 pA = cmul2(cp.x0, p0, n0y), pB = cmul2(cp.y0, p1, n1y);
+        const C2 pC = cmul2(cp.x1, p0, n0y), pD = cmul2(cp.y1, p1, n1y);
+        fp0 = quad_of2(pA, pB), fp1 = quad_of2(pC, pD);
     }
-    float acc[2][4] = {};
+    // the nodes (see pc_point): sums of w |x_0[1]|^2 / |x_0[0]|^2 and w E / |x_0[0]|^2
+    float2 aRs = bc2(0.f), aTs = bc2(0.f), aRp = bc2(0.f), aTp = bc2(0.f);
+    auto node = [&](float2 c2, float2 s2, float2 E, float w) {
+        if (POL & 1) {
+            const float2 x0 = quad_at2(fs0, c2, s2, E);
+            const float2 wr = f2(w / x0.x, w / x0.y);
+            aRs = fma2(wr, quad_at2(fs1, c2, s2, E), aRs);
+            aTs = fma2(wr, E, aTs);
+        }
+        if (POL & 2) {
+            const float2 x0 = quad_at2(fp0, c2, s2, E);
+            const float2 wr = f2(w / x0.x, w / x0.y);
+            aRp = fma2(wr, quad_at2(fp1, c2, s2, E), aRp);
+            aTp = fma2(wr, E, aTp);
+        }
+    };
+    const float dl0 = dj * inv_lam, dmax = sig * nd.off[0] * inv_lam;
+    const bool rotate = dj >= sig * nd.off[0] && (dl0 + dmax) * fmaxf(qja.y, qjb.y) <= yi_max;
+    const bool lossy = qja.y != 0.f || qjb.y != 0.f;
+    float2 C0, S0, E0;
+    twice_phase(dl0, qja, yi_max, C0.x, S0.x, E0.x);
+    twice_phase(dl0, qjb, yi_max, C0.y, S0.y, E0.y);
     for (int i = 0; i < nd.n_half; ++i) {
-        const int nsign = (nd.odd && i == nd.n_half - 1) ? 1 : 2;
-        for (int sgn = 0; sgn < nsign; ++sgn) {
-            const float D = sig * (sgn ? -nd.off[i] : nd.off[i]);
-            const float dl = fmaxf(dj + D, 0.f) * inv_lam;
-            const Phase2 f = phase_pair(dl, qja, qjb, yi_max);
-            C2 xs0 = zero, xs1 = zero, xp0 = zero, xp1 = zero;
-            if (POL & 1) {
-                const C2 a = turn_minus(sA, f), b = turn_plus(sB, f), c = turn_minus(sC, f), d = turn_plus(sD, f);
-                xs0 = C2{add2(a.x, b.x), add2(a.y, b.y)};
-                xs1 = C2{add2(c.x, d.x), add2(c.y, d.y)};
+        const bool both = !(nd.odd && i == nd.n_half - 1);
+        const float D = sig * nd.off[i], w = nd.w[i];
+        if (rotate) {
+            const float dl = D * inv_lam;
+            const float ya = 2.f * dl * qja.x, yb = 2.f * dl * qjb.x;
+            float2 sd, cd;
+            sincos_turn(ya - rintf(ya), &sd.x, &cd.x);
+            sincos_turn(yb - rintf(yb), &sd.y, &cd.y);
+            const float2 a = mul2(C0, cd), b = mul2(S0, sd), c = mul2(S0, cd), d = mul2(C0, sd);
+            float2 Ep = E0, Em = E0;
+            if (lossy) {  // a lossless layer's E is E_0 at every node
+                const float2 ei = f2(dl * qja.y, dl * qjb.y);
+                Ep = mul2(E0, f2(exp_m2_turn(ei.x), exp_m2_turn(ei.y)));
+                Em = mul2(E0, f2(exp_m2_turn(-ei.x), exp_m2_turn(-ei.y)));
             }
-            if (POL & 2) {
-                const C2 a = turn_minus(pA, f), b = turn_plus(pB, f), c = turn_minus(pC, f), d = turn_plus(pD, f);
-                xp0 = C2{add2(a.x, b.x), add2(a.y, b.y)};
-                xp1 = C2{add2(c.x, d.x), add2(c.y, d.y)};
-            }
-#pragma unroll
-            for (int ln = 0; ln < 2; ++ln) {
-                float res[4] = {0.f, 0.f, 0.f, 0.f};
-                finish(ln, lane(xs0, ln), lane(xs1, ln), lane(xp0, ln), lane(xp1, ln),
-                       (ln ? Y.y : Y.x) + (ln ? f.yi.y : f.yi.x), (ln ? esb : esa) + (ln ? elsb : elsa),
-                       (ln ? epb : epa) + (ln ? elpb : elpa), res);
-#pragma unroll
-                for (int c = 0; c < 4; ++c) acc[ln][c] = fmaf(nd.w[i], res[c], acc[ln][c]);
+            node(sub2(a, b), add2(c, d), Ep, w);
+            if (both) node(add2(a, b), sub2(c, d), Em, w);
+        } else {
+            for (int sg = 0; sg < (both ? 2 : 1); ++sg) {
+                const float dl = fmaxf(dj + (sg ? -D : D), 0.f) * inv_lam;
+                float2 c2, s2, E;
+                twice_phase(dl, qja, yi_max, c2.x, s2.x, E.x);
+                twice_phase(dl, qjb, yi_max, c2.y, s2.y, E.y);
+                node(c2, s2, E, w);
             }
         }
     }
 #pragma unroll
-    for (int ln = 0; ln < 2; ++ln)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) out[ln][c] = acc[ln][c];
+    for (int ln = 0; ln < 2; ++ln) {
+        const float c0i = ln ? c0.y : c0.x;
+        const Cx<float> q_out = ln ? qob : qoa;
+        float u = float(-2.0 * kTwoPi * kLog2e) * (ln ? Y.y : Y.x);
+        u = fmaxf(u, -1.0e6f);
+        const float un = floorf(u);
+        const float ys = (ln ? Ps.y : Ps.x) * (c0i * c0i) * exp2f(u - un);
+        const int e = e4 + (ln ? ePb : ePa) + (int)un;
+        out[ln][0] = ln ? aRs.y : aRs.x;
+        out[ln][1] = q_out.x / c0i * ldexpf(ys * (ln ? aTs.y : aTs.x), e - 2 * (ln ? esb + elsb : esa + elsa));
+        out[ln][2] = ln ? aRp.y : aRp.x;
+        out[ln][3] = cmul(n2_out, conj(q_out)).x / (n0 * n0 * c0i) *
+                     ldexpf(ys * Pp * (ln ? aTp.y : aTp.x), e + ePp - 2 * (ln ? epb + elpb : epa + elpa));
+        if (n0 * (ln ? st.y : st.x) >= n0) out[ln][0] = out[ln][2] = 1.f, out[ln][1] = out[ln][3] = 0.f;  // grazing
+    }
 }
 
 template <typename R, int POL, bool WITH_T, bool PAIR>
-__global__ void __launch_bounds__(kPcThreads) tmm_pcoh_kernel(const tmm_problem p, const int32_t *__restrict__ layer,
+__global__ void __launch_bounds__(kPcThreads, 2) tmm_pcoh_kernel(const tmm_problem p, const int32_t *__restrict__ layer,
                                                                const R *__restrict__ sigma, const Nodes<R> nd, int TL,
                                                                int TT, int n_lt, int n_tt, R *__restrict__ Rout,
                                                                R *__restrict__ Tout)
