@@ -38,9 +38,10 @@
  *     limit only ever grows, so calls may come from several host threads at
  *     once, each with its own stream and buffers.  Two exceptions share state
  *     across calls: tmm_coh_batched_noalloc (one scratch array, see there) and
- *     the bf16 GEMMs of the surrogate and tmm_gemm_bf16(_t), which report an
- *     expired pipeline wait through one flag per device, so concurrent calls
- *     of those can attribute a timeout to the wrong call.
+ *     tmm_gemm_bf16(_t), which report an expired pipeline wait through one
+ *     flag per device, so concurrent calls of those can attribute a timeout
+ *     to the wrong call.  Each surrogate object has its own flag; calls on one
+ *     object are ordered by their stream.
  */
 #ifndef TMM_GB300_TMM_H
 #define TMM_GB300_TMM_H
@@ -436,7 +437,8 @@ typedef struct {
     const float *W, *b, *dW, *db;
 } tmm_surrogate_layer_view;
 TMM_API tmm_status tmm_surrogate_layer(const tmm_surrogate *s, int32_t i, tmm_surrogate_layer_view *out);
-/* TMM_OK, or TMM_ERR_TIMEOUT if a tensor-core pipeline wait expired (synchronises). */
+/* TMM_OK, or TMM_ERR_TIMEOUT if a tensor-core pipeline wait of this object's last
+ * generate / train_step / infer expired (its own flag; synchronises `stream`). */
 TMM_API tmm_status tmm_surrogate_status(tmm_surrogate *s, void *stream);
 /* Checkpoint: weights, Adam moments and step count (host file). */
 TMM_API tmm_status tmm_surrogate_save(tmm_surrogate *s, const char *path);

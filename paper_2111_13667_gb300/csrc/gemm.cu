@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
+#include <cstring>
 #include <mutex>
 
 #include "tcgen05_gemm.cuh"
@@ -70,6 +72,60 @@ static tmm_status launch_bn(const CUtensorMap &ta, const CUtensorMap &tb, int M,
     return check_launch();
 }
 
+// Pair form: clusters of two CTAs, one cluster per two SMs (or as many as
+// can be resident), each cluster a persistent worker over 256 x 256 tiles.
+template <int STAGES, int EPI_WARPS>
+static tmm_status launch_pair(const CUtensorMap &ta, const CUtensorMap &tb, int M, int N, int K, const EpiArgs &ep,
+                              cudaStream_t st)
+{
+    auto k = gemm_bf16_pair_kernel<STAGES, EPI_WARPS>;
+    constexpr size_t smem = PairSmem<STAGES, EPI_WARPS>::total;
+    tmm_status s = ensure_dynamic_smem(reinterpret_cast<const void *>(k), smem);
+    if (s != TMM_OK) return s;
+    DeviceInfo di;
+    s = device_info(&di);
+    if (s != TMM_OK) return s;
+    const long long tiles = (long long)((M + BM2 - 1) / BM2) * ((N + BN2 - 1) / BN2);
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.blockDim = dim3(PairSmem<STAGES, EPI_WARPS>::threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cfg.gridDim = dim3(2 * std::max(1, di.sms / 2));
+    int clusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&clusters, k, &cfg) != cudaSuccess || clusters < 1) {
+        (void)cudaGetLastError();
+        clusters = std::max(1, di.sms / 2);
+    }
+    const int pairs = (int)std::min<long long>(tiles, std::min(clusters, std::max(1, di.sms / 2)));
+    cfg.gridDim = dim3(2 * pairs);
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, k, ta, tb, M, N, K, ep);
+    if (e != cudaSuccess) return cuda_fail(e);
+    return check_launch();
+}
+
+// Which kernel.  The pair form streams the main loop faster (1726 against 1585
+// TFLOP/s at K = 4096 without an epilogue, M = 65536, N = 1024) and its
+// eight epilogue warps store fp32 faster; the one-CTA form's sixteen epilogue
+// warps run the GELU epilogues faster, which decides at K = 1024 (119.8 us
+// against 124.0).  So: the pair form for N >= 256 past one row block when the
+// epilogue stores fp32, K >= 2048 or N >= 2048; TMM_GEMM_FORM=single or =pair
+// forces one (tests compare the two on the same shapes).
+static bool use_pair(int M, int N, int K, int epi)
+{
+    const char *f = std::getenv("TMM_GEMM_FORM");
+    if (f && std::strcmp(f, "single") == 0) return false;
+    if (f && std::strcmp(f, "pair") == 0) return N >= 256;
+    const bool f32 = epi == EPI_F32 || epi == EPI_F32_CLAMP;
+    return N >= 256 && M > BM && (f32 || K >= 2048 || N >= 2048);
+}
+
 int *error_flag()
 {
     int *p = nullptr;
@@ -96,12 +152,19 @@ tmm_status gemm(const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *B, int ldb
     CUtensorMap ta, tb;
     tmm_status s = make_tmap(&ta, A, M, K, lda, BM);
     if (s != TMM_OK) return s;
+    if (use_pair(M, N, K, ep.epi)) {
+        s = make_tmap(&tb, B, N, K, ldb, BN2 / 2);
+        if (s != TMM_OK) return s;
+        return launch_pair<6, 8>(ta, tb, M, N, K, ep, st);
+    }
     s = make_tmap(&tb, B, N, K, ldb, BN);
     if (s != TMM_OK) return s;
     if (BN == 256) return launch_bn<256, 3>(ta, tb, M, N, K, ep, st);
     if (BN == 128) return launch_bn<128, 4>(ta, tb, M, N, K, ep, st);
     return launch_bn<64, 6>(ta, tb, M, N, K, ep, st);
 }
+
+tmm_status flag_status(const int *flag, cudaStream_t st);
 
 // Clear the wait-error flag (a set flag makes every later wait give up).
 tmm_status clear_error(cudaStream_t st)
@@ -112,10 +175,14 @@ tmm_status clear_error(cudaStream_t st)
     return e == cudaSuccess ? TMM_OK : cuda_fail(e);
 }
 
-tmm_status gemm_status(cudaStream_t st)
+tmm_status gemm_status(cudaStream_t st) { return flag_status(error_flag(), st); }
+
+// TMM_ERR_TIMEOUT if the device flag `flag` is set (synchronises st).
+tmm_status flag_status(const int *flag, cudaStream_t st)
 {
+    if (!flag) return TMM_ERR_CUDA;
     int h = 0;
-    cudaError_t e = cudaMemcpyFromSymbolAsync(&h, g_gemm_err, sizeof(int), 0, cudaMemcpyDeviceToHost, st);
+    cudaError_t e = cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e != cudaSuccess) return cuda_fail(e);
     e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e);

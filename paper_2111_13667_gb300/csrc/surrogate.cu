@@ -29,6 +29,7 @@ tmm_status gemm(const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *B, int ldb
                 cudaStream_t st);
 tmm_status clear_error(cudaStream_t st);
 tmm_status gemm_status(cudaStream_t st);
+tmm_status flag_status(const int *flag, cudaStream_t st);
 int *error_flag();
 }  // namespace gemm
 
@@ -254,6 +255,7 @@ struct tmm_surrogate {
     float2 *jn = nullptr;
     int *jcount = nullptr;
     unsigned int *jmax = nullptr;
+    int *err = nullptr;  // this object's GEMM pipeline-timeout flag (device)
 };
 
 namespace {
@@ -364,6 +366,7 @@ tmm_status forward(tmm_surrogate *s, const float *d, int B, float *out, bool tra
     int K = KIN;
     for (int i = 0; i < s->depth; ++i) {
         gemm::EpiArgs ep{};
+        ep.err = s->err;
         ep.epi = gemm::EPI_GELU;
         ep.bias = s->layers[i].b;
         ep.out_bf = s->H[i];
@@ -377,6 +380,7 @@ tmm_status forward(tmm_surrogate *s, const float *d, int B, float *out, bool tra
         K = s->hidden;
     }
     gemm::EpiArgs ep{};
+    ep.err = s->err;
     ep.epi = train ? gemm::EPI_F32 : gemm::EPI_F32_CLAMP;
     ep.bias = s->layers[s->depth].b;
     ep.out_f32 = out;
@@ -434,7 +438,9 @@ TMM_API tmm_status tmm_surrogate_create(const tmm_surrogate_desc *desc, tmm_surr
     for (int j = 0; j < s->L + 2; ++j) row[j] = make_float2((float)desc->n_media[2 * j], (float)desc->n_media[2 * j + 1]);
     std::vector<float> th(desc->theta, desc->theta + s->nt), la(desc->lambda, desc->lambda + s->nl);
     if ((st = dalloc(s->owned, &s->n_row, row.size())) != TMM_OK || (st = dalloc(s->owned, &s->theta, th.size())) != TMM_OK ||
-        (st = dalloc(s->owned, &s->lam, la.size())) != TMM_OK) {
+        (st = dalloc(s->owned, &s->lam, la.size())) != TMM_OK || (st = dalloc(s->owned, &s->err, 1)) != TMM_OK ||
+        cudaMemset(s->err, 0, sizeof(int)) != cudaSuccess) {
+        if (st == TMM_OK) st = cuda_fail(cudaGetLastError());
         tmm_surrogate_destroy(s);
         return st;
     }
@@ -519,7 +525,7 @@ TMM_API tmm_status tmm_surrogate_train_step(tmm_surrogate *s, const float *d, co
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     tmm_status r = ensure_batch(s, B);
     if (r != TMM_OK) return r;
-    if ((r = gemm::clear_error(st)) != TMM_OK) return r;
+    if (cudaMemsetAsync(s->err, 0, sizeof(int), st) != cudaSuccess) return cuda_fail(cudaGetLastError());
     if ((r = forward(s, d, B, s->Y, true, st)) != TMM_OK) return r;
     float *lossp = loss ? loss : s->loss_tmp;
     cudaMemsetAsync(lossp, 0, sizeof(float), st);
@@ -530,12 +536,14 @@ TMM_API tmm_status tmm_surrogate_train_step(tmm_surrogate *s, const float *d, co
     Layer &head = s->layers[s->depth];
     {
         gemm::EpiArgs ep{};
+        ep.err = s->err;
         ep.epi = gemm::EPI_F32;
         ep.out_f32 = head.dW;
         ep.ldo = head.K;
         if ((r = gemm::gemm(s->dYT, B, s->HT[s->depth - 1], B, head.N, head.K, B, ep, st)) != TMM_OK) return r;
         if ((r = colsum(s, s->dY, B, head.N, head.db, st)) != TMM_OK) return r;
         gemm::EpiArgs eb{};
+        eb.err = s->err;
         eb.epi = gemm::EPI_DGELU;
         eb.aux = s->Z[s->depth - 1];
         eb.out_bf = s->dZ[0];
@@ -549,6 +557,7 @@ TMM_API tmm_status tmm_surrogate_train_step(tmm_surrogate *s, const float *d, co
         Layer &l = s->layers[i];
         const __nv_bfloat16 *inT = i == 0 ? s->X0T : s->HT[i - 1];
         gemm::EpiArgs ep{};
+        ep.err = s->err;
         ep.epi = gemm::EPI_F32;
         ep.out_f32 = l.dW;
         ep.ldo = l.K;
@@ -556,6 +565,7 @@ TMM_API tmm_status tmm_surrogate_train_step(tmm_surrogate *s, const float *d, co
         if ((r = colsum(s, s->dZ[cur], B, l.N, l.db, st)) != TMM_OK) return r;
         if (i > 0) {
             gemm::EpiArgs eb{};
+            eb.err = s->err;
             eb.epi = gemm::EPI_DGELU;
             eb.aux = s->Z[i - 1];
             eb.out_bf = s->dZ[cur ^ 1];
@@ -590,7 +600,7 @@ TMM_API tmm_status tmm_surrogate_infer(tmm_surrogate *s, const float *d, int32_t
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     tmm_status r = ensure_batch(s, B);
     if (r != TMM_OK) return r;
-    if ((r = gemm::clear_error(st)) != TMM_OK) return r;
+    if (cudaMemsetAsync(s->err, 0, sizeof(int), st) != cudaSuccess) return cuda_fail(cudaGetLastError());
     if ((r = forward(s, d, B, R, false, st)) != TMM_OK) return r;
     if (judge_fraction <= 0.0f) return TMM_OK;
     const int stride = std::max(1, (int)lroundf(1.0f / judge_fraction));
@@ -628,7 +638,7 @@ TMM_API tmm_status tmm_surrogate_layer(const tmm_surrogate *s, int32_t i, tmm_su
 TMM_API tmm_status tmm_surrogate_status(tmm_surrogate *s, void *stream)
 {
     if (!s) return TMM_ERR_INVALID_ARG;
-    return gemm::gemm_status(static_cast<cudaStream_t>(stream));
+    return gemm::flag_status(s->err, static_cast<cudaStream_t>(stream));
 }
 
 TMM_API tmm_status tmm_surrogate_save(tmm_surrogate *s, const char *path)

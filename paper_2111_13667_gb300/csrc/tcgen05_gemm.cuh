@@ -16,6 +16,13 @@
 //     per-warp staging buffer with 16-byte stores.
 // Every wait is bounded by %globaltimer: on expiry the CTA records an error,
 // drains what it issued (again bounded), frees its tensor memory and returns.
+//
+// The pair form (gemm_bf16_pair_kernel) runs the same roles on a cluster of
+// two CTAs that share one 256 x 256 tile: each CTA loads its own 128 rows of A
+// and its own 128 rows of B, and the even CTA issues tcgen05.mma.cta_group::2
+// (M = 256, N = 256), which reads both CTAs' shared memory and writes rows
+// 0-127 of the accumulator into its own tensor memory and rows 128-255 into
+// its peer's.  Per SM this halves the B bytes through shared memory per flop.
 #pragma once
 
 #include <cuda.h>
@@ -88,9 +95,11 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
 }
 
 // Bounded wait: false if the phase did not complete within kWaitNs or another
-// thread of the grid already reported an error.
+// thread of the grid already reported an error.  The clock is read only once
+// the first test has failed (most waits of the pipeline find the phase done).
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, const int *err)
 {
+    if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = globaltimer();
     for (uint32_t it = 0;; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
@@ -166,37 +175,92 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// 16 consecutive fp32 columns of this thread's TMEM lane.
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16])
-{
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// 32 consecutive fp32 columns of this thread's TMEM lane.
+// 32 consecutive fp32 columns of this thread's TMEM lane: one load, one wait.
+// The wait names the loaded registers as operands, so no use of them can be
+// scheduled before it.
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float v[32])
 {
-    tmem_ld16(taddr, v);
-    tmem_ld16(taddr + 16, v + 16);
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+                 :
+                 : "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// GELU, erf form: gelu(z) = z Phi(z) = 0.5 z (1 + erf(z / sqrt 2)), with CUDA's
-// erff; its derivative Phi(z) + z phi(z), phi(z) = exp(-z^2 / 2) / sqrt(2 pi).
-__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
-__device__ __forceinline__ float gelu_grad(float z)
+// GELU, erf form: gelu(z) = z Phi(z) = 0.5 z (1 + erf(z / sqrt 2)) = relu(z) -
+// (a / sqrt 2) erfc(a) with a = |z| / sqrt 2; its derivative Phi(z) + z phi(z),
+// Phi(z) = 1 - erfc(a) / 2 for z >= 0 and erfc(a) / 2 below, phi(z) =
+// exp(-a^2) / sqrt(2 pi).  erfc(a) is the Chebyshev-fitted form of Press et
+// al. (Numerical Recipes, 2nd ed., Sec. 6.2):
+//   erfc(a) = t exp(-a^2 + P(t)),  t = 1 / (1 + a / 2),  P of degree 9,
+// whose relative error is below 1.1e-7 for every a >= 0 (8e-6 evaluated in
+// FP32 up to a = 9, where exp(-a^2) is near FP32's range end): far below the
+// bf16 rounding of the outputs, in both tails.  Two lanes at a time on the
+// paired FP32 pipes; rcp and ex2 are the MUFU approximations.
+__device__ __forceinline__ float rcp_mufu(float v)
 {
-    const float cdf = 0.5f * (1.0f + erff(z * 0.70710678118654752f));
-    const float pdf = 0.39894228040143268f * __expf(-0.5f * z * z);
-    return fmaf(z, pdf, cdf);
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
 }
+__device__ __forceinline__ float ex2_mufu(float v)
+{
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+}
+__device__ __forceinline__ float2 g2(float a) { return make_float2(a, a); }
+
+// a >= 0 on both lanes: (erfc(a), exp(-a^2)) per lane; the second only when wanted
+template <bool WANT_G>
+__device__ __forceinline__ float2 erfc_pair(float2 a, float2 *g)
+{
+    constexpr float kL2e = 1.4426950408889634f;
+    const float2 t = make_float2(rcp_mufu(fmaf(0.5f, a.x, 1.0f)), rcp_mufu(fmaf(0.5f, a.y, 1.0f)));
+    float2 p = __ffma2_rn(t, g2(0.17087277f), g2(-0.82215223f));
+    p = __ffma2_rn(t, p, g2(1.48851587f));
+    p = __ffma2_rn(t, p, g2(-1.13520398f));
+    p = __ffma2_rn(t, p, g2(0.27886807f));
+    p = __ffma2_rn(t, p, g2(-0.18628806f));
+    p = __ffma2_rn(t, p, g2(0.09678418f));
+    p = __ffma2_rn(t, p, g2(0.37409196f));
+    p = __ffma2_rn(t, p, g2(1.00002368f));
+    p = __ffma2_rn(t, p, g2(-1.26551223f));
+    const float2 na = __fmul2_rn(a, g2(-kL2e));           // -a log2(e)
+    const float2 x = __ffma2_rn(na, a, __fmul2_rn(p, g2(kL2e)));  // (-a^2 + P) log2(e)
+    if (WANT_G) {
+        const float2 y = __fmul2_rn(na, a);
+        *g = make_float2(ex2_mufu(y.x), ex2_mufu(y.y));
+    }
+    return __fmul2_rn(t, make_float2(ex2_mufu(x.x), ex2_mufu(x.y)));
+}
+
+__device__ __forceinline__ float2 gelu2(float2 z)
+{
+    const float2 a = __fmul2_rn(make_float2(fabsf(z.x), fabsf(z.y)), g2(0.70710678118654752f));
+    const float2 h = __fmul2_rn(__fmul2_rn(a, g2(0.70710678118654752f)), erfc_pair<false>(a, nullptr));
+    return make_float2(fmaxf(z.x, 0.0f) - h.x, fmaxf(z.y, 0.0f) - h.y);
+}
+
+__device__ __forceinline__ float2 gelu_grad2(float2 z)
+{
+    const float2 a = __fmul2_rn(make_float2(fabsf(z.x), fabsf(z.y)), g2(0.70710678118654752f));
+    float2 g;
+    const float2 E = erfc_pair<true>(a, &g);
+    const float2 half = __fmul2_rn(E, g2(0.5f));
+    const float2 cdf = make_float2(z.x >= 0.0f ? 1.0f - half.x : half.x, z.y >= 0.0f ? 1.0f - half.y : half.y);
+    return __ffma2_rn(__fmul2_rn(z, g2(0.39894228040143268f)), g, cdf);
+}
+
+__device__ __forceinline__ float gelu(float z) { return gelu2(make_float2(z, z)).x; }
+__device__ __forceinline__ float gelu_grad(float z) { return gelu_grad2(make_float2(z, z)).x; }
 
 // Two floats to one word of two bf16 (round to nearest even), a in the low half.
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b)
@@ -222,7 +286,7 @@ struct GemmSmem {
     static constexpr size_t a_bytes = (size_t)BM * BK * 2;
     static constexpr size_t b_bytes = (size_t)BN * BK * 2;
     static constexpr size_t ring = STAGES * (a_bytes + b_bytes);
-    static constexpr size_t stage = (size_t)kEpiWarps * 32 * 33 * 4;  // per warp 32 x 33 floats (16-byte multiple)
+    static constexpr size_t stage = (size_t)kEpiWarps * 32 * 32 * 4;  // per warp 32 x 32 floats
     static constexpr size_t bars = (2 * STAGES + 5) * 8 + 16;
     static constexpr size_t total = 1024 + ring + stage + bars;  // + alignment slack
 };
@@ -376,7 +440,10 @@ __device__ __forceinline__ void epilogue_chunk_vec(const EpiArgs &ep, const floa
             __syncwarp();
         }
 #pragma unroll
-        for (int i = 0; i < 16; ++i) w[i] = pack_bf16(gelu(bf_lo(w[i])), gelu(bf_hi(w[i])));
+        for (int i = 0; i < 16; ++i) {
+            const float2 y = gelu2(make_float2(bf_lo(w[i]), bf_hi(w[i])));
+            w[i] = pack_bf16(y.x, y.y);
+        }
         write_bf_chunk(ep, w, stg, row0, col0, M, lane);
     } else {  // EPI_DGELU: y = acc * gelu'(aux); rows of aux read through the staging buffer
         {
@@ -399,14 +466,17 @@ __device__ __forceinline__ void epilogue_chunk_vec(const EpiArgs &ep, const floa
         }
         __syncwarp();
 #pragma unroll
-        for (int i = 0; i < 16; ++i)
-            zw[i] = pack_bf16(v[2 * i] * gelu_grad(bf_lo(zw[i])), v[2 * i + 1] * gelu_grad(bf_hi(zw[i])));
+        for (int i = 0; i < 16; ++i) {
+            const float2 d = __fmul2_rn(make_float2(v[2 * i], v[2 * i + 1]), gelu_grad2(make_float2(bf_lo(zw[i]), bf_hi(zw[i]))));
+            zw[i] = pack_bf16(d.x, d.y);
+        }
         write_bf_chunk(ep, zw, stg, row0, col0, M, lane);
     }
 }
 
 // Any chunk (ragged columns, unaligned outputs): element by element, staged
-// through shared memory (stride 33 floats) for row-wise stores.
+// through shared memory (rows of 32 floats, element i of row r at i ^ r, so
+// that row writes and column reads meet no bank conflicts) for row-wise stores.
 __device__ __forceinline__ void epilogue_chunk_scalar(const EpiArgs &ep, const float (&v)[32], float *stg, int row0,
                                                       int n0c, int M, int N, int lane)
 {
@@ -430,7 +500,7 @@ __device__ __forceinline__ void epilogue_chunk_scalar(const EpiArgs &ep, const f
         }
         if (ep.out_bfT && in)  // lanes hold consecutive rows: coalesced
             ep.out_bfT[(long long)col * ep.ldoT + row] = __float2bfloat16(y);
-        stg[lane * 33 + i] = y;
+        stg[lane * 32 + (i ^ lane)] = y;
     }
     __syncwarp();
     const int col = n0c + lane;
@@ -438,7 +508,7 @@ __device__ __forceinline__ void epilogue_chunk_scalar(const EpiArgs &ep, const f
         for (int r = 0; r < 32; ++r) {
             const int rr = row0 + r;
             if (rr >= M) break;
-            const float y = stg[r * 33 + lane];
+            const float y = stg[r * 32 + (lane ^ r)];
             const long long o = (long long)rr * ep.ldo + col;
             if (ep.epi == EPI_F32 || ep.epi == EPI_F32_CLAMP) ep.out_f32[o] = y;
             else ep.out_bf[o] = __float2bfloat16(y);
@@ -537,8 +607,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            // MMA issuer
+            // MMA issuer; stage descriptors are the ring's base descriptor plus the
+            // offset / 16 (the start-address field; shared memory is below 256 KB)
             constexpr uint32_t idesc = instr_desc_bf16(BM, BN);
+            const uint64_t a_desc0 = smem_desc_sw128(sA), b_desc0 = smem_desc_sw128(sB);
             long long it = 0;
             int t = 0;
             bool ok = true;
@@ -559,8 +631,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                     tc_fence_after();
 #pragma unroll
                     for (int k = 0; k < BK / UMMA_K; ++k) {
-                        const uint64_t ad = smem_desc_sw128(sA + s * L::a_bytes + k * UMMA_K * 2);
-                        const uint64_t bd = smem_desc_sw128(sB + s * L::b_bytes + k * UMMA_K * 2);
+                        const uint64_t ad = a_desc0 + (uint64_t)((s * L::a_bytes + k * UMMA_K * 2) >> 4);
+                        const uint64_t bd = b_desc0 + (uint64_t)((s * L::b_bytes + k * UMMA_K * 2) >> 4);
                         umma_bf16(d, ad, bd, idesc, (kb | k) != 0 ? 1u : 0u);
                     }
                     umma_commit(&empty[s]);
@@ -578,7 +650,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         constexpr int kSliceCols = BN / kSlices;  // warps with half >= kSlices have no columns
         static_assert(kSliceCols % 32 == 0, "column slice must hold whole 32-column chunks");
         const int ew = warp - 2, q = warp & 3, half = ew >> 2;
-        float *stg = stg_all + ew * (32 * 33);
+        float *stg = stg_all + ew * (32 * 32);
         int t = 0;
         for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++t) {
             const int buf = t & 1, use = t >> 1;
@@ -607,6 +679,291 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     if (warp == 1) {
         __syncwarp();  // lanes 1..31 waited while lane 0 issued: reconverge for the aligned dealloc
         tmem_dealloc(tmem, kCols);
+    }
+}
+
+// ---- pair-CTA form ---------------------------------------------------------
+
+constexpr int BM2 = 2 * BM;  // rows of a pair tile, 128 per CTA
+constexpr int BN2 = 256;     // columns of a pair tile; B rows 128 per CTA
+
+__device__ __forceinline__ uint32_t cluster_ctarank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t cluster_id_x()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t cluster_count_x()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
+    return r;
+}
+
+// The shared::cluster address of this CTA's shared variable at addr in CTA rank.
+__device__ __forceinline__ uint32_t mapa_shared(uint32_t addr, uint32_t rank)
+{
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+    return r;
+}
+
+// Every thread of both CTAs (not .aligned: warps may arrive diverged).
+__device__ __forceinline__ void cluster_sync()
+{
+    asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+}
+
+// Arrive on an mbarrier given by its shared::cluster address (own or peer CTA).
+// Default (CTA-scope release) semantics: the arrival only has to follow the
+// arriving warp's tcgen05.ld reads, which tcgen05.wait::ld and
+// tcgen05.fence::before_thread_sync order; a cluster-scope release would also
+// wait for the warp's global stores in flight.
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cluster.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// TMA load into this CTA's shared memory whose completion is counted on the
+// mbarrier at the shared::cluster address bar (the even CTA's).
+__device__ __forceinline__ void tma_load_2d_pair(void *dst, const CUtensorMap *map, uint32_t bar, int c0, int c1)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, "
+        "%3}], [%4];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void umma_bf16_pair(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                               uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+        ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// Completion of this thread's MMAs arrives once on the mbarrier at the same
+// offset in both CTAs of the pair.
+__device__ __forceinline__ void umma_commit_pair_both(uint64_t *bar)
+{
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+            smem_u32(bar)),
+        "h"((uint16_t)3)
+        : "memory");
+}
+
+// ... on this CTA's mbarrier only.
+__device__ __forceinline__ void umma_commit_pair_own(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+// One warp of each CTA of the pair, collectively: the same columns in both.
+__device__ __forceinline__ void tmem_alloc_pair(uint32_t *slot, uint32_t ncols)
+{
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc_pair(uint32_t taddr, uint32_t ncols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+template <int STAGES, int EPI_WARPS>
+struct PairSmem {
+    static constexpr int threads = 64 + 32 * EPI_WARPS;            // producer warp, MMA warp, epilogue warps
+    static constexpr size_t a_bytes = (size_t)BM * BK * 2;         // this CTA's 128 rows of A
+    static constexpr size_t b_bytes = (size_t)(BN2 / 2) * BK * 2;  // this CTA's 128 rows of B
+    static constexpr size_t ring = STAGES * (a_bytes + b_bytes);
+    static constexpr size_t stage = (size_t)EPI_WARPS * 32 * 32 * 4;
+    static constexpr size_t bars = (2 * STAGES + 5) * 8 + 16;
+    static constexpr size_t total = 1024 + ring + stage + bars;
+};
+
+// Persistent pair kernel: clusters of two CTAs (ranks 0 and 1); pair tiles of
+// 256 x 256 dealt round-robin to the clusters.  Roles as in gemm_bf16_kernel;
+// in addition:
+//   full[s]      even CTA only: its producer's arrive with the byte count of
+//                both CTAs' loads, which all complete on it;
+//   empty[s]     both CTAs: the MMA's commit, multicast;
+//   acc_full[b]  both CTAs: the MMA's commit, multicast;
+//   acc_empty[b] even CTA only: one arrival per epilogue warp of either CTA;
+//   done         even CTA: the MMA drain.
+// All waits are CTA-scope acquires: what crosses CTAs is ordered by TMA
+// completion, tcgen05.commit and the tcgen05 fences, not by memory ordering.
+// A cluster barrier after set-up (barriers initialised, tensor memory
+// allocated) and one before teardown (no CTA leaves while its peer may still
+// read its shared memory, write its tensor memory or signal its barriers).
+template <int STAGES, int EPI_WARPS>
+__global__ void __launch_bounds__(PairSmem<STAGES, EPI_WARPS>::threads, 1)
+    gemm_bf16_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M,
+                          int N, int K, EpiArgs ep)
+{
+    using L = PairSmem<STAGES, EPI_WARPS>;
+    static_assert(EPI_WARPS % 4 == 0, "whole TMEM lane quarters");
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t *sA = smem;
+    uint8_t *sB = smem + STAGES * L::a_bytes;
+    float *stg_all = reinterpret_cast<float *>(smem + L::ring);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + L::ring + L::stage);
+    uint64_t *empty = full + STAGES;
+    uint64_t *acc_full = empty + STAGES;
+    uint64_t *acc_empty = acc_full + 2;
+    uint64_t *done = acc_empty + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
+    int *s_fail = reinterpret_cast<int *>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = cluster_ctarank();
+    const bool even = rank == 0;
+    const int pair = (int)cluster_id_x(), n_pairs = (int)cluster_count_x();
+    const int n_tiles = (N + BN2 - 1) / BN2;
+    const int tiles = ((M + BM2 - 1) / BM2) * n_tiles;
+    const int nkb = (K + BK - 1) / BK;
+    constexpr uint32_t kCols = 2 * BN2;  // two accumulators of 256 columns: all 512
+
+    if (threadIdx.x == 0) {
+        *s_fail = 0;
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], 2 * EPI_WARPS);
+        }
+        mbar_init(done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) tmem_alloc_pair(tmem_slot, kCols);
+    tc_fence_before();
+    cluster_sync();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    auto fail = [&]() {
+        *s_fail = 1;
+        atomicExch(ep.err, 1);  // the peer's waits give up at once
+    };
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // producer: this CTA's halves of A and B; completion on the even CTA's full[s]
+            const uint32_t full_even = mapa_shared(smem_u32(full), 0);
+            long long it = 0;
+            bool ok = true;
+            for (int tile = pair; tile < tiles && ok; tile += n_pairs) {
+                const int m0 = (tile / n_tiles) * BM2 + (int)rank * BM;
+                const int n0 = (tile % n_tiles) * BN2 + (int)rank * (BN2 / 2);
+                for (int kb = 0; kb < nkb; ++kb, ++it) {
+                    const int s = (int)(it % STAGES);
+                    if (it >= STAGES && !mbar_wait(&empty[s], (uint32_t)(((it / STAGES) - 1) & 1), ep.err)) {
+                        ok = false;
+                        break;
+                    }
+                    if (even) mbar_expect_tx(&full[s], (uint32_t)(2 * (L::a_bytes + L::b_bytes)));
+                    tma_load_2d_pair(sA + s * L::a_bytes, &tmA, full_even + 8u * s, kb * BK, m0);
+                    tma_load_2d_pair(sB + s * L::b_bytes, &tmB, full_even + 8u * s, kb * BK, n0);
+                }
+            }
+            // the even CTA sees both CTAs' loads land: none is in flight at teardown
+            if (even)
+                for (long long j = (it > STAGES ? it - STAGES : 0); j < it; ++j)
+                    if (!mbar_wait(&full[j % STAGES], (uint32_t)((j / STAGES) & 1), ep.err)) ok = false;
+            if (!ok) fail();
+        }
+    } else if (warp == 1) {
+        if (even && lane == 0) {
+            // MMA issuer for the pair (descriptors as in gemm_bf16_kernel)
+            constexpr uint32_t idesc = instr_desc_bf16(BM2, BN2);
+            const uint64_t a_desc0 = smem_desc_sw128(sA), b_desc0 = smem_desc_sw128(sB);
+            long long it = 0;
+            int t = 0;
+            bool ok = true;
+            for (int tile = pair; tile < tiles && ok; tile += n_pairs, ++t) {
+                const int buf = t & 1, use = t >> 1;
+                if (t >= 2 && !mbar_wait(&acc_empty[buf], (uint32_t)((use - 1) & 1), ep.err)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d = tmem + (uint32_t)(buf * BN2);
+                for (int kb = 0; kb < nkb; ++kb, ++it) {
+                    const int s = (int)(it % STAGES);
+                    if (!mbar_wait(&full[s], (uint32_t)((it / STAGES) & 1), ep.err)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+#pragma unroll
+                    for (int k = 0; k < BK / UMMA_K; ++k) {
+                        const uint64_t ad = a_desc0 + (uint64_t)((s * L::a_bytes + k * UMMA_K * 2) >> 4);
+                        const uint64_t bd = b_desc0 + (uint64_t)((s * L::b_bytes + k * UMMA_K * 2) >> 4);
+                        umma_bf16_pair(d, ad, bd, idesc, (kb | k) != 0 ? 1u : 0u);
+                    }
+                    umma_commit_pair_both(&empty[s]);
+                }
+                if (ok) umma_commit_pair_both(&acc_full[buf]);
+            }
+            umma_commit_pair_own(done);
+            if (!mbar_wait(done, 0, ep.err)) ok = false;
+            if (!ok) fail();
+        }
+    } else {
+        // epilogue warps: this CTA's 128 rows of the pair tile
+        constexpr int kSlices = (EPI_WARPS / 4) < (BN2 / 32) ? (EPI_WARPS / 4) : (BN2 / 32);
+        constexpr int kSliceCols = BN2 / kSlices;
+        static_assert(kSliceCols % 32 == 0, "column slice must hold whole 32-column chunks");
+        const int ew = warp - 2, q = warp & 3, half = ew >> 2;
+        float *stg = stg_all + ew * (32 * 32);
+        const uint32_t acc_empty_even = mapa_shared(smem_u32(acc_empty), 0);
+        int t = 0;
+        for (int tile = pair; tile < tiles; tile += n_pairs, ++t) {
+            const int buf = t & 1, use = t >> 1;
+            const bool have =
+                __all_sync(0xffffffffu, mbar_wait(&acc_full[buf], (uint32_t)(use & 1), ep.err));
+            if (!have) {
+                if (lane == 0) fail();
+                break;
+            }
+            tc_fence_after();
+            const int m0 = (tile / n_tiles) * BM2 + (int)rank * BM, n0 = (tile % n_tiles) * BN2;
+            const int row0 = m0 + q * 32;
+#pragma unroll 1
+            for (int c = half * kSliceCols; half < kSlices && c < (half + 1) * kSliceCols; c += 32) {
+                float v[32];
+                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * BN2 + c), v);
+                epilogue_chunk(ep, v, stg, row0, n0 + c, M, N, lane);
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive_cluster(acc_empty_even + 8u * buf);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && *s_fail) atomicExch(ep.err, 1);
+    tc_fence_before();
+    cluster_sync();
+    tc_fence_after();
+    if (warp == 1) {
+        __syncwarp();
+        tmem_dealloc_pair(tmem, kCols);
     }
 }
 

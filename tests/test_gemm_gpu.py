@@ -1,6 +1,10 @@
 """The tcgen05 bf16 GEMM (surrogate building block) against an fp32 matmul of
 the same bf16 operands, for every fused epilogue, tile width, ragged M and N
-(the element-wise tail path) and the transposed copy of the training step."""
+(the element-wise tail path) and the transposed copy of the training step;
+the one-CTA and pair-CTA (cta_group::2) kernels on the same shapes; the GELU
+and GELU' epilogues against the correctly rounded bf16 of the exact function."""
+import math
+
 import pytest
 import torch
 
@@ -105,3 +109,62 @@ def test_gemm_transposed_entry_rejects_bad_arguments():
     outT = torch.empty(64, 64, dtype=torch.bfloat16, device="cuda")
     with pytest.raises(RuntimeError):
         abi.tmm_gemm_bf16_t(A, B, bias, 0, torch.empty(64, 64, device="cuda"), None, outT)
+
+
+FORMS = ["single", "pair"]
+
+
+@pytest.mark.parametrize("M,N,K", [(256, 256, 64), (300, 1024, 256), (1000, 512, 192), (4096, 1024, 1024)])
+def test_pair_and_single_forms_agree_bit_for_bit(M, N, K, monkeypatch):
+    A, B, bias = operands(M, N, K, M + 3 * N)
+    outs = []
+    for form in FORMS:
+        monkeypatch.setenv("TMM_GEMM_FORM", form)
+        o32 = torch.empty(M, N, device="cuda")
+        abi.tmm_gemm_bf16(A, B, bias, 0, o32)
+        ob = torch.empty(M, N, dtype=torch.bfloat16, device="cuda")
+        aux = torch.empty(M, N, dtype=torch.bfloat16, device="cuda")
+        abi.tmm_gemm_bf16(A, B, bias, 1, ob, aux)
+        od = torch.empty(M, N, dtype=torch.bfloat16, device="cuda")
+        abi.tmm_gemm_bf16(A, B, None, 2, od, aux)
+        outs.append((o32, ob, aux, od))
+    ref = A.float() @ B.float().T + bias
+    assert (outs[0][0] - ref).abs().max().item() <= 1e-4 * max(1.0, ref.abs().max().item())
+    for a, b in zip(*outs):
+        assert torch.equal(a, b)
+
+
+def _bf16_ulp(x):
+    """One bf16 unit in the last place of |x| (x != 0), as float64."""
+    e = torch.floor(torch.log2(x.abs()))
+    return torch.pow(2.0, e - 7)
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_gelu_epilogues_round_the_exact_function(form, monkeypatch):
+    """B = I passes each bf16 z of A through the accumulator exactly, so the
+    GELU epilogue's output is its bf16 of GELU(z) and the GELU' epilogue's (with
+    A = 1) its bf16 of GELU'(aux).  Against the exact functions (fp64, erfc form,
+    accurate in both tails): within one bf16 unit everywhere, and the correctly
+    rounded value for all but near-ties."""
+    monkeypatch.setenv("TMM_GEMM_FORM", form)
+    M, N = 2048, 256
+    z = torch.linspace(-12.0, 12.0, M * N, dtype=torch.float64)
+    z = z[torch.randperm(M * N, generator=torch.Generator().manual_seed(3))].reshape(M, N)
+    zb = z.to(torch.bfloat16)
+    eye = torch.eye(N, dtype=torch.bfloat16, device="cuda")
+    out = torch.empty(M, N, dtype=torch.bfloat16, device="cuda")
+    aux = torch.empty(M, N, dtype=torch.bfloat16, device="cuda")
+    abi.tmm_gemm_bf16(zb.cuda(), eye, None, 1, out, aux)
+    assert torch.equal(aux.cpu(), zb)
+    x = zb.double()
+    g = 0.5 * x * torch.special.erfc(-x / math.sqrt(2.0))
+    dg = 0.5 * torch.special.erfc(-x / math.sqrt(2.0)) + x * torch.exp(-0.5 * x * x) / math.sqrt(2.0 * math.pi)
+    ones = torch.ones(M, N, dtype=torch.bfloat16, device="cuda")
+    dout = torch.empty(M, N, dtype=torch.bfloat16, device="cuda")
+    abi.tmm_gemm_bf16(ones, eye, None, 2, dout, aux)
+    for got, ref in ((out.cpu().double(), g), (dout.cpu().double(), dg)):
+        nz = ref != 0
+        assert bool(((got - ref).abs()[nz] <= _bf16_ulp(ref[nz])).all())
+        exact = (got == ref.to(torch.bfloat16).double()).double().mean().item()
+        assert exact >= 0.999, exact
