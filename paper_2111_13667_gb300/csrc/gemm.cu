@@ -59,7 +59,8 @@ template <int BN, int STAGES>
 static tmm_status launch_bn(const CUtensorMap &ta, const CUtensorMap &tb, int M, int N, int K, const EpiArgs &ep,
                             cudaStream_t st)
 {
-    auto k = gemm_bf16_kernel<BN, STAGES>;
+    auto k = ep.epi == EPI_GELU || ep.epi == EPI_DGELU ? gemm_bf16_kernel<BN, STAGES, FAM_GELU>
+                                                       : gemm_bf16_kernel<BN, STAGES, FAM_F32>;
     constexpr size_t smem = GemmSmem<BN, STAGES>::total;
     tmm_status s = ensure_dynamic_smem(reinterpret_cast<const void *>(k), smem);
     if (s != TMM_OK) return s;
@@ -78,7 +79,8 @@ template <int STAGES, int EPI_WARPS>
 static tmm_status launch_pair(const CUtensorMap &ta, const CUtensorMap &tb, int M, int N, int K, const EpiArgs &ep,
                               cudaStream_t st)
 {
-    auto k = gemm_bf16_pair_kernel<STAGES, EPI_WARPS>;
+    auto k = ep.epi == EPI_GELU || ep.epi == EPI_DGELU ? gemm_bf16_pair_kernel<STAGES, EPI_WARPS, FAM_GELU>
+                                                       : gemm_bf16_pair_kernel<STAGES, EPI_WARPS, FAM_F32>;
     constexpr size_t smem = PairSmem<STAGES, EPI_WARPS>::total;
     tmm_status s = ensure_dynamic_smem(reinterpret_cast<const void *>(k), smem);
     if (s != TMM_OK) return s;

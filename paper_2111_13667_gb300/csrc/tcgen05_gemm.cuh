@@ -175,6 +175,24 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
+// 16 consecutive fp32 columns of this thread's TMEM lane (load, then a wait that
+// names the loaded registers, so no use of them is scheduled before it).
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16])
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
+                 :
+                 : "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 // 32 consecutive fp32 columns of this thread's TMEM lane: one load, one wait.
 // The wait names the loaded registers as operands, so no use of them can be
 // scheduled before it.
@@ -304,14 +322,6 @@ struct GemmSmem {
 __device__ __forceinline__ int stg_f32(int r, int g) { return r * 32 + 4 * (g ^ (r & 7)); }
 __device__ __forceinline__ int stg_bf(int r, int g) { return r * 16 + 4 * (g ^ ((r >> 1) & 3)); }
 
-// this lane's row of 16 bf16 pairs into the staging buffer
-__device__ __forceinline__ void stage_row_bf(uint32_t *stg, const uint32_t (&w)[16], int lane)
-{
-#pragma unroll
-    for (int g = 0; g < 4; ++g)
-        *reinterpret_cast<uint4 *>(stg + stg_bf(lane, g)) = make_uint4(w[4 * g], w[4 * g + 1], w[4 * g + 2], w[4 * g + 3]);
-}
-
 // staged bf16 rows -> out[row0 + r][col0 ...]: four lanes per 64-byte row
 __device__ __forceinline__ void store_rows_bf(const uint32_t *stg, __nv_bfloat16 *out, int ldo, int row0, int col0,
                                               int M, int lane)
@@ -385,21 +395,7 @@ __device__ __forceinline__ float4 bias4(const float *bias, int col0, int j)
     return bias ? __ldg(reinterpret_cast<const float4 *>(bias + col0) + j) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
 }
 
-// bf16 packed outputs of a full 32-column chunk: row-major out, optional transposed copy
-__device__ __forceinline__ void write_bf_chunk(const EpiArgs &ep, const uint32_t (&y)[16], uint32_t *stg, int row0,
-                                               int col0, int M, int lane)
-{
-    stage_row_bf(stg, y, lane);
-    __syncwarp();
-    store_rows_bf(stg, ep.out_bf, ep.ldo, row0, col0, M, lane);
-    if (ep.out_bfT) {
-        if (row0 + 32 <= M) store_cols_bf(stg, ep.out_bfT, ep.ldoT, row0, col0, lane);
-        else store_cols_bf_tail(stg, ep.out_bfT, ep.ldoT, row0, col0, M, lane);
-    }
-    __syncwarp();
-}
-
-// Full 32-column chunk, 16-byte aligned outputs.
+// Full 32-column chunk, 16-byte aligned outputs, fp32 epilogues.
 template <int EPI>
 __device__ __forceinline__ void epilogue_chunk_vec(const EpiArgs &ep, const float (&v)[32], uint32_t *stg, int row0,
                                                    int col0, int M, int lane)
@@ -425,52 +421,6 @@ __device__ __forceinline__ void epilogue_chunk_vec(const EpiArgs &ep, const floa
                     *reinterpret_cast<const float4 *>(stg + stg_f32(r, g));
         }
         __syncwarp();
-    } else if (EPI == EPI_GELU) {
-        uint32_t w[16];  // bf16 pre-activations, then activations
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const float4 b = bias4(ep.bias, col0, j);
-            w[2 * j] = pack_bf16(v[4 * j] + b.x, v[4 * j + 1] + b.y);
-            w[2 * j + 1] = pack_bf16(v[4 * j + 2] + b.z, v[4 * j + 3] + b.w);
-        }
-        if (ep.aux) {
-            stage_row_bf(stg, w, lane);
-            __syncwarp();
-            store_rows_bf(stg, ep.aux, ep.ldo, row0, col0, M, lane);
-            __syncwarp();
-        }
-#pragma unroll
-        for (int i = 0; i < 16; ++i) {
-            const float2 y = gelu2(make_float2(bf_lo(w[i]), bf_hi(w[i])));
-            w[i] = pack_bf16(y.x, y.y);
-        }
-        write_bf_chunk(ep, w, stg, row0, col0, M, lane);
-    } else {  // EPI_DGELU: y = acc * gelu'(aux); rows of aux read through the staging buffer
-        {
-            const int g = lane & 3;
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int r = 8 * k + (lane >> 2);
-                uint4 t = make_uint4(0u, 0u, 0u, 0u);
-                if (row0 + r < M)
-                    t = __ldg(reinterpret_cast<const uint4 *>(ep.aux + (long long)(row0 + r) * ep.ldo + col0 + 8 * g));
-                *reinterpret_cast<uint4 *>(stg + stg_bf(r, g)) = t;
-            }
-        }
-        __syncwarp();
-        uint32_t zw[16];
-#pragma unroll
-        for (int g = 0; g < 4; ++g) {
-            const uint4 t = *reinterpret_cast<const uint4 *>(stg + stg_bf(lane, g));
-            zw[4 * g] = t.x, zw[4 * g + 1] = t.y, zw[4 * g + 2] = t.z, zw[4 * g + 3] = t.w;
-        }
-        __syncwarp();
-#pragma unroll
-        for (int i = 0; i < 16; ++i) {
-            const float2 d = __fmul2_rn(make_float2(v[2 * i], v[2 * i + 1]), gelu_grad2(make_float2(bf_lo(zw[i]), bf_hi(zw[i]))));
-            zw[i] = pack_bf16(d.x, d.y);
-        }
-        write_bf_chunk(ep, zw, stg, row0, col0, M, lane);
     }
 }
 
@@ -517,17 +467,102 @@ __device__ __forceinline__ void epilogue_chunk_scalar(const EpiArgs &ep, const f
     __syncwarp();
 }
 
-__device__ __forceinline__ void epilogue_chunk(const EpiArgs &ep, const float (&v)[32], float *stg, int row0, int n0c,
-                                               int M, int N, int lane)
+// this lane's 8 words (16 bf16 columns, half h of a 32-column chunk) into its staged row
+__device__ __forceinline__ void stage_half_bf(uint32_t *stg, const uint32_t (&w)[8], int lane, int h)
 {
-    if (ep.vec && n0c + 32 <= N) {
-        uint32_t *sw = reinterpret_cast<uint32_t *>(stg);
-        switch (ep.epi) {
-        case EPI_F32: epilogue_chunk_vec<EPI_F32>(ep, v, sw, row0, n0c, M, lane); return;
-        case EPI_F32_CLAMP: epilogue_chunk_vec<EPI_F32_CLAMP>(ep, v, sw, row0, n0c, M, lane); return;
-        case EPI_GELU: epilogue_chunk_vec<EPI_GELU>(ep, v, sw, row0, n0c, M, lane); return;
-        default: epilogue_chunk_vec<EPI_DGELU>(ep, v, sw, row0, n0c, M, lane); return;
+    *reinterpret_cast<uint4 *>(stg + stg_bf(lane, 2 * h)) = make_uint4(w[0], w[1], w[2], w[3]);
+    *reinterpret_cast<uint4 *>(stg + stg_bf(lane, 2 * h + 1)) = make_uint4(w[4], w[5], w[6], w[7]);
+}
+
+// GELU and GELU' epilogues of a full 32-column chunk with 16-byte aligned
+// outputs, in two halves of 16 columns read from TMEM one after the other, so
+// that only half a chunk's values and activations are live at a time.  The
+// warp's 4 KB staging buffer holds two 32-row bf16 tiles: the pre-activations
+// (aux) and the outputs.
+template <int EPI>
+__device__ __forceinline__ void epilogue_chunk_halves(const EpiArgs &ep, uint32_t taddr, uint32_t *stg, int row0,
+                                                      int col0, int M, int lane)
+{
+    uint32_t *stA = stg, *stO = stg + 32 * 16;
+    if (EPI == EPI_DGELU) {  // rows of aux through the staging buffer (coalesced loads)
+        const int g = lane & 3;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int r = 8 * k + (lane >> 2);
+            uint4 t = make_uint4(0u, 0u, 0u, 0u);
+            if (row0 + r < M)
+                t = __ldg(reinterpret_cast<const uint4 *>(ep.aux + (long long)(row0 + r) * ep.ldo + col0 + 8 * g));
+            *reinterpret_cast<uint4 *>(stA + stg_bf(r, g)) = t;
         }
+        __syncwarp();
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        float v[16];
+        tmem_ld16(taddr + 16 * h, v);
+        uint32_t w[8];
+        if (EPI == EPI_GELU) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float4 b = bias4(ep.bias, col0 + 16 * h, j);
+                w[2 * j] = pack_bf16(v[4 * j] + b.x, v[4 * j + 1] + b.y);
+                w[2 * j + 1] = pack_bf16(v[4 * j + 2] + b.z, v[4 * j + 3] + b.w);
+            }
+            if (ep.aux) stage_half_bf(stA, w, lane, h);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const float2 y = gelu2(make_float2(bf_lo(w[i]), bf_hi(w[i])));
+                w[i] = pack_bf16(y.x, y.y);
+            }
+        } else {
+            const uint4 t0 = *reinterpret_cast<const uint4 *>(stA + stg_bf(lane, 2 * h));
+            const uint4 t1 = *reinterpret_cast<const uint4 *>(stA + stg_bf(lane, 2 * h + 1));
+            const uint32_t z[8] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const float2 d = __fmul2_rn(make_float2(v[2 * i], v[2 * i + 1]),
+                                            gelu_grad2(make_float2(bf_lo(z[i]), bf_hi(z[i]))));
+                w[i] = pack_bf16(d.x, d.y);
+            }
+        }
+        stage_half_bf(stO, w, lane, h);
+    }
+    __syncwarp();
+    if (EPI == EPI_GELU && ep.aux) store_rows_bf(stA, ep.aux, ep.ldo, row0, col0, M, lane);
+    store_rows_bf(stO, ep.out_bf, ep.ldo, row0, col0, M, lane);
+    if (ep.out_bfT) {
+        if (row0 + 32 <= M) store_cols_bf(stO, ep.out_bfT, ep.ldoT, row0, col0, lane);
+        else store_cols_bf_tail(stO, ep.out_bfT, ep.ldoT, row0, col0, M, lane);
+    }
+    __syncwarp();
+}
+
+// Epilogue families: the kernels are instantiated per family so that each
+// carries only its own epilogue code (and register pressure).
+enum EpiFamily : int {
+    FAM_F32 = 0,   // EPI_F32, EPI_F32_CLAMP
+    FAM_GELU = 1,  // EPI_GELU, EPI_DGELU
+};
+__host__ __device__ constexpr int family_of(int epi) { return (epi == EPI_GELU || epi == EPI_DGELU) ? FAM_GELU : FAM_F32; }
+
+// One 32-column chunk of the accumulator at TMEM address taddr.
+template <int FAM>
+__device__ __forceinline__ void epilogue_chunk_tmem(const EpiArgs &ep, uint32_t taddr, float *stg, int row0, int n0c,
+                                                    int M, int N, int lane)
+{
+    if (FAM == FAM_GELU && ep.vec && n0c + 32 <= N) {
+        uint32_t *sw = reinterpret_cast<uint32_t *>(stg);
+        if (ep.epi == EPI_GELU) epilogue_chunk_halves<EPI_GELU>(ep, taddr, sw, row0, n0c, M, lane);
+        else epilogue_chunk_halves<EPI_DGELU>(ep, taddr, sw, row0, n0c, M, lane);
+        return;
+    }
+    float v[32];
+    tmem_ld32(taddr, v);
+    if (FAM == FAM_F32 && ep.vec && n0c + 32 <= N) {
+        uint32_t *sw = reinterpret_cast<uint32_t *>(stg);
+        if (ep.epi == EPI_F32) epilogue_chunk_vec<EPI_F32>(ep, v, sw, row0, n0c, M, lane);
+        else epilogue_chunk_vec<EPI_F32_CLAMP>(ep, v, sw, row0, n0c, M, lane);
+        return;
     }
     epilogue_chunk_scalar(ep, v, stg, row0, n0c, M, N, lane);
 }
@@ -537,7 +572,7 @@ __device__ __forceinline__ void epilogue_chunk(const EpiArgs &ep, const float (&
 // memory (2 x BN columns) so the epilogue of one tile overlaps the MMAs of the
 // next.  Barriers: full/empty per ring stage (TMA <-> MMA), acc_full/acc_empty
 // per accumulator (MMA <-> epilogue), done (MMA drain before teardown).
-template <int BN, int STAGES>
+template <int BN, int STAGES, int FAM>
 __global__ void __launch_bounds__(kGemmThreads, 1)
     gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int N,
                      int K, EpiArgs ep)
@@ -664,9 +699,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             const int row0 = m0 + q * 32;
 #pragma unroll 1
             for (int c = half * kSliceCols; half < kSlices && c < (half + 1) * kSliceCols; c += 32) {
-                float v[32];
-                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * BN + c), v);
-                epilogue_chunk(ep, v, stg, row0, n0 + c, M, N, lane);
+                epilogue_chunk_tmem<FAM>(ep, tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * BN + c), stg, row0,
+                                    n0 + c, M, N, lane);
             }
             tc_fence_before();
             __syncwarp();
@@ -809,7 +843,7 @@ struct PairSmem {
 // A cluster barrier after set-up (barriers initialised, tensor memory
 // allocated) and one before teardown (no CTA leaves while its peer may still
 // read its shared memory, write its tensor memory or signal its barriers).
-template <int STAGES, int EPI_WARPS>
+template <int STAGES, int EPI_WARPS, int FAM>
 __global__ void __launch_bounds__(PairSmem<STAGES, EPI_WARPS>::threads, 1)
     gemm_bf16_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M,
                           int N, int K, EpiArgs ep)
@@ -947,9 +981,8 @@ __global__ void __launch_bounds__(PairSmem<STAGES, EPI_WARPS>::threads, 1)
             const int row0 = m0 + q * 32;
 #pragma unroll 1
             for (int c = half * kSliceCols; half < kSlices && c < (half + 1) * kSliceCols; c += 32) {
-                float v[32];
-                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * BN2 + c), v);
-                epilogue_chunk(ep, v, stg, row0, n0 + c, M, N, lane);
+                epilogue_chunk_tmem<FAM>(ep, tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * BN2 + c), stg, row0,
+                                    n0 + c, M, N, lane);
             }
             tc_fence_before();
             __syncwarp();
