@@ -649,7 +649,7 @@ def bench_surrogate(args, torch, abi, W, flush, world, max_over_ranks):
             "speedup_network_only": ms_e / ms_n,
             "speedup_at_max_err_1e-3": ms_e / full["ms_per_step"],
             "speedup_judge_fraction_1_16": ms_e / judged["judge_fraction_0.0625"]["ms_per_step"],
-            "roofline": {"bound": "tensor", "kernel": "gemm_bf16_kernel (7 GEMMs of one inference)",
+            "roofline": {"bound": "tensor", "kernel": "gemm_bf16_kernel + gemm_bf16_pair_kernel (7 GEMMs of one inference)",
                          "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                          "peak_source": peak_src, "work": f"{flops / 1e12:.3f} TFLOP per 65536-spectrum batch"},
             "status": status, "steps": steps}
