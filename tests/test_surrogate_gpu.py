@@ -154,3 +154,21 @@ def test_judged_inference_delivers_tolerance_and_reports_speedup():
         print(f"tol {tol:g}: judged path {B / t_j * 1e3:.3e} spectra/s ({n_fb} of {B // stride} judged rows "
               f"replaced), exact {B / t_e * 1e3:.3e} spectra/s, speed-up {t_e / t_j:.2f}")
     assert sur.status() == abi.TMM_OK
+
+
+def test_two_surrogates_on_two_streams_keep_their_own_status():
+    """Each surrogate object owns its GEMM timeout flag: two objects driven on
+    two streams each report their own TMM_OK, and their results equal the same
+    calls made one after the other on the default stream."""
+    a, b = small(seed=5), small(seed=6)
+    d = random_thicknesses(512, seed=71)
+    sa, sb = torch.cuda.Stream(), torch.cuda.Stream()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(sa):
+        ra = a.infer(d, stream=sa)
+    with torch.cuda.stream(sb):
+        rb = b.infer(d, stream=sb)
+    torch.cuda.synchronize()
+    assert a.status() == abi.TMM_OK and b.status() == abi.TMM_OK
+    assert torch.equal(ra, a.infer(d)) and torch.equal(rb, b.infer(d))
+    assert not torch.equal(ra, rb)
