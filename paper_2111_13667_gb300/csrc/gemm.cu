@@ -8,6 +8,8 @@
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
+#include <tuple>
+#include <vector>
 
 #include "tcgen05_gemm.cuh"
 #include "tmm_internal.h"
@@ -73,6 +75,32 @@ static tmm_status launch_bn(const CUtensorMap &ta, const CUtensorMap &tb, int M,
     return check_launch();
 }
 
+// Two-CTA clusters of kernel fn that fit on the current device at once, asked
+// once per (kernel, device): the query costs more than a launch.
+static int resident_clusters(const void *fn, const cudaLaunchConfig_t &cfg, int fallback)
+{
+    static std::mutex mu;
+    static std::vector<std::tuple<const void *, int, int>> cache;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return fallback;
+    }
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        for (const auto &e : cache)
+            if (std::get<0>(e) == fn && std::get<1>(e) == dev) return std::get<2>(e);
+    }
+    int clusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&clusters, fn, &cfg) != cudaSuccess || clusters < 1) {
+        (void)cudaGetLastError();
+        clusters = fallback;
+    }
+    std::lock_guard<std::mutex> lock(mu);
+    cache.emplace_back(fn, dev, clusters);
+    return clusters;
+}
+
 // Pair form: clusters of two CTAs, one cluster per two SMs (or as many as
 // can be resident), each cluster a persistent worker over 256 x 256 tiles.
 template <int STAGES, int EPI_WARPS>
@@ -100,11 +128,7 @@ static tmm_status launch_pair(const CUtensorMap &ta, const CUtensorMap &tb, int 
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     cfg.gridDim = dim3(2 * std::max(1, di.sms / 2));
-    int clusters = 0;
-    if (cudaOccupancyMaxActiveClusters(&clusters, k, &cfg) != cudaSuccess || clusters < 1) {
-        (void)cudaGetLastError();
-        clusters = std::max(1, di.sms / 2);
-    }
+    const int clusters = resident_clusters(reinterpret_cast<const void *>(k), cfg, std::max(1, di.sms / 2));
     const int pairs = (int)std::min<long long>(tiles, std::min(clusters, std::max(1, di.sms / 2)));
     cfg.gridDim = dim3(2 * pairs);
     const cudaError_t e = cudaLaunchKernelEx(&cfg, k, ta, tb, M, N, K, ep);
