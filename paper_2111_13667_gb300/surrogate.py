@@ -163,13 +163,35 @@ def train(sur: Surrogate, d: torch.Tensor, R: torch.Tensor, steps: int, batch: i
     return TrainReport(steps, batch, time.perf_counter() - t0, first or float("nan"), float(loss.item()))
 
 
+def _gemm_shape(M, N, K, epilogue, repeat, seed=2):
+    """`repeat` launches of one tcgen05 GEMM on random bf16 operands (profiling
+    helper; the kernel form follows the library's choice unless TMM_GEMM_FORM is set)."""
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    A = (torch.randn(M, K, generator=g) / K ** 0.5).to(torch.bfloat16).cuda()
+    B = torch.randn(N, K, generator=g).to(torch.bfloat16).cuda()
+    bias = torch.randn(N, generator=g).cuda()
+    f32 = epilogue in (0, 3)
+    out = torch.empty(M, N, device="cuda", dtype=torch.float32 if f32 else torch.bfloat16)
+    aux = None if epilogue == 1 else (torch.randn(M, N, generator=g).to(torch.bfloat16).cuda() if epilogue == 2 else None)
+    for _ in range(repeat):
+        abi.tmm_gemm_bf16(A, B, None if epilogue == 2 else bias, epilogue, out, aux)
+    torch.cuda.synchronize()
+
+
 def _main():
     import argparse
-    ap = argparse.ArgumentParser(description="run surrogate inference (profiling helper)")
+    ap = argparse.ArgumentParser(description="run surrogate inference, or one GEMM shape (profiling helper)")
     ap.add_argument("--infer-batch", type=int, default=65536)
     ap.add_argument("--repeat", type=int, default=4)
+    ap.add_argument("--gemm", type=int, nargs=3, metavar=("M", "N", "K"), default=None,
+                    help="time one GEMM shape instead of the inference")
+    ap.add_argument("--epilogue", type=int, default=1, help="0 fp32, 1 GELU, 2 GELU', 3 clamp (with --gemm)")
     a = ap.parse_args()
     abi.load()
+    if a.gemm:
+        _gemm_shape(*a.gemm, a.epilogue, a.repeat)
+        print("gemm", a.gemm, "epilogue", a.epilogue, "status ok")
+        return
     sur = Surrogate()
     d = random_thicknesses(a.infer_batch, seed=44)
     out = torch.empty(a.infer_batch, sur.outputs, device="cuda")
