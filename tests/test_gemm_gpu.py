@@ -114,7 +114,8 @@ def test_gemm_transposed_entry_rejects_bad_arguments():
 FORMS = ["single", "pair"]
 
 
-@pytest.mark.parametrize("M,N,K", [(256, 256, 64), (300, 1024, 256), (1000, 512, 192), (4096, 1024, 1024)])
+@pytest.mark.parametrize("M,N,K", [(256, 256, 64), (300, 1024, 256), (1000, 512, 192), (4096, 1024, 1024),
+                                   (130, 256, 64), (100, 512, 128), (513, 300, 64)])
 def test_pair_and_single_forms_agree_bit_for_bit(M, N, K, monkeypatch):
     A, B, bias = operands(M, N, K, M + 3 * N)
     outs = []
