@@ -601,6 +601,7 @@ def bench_surrogate(args, torch, abi, W, flush, world, max_over_ranks):
                                                      "train_loss": loss, **held_out()}))
     mean_mse = float(((R_test - R.mean(dim=0)) ** 2).mean())  # the mean spectrum as predictor
     del d, R
+    activation_floor = surrogate_fp32_activations(sur, d_test, R_test, tols, torch)
     torch.cuda.empty_cache()
     B = 65536
     dt = random_thicknesses(B, seed=44)
@@ -641,6 +642,7 @@ def bench_surrogate(args, torch, abi, W, flush, world, max_over_ranks):
             "train": {"steps": rep.steps, "batch": rep.batch, "seconds": rep.seconds, "loss_first": rep.loss_first,
                       "loss_last": rep.loss_last, "lr": "1e-3 peak, 200 warm-up steps, cosine to 1e-5",
                       "held_out_mse_of_mean_spectrum": mean_mse, "learning_curve": curve},
+            "fp32_activations": activation_floor,
             "exact_tmm": {"value": B * world / (ms_e * 1e-3), "ms_per_step": ms_e},
             "network_only": {"value": B * world / (ms_n * 1e-3), "ms_per_step": ms_n,
                              "max_abs_err": float(err.max()), "mean_abs_err": mean_abs,
@@ -695,6 +697,34 @@ def bench_paper_shapes(args, torch, abi, W, flush):
             ent["oracle_cores"] = cpu_threads()
         res[name] = ent
     return res
+
+
+def surrogate_fp32_activations(sur, d, R_exact, tols, torch):
+    """How much of the trained network's error is its bf16 arithmetic: the same
+    weights (bf16-rounded, as the kernels read them) evaluated with fp32
+    activations and the exact erf GELU by plain torch matmuls -- a measurement
+    aid beside the benchmark, not a product path -- against the exact spectra
+    and against the library's bf16 inference of the same rows."""
+    import torch.nn.functional as F
+    with torch.no_grad():
+        y_bf16 = sur.infer(d)
+        x = torch.zeros(d.shape[0], 64, device=d.device)
+        lo, hi = sur.d_range
+        x[:, :d.shape[1]] = (d - lo) / (hi - lo)
+        h = x.bfloat16().float()
+        for i in range(sur.depth + 1):
+            W, b = sur.layer_tensors(i)[:2]
+            z = h @ W.bfloat16().float().T + b
+            h = F.gelu(z) if i < sur.depth else z.clamp(0.0, 1.0)
+        e32 = (h - R_exact).abs()
+        row32 = e32.amax(dim=1)
+        drow = (y_bf16 - h).abs().amax(dim=1)
+        return {"rows": int(d.shape[0]), "mse": float((e32 * e32).mean()), "mean_abs_err": float(e32.mean()),
+                "row_max_err_median": float(row32.median()),
+                "rows_within": {f"{t:g}": float((row32 <= t).float().mean()) for t in tols},
+                "bf16_vs_fp32_row_max_diff": {"min": float(drow.min()), "median": float(drow.median()),
+                                              "max": float(drow.max())},
+                "bf16_vs_fp32_mean_abs_diff": float((y_bf16 - h).abs().mean())}
 
 
 def sur_shapes(sur):
