@@ -628,6 +628,7 @@ def bench_surrogate(args, torch, abi, W, flush, world, max_over_ranks):
             "max_abs_err_all_rows_delivered": float((outR - exact).abs().max()), "tol": 1e-3}
     ms_e = max_over_ranks(sum(t_exact) / len(t_exact))
     ms_n = max_over_ranks(sum(t_net) / len(t_net))
+    screening = surrogate_screening(sur, dt, exact, W, torch, flush, steps)
     flops = 2.0 * B * sum(n * k for n, k in sur_shapes(sur))
     peaks = measured_peaks() or {}
     peak = peaks.get("bf16_tflops")
@@ -648,6 +649,7 @@ def bench_surrogate(args, torch, abi, W, flush, world, max_over_ranks):
                              "max_abs_err": float(err.max()), "mean_abs_err": mean_abs,
                              "rows_within_1e-3": within["0.001"], "rows_within": within},
             "judged": judged,
+            "screening": screening,
             "speedup_network_only": ms_e / ms_n,
             "speedup_at_max_err_1e-3": ms_e / full["ms_per_step"],
             "speedup_judge_fraction_1_16": ms_e / judged["judge_fraction_0.0625"]["ms_per_step"],
@@ -697,6 +699,42 @@ def bench_paper_shapes(args, torch, abi, W, flush):
             ent["oracle_cores"] = cpu_threads()
         res[name] = ent
     return res
+
+
+def surrogate_screening(sur, pool, exact, W, torch, flush, steps, k=256):
+    """The trained network as a design screen: the pool's thickness sets are
+    ranked by the network's merit mean (R - R_target)^2 against the band-stop
+    target and only the k best-ranked are evaluated exactly; the method without
+    the network spends the same k exact evaluations on random members (the
+    pool's disjoint groups of k).  The merit and the ranking are torch glue
+    around the library's inference and exact kernels."""
+    B = int(pool.shape[0])
+    Rt = torch.as_tensor(W.band_stop_target(sur.lam, 2, sur.theta.shape[0]).reshape(-1), device=pool.device,
+                         dtype=torch.float32)
+
+    def screen():
+        m_net = ((sur.infer(pool) - Rt) ** 2).mean(dim=1)
+        pick = torch.topk(m_net, k, largest=False).indices
+        return pick, ((sur.generate(pool[pick]) - Rt) ** 2).mean(dim=1)
+
+    pick, m_pick = screen()
+    m_all = ((exact - Rt) ** 2).mean(dim=1)
+    best = float(m_pick.min())
+    group_best = m_all.view(B // k, k).amin(dim=1)
+    n_as_good = int((m_all <= best).sum())
+    t_screen = time_steps(screen, steps, 3, torch, flush)
+    t_pool = time_steps(lambda: ((sur.generate(pool) - Rt) ** 2).mean(dim=1), steps, 3, torch, flush)
+    ms_s, ms_p = sum(t_screen) / len(t_screen), sum(t_pool) / len(t_pool)
+    return {"pool": B, "exact_evaluations": k, "target": "band-stop 550-650 nm (R 0.95, else 0.02), s+p, all angles",
+            "best_exact_merit_screened": best, "best_exact_merit_pool": float(m_all.min()),
+            "median_best_of_random_groups": float(group_best.median()),
+            "random_groups_beaten": float((group_best > best).float().mean()),
+            "pool_members_as_good": n_as_good,
+            "random_search_exact_evaluations_to_match": B / n_as_good,
+            "ms_screen": ms_s, "ms_exact_pool": ms_p,
+            # a random search's expected time to a design as good: its exact
+            # evaluations at the pool's exact rate, against the screen's time
+            "speedup_to_match_screened_design": (ms_p / B) * (B / n_as_good) / ms_s}
 
 
 def surrogate_fp32_activations(sur, d, R_exact, tols, torch):

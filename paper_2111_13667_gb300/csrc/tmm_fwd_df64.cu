@@ -229,10 +229,18 @@ __device__ __forceinline__ void eval_point_dd(const DStage *__restrict__ st, con
 using df2::cdd2;
 using df2::dd2;
 
-__device__ __forceinline__ void sincos_turn_dd2(const dd2 &f, const float4 *tab, dd2 *s, dd2 *c)
+// sin and cos of 2 pi y per lane for a phase y in turns: y = n + m/256 + r
+// with n = rint(y.hi), m = rint(256 (y.hi - n)) and r = ((y.hi - n) - m/256) +
+// y.lo.  Both float differences are exact (Sterbenz: the operands lie within a
+// factor of two of each other, or the subtrahend is 0), so the reduction takes
+// no error-free transformation; |r.hi| <= 1/512 and r is an unnormalised pair.
+// Taylor series of sin, cos (2 pi r) to x^5 / x^6 and the angle-addition
+// formulas with the table entry of m mod 256, as sincos_turn_dd.
+__device__ __forceinline__ void sincos_turn_dd2(const dd2 &y, const float4 *tab, dd2 *s, dd2 *c)
 {
-    const float2 jf = df2::p2(rintf(__fmul_rn(f.hi.x, 256.0f)), rintf(__fmul_rn(f.hi.y, 256.0f)));
-    const dd2 r = df2::add_f(f, df2::pneg(df2::pmul(jf, df2::b2(1.0f / 256.0f))));
+    const float2 c0 = df2::psub(y.hi, df2::p2(rintf(y.hi.x), rintf(y.hi.y)));
+    const float2 jf = df2::p2(rintf(__fmul_rn(c0.x, 256.0f)), rintf(__fmul_rn(c0.y, 256.0f)));
+    const dd2 r{df2::pfma(jf, df2::b2(-1.0f / 256.0f), c0), y.lo};
     const dd2 x = df2::mul(r, df2::bcast(dconst(2.0 * kPi)));
     const dd2 x2 = df2::sqr(x);
     const dd2 t = df2::mul(x2, df2::bcast(dconst(1.0 / 6.0)));
@@ -258,22 +266,25 @@ __device__ __forceinline__ void sincos_turn_dd2(const dd2 &f, const float4 *tab,
     *c = df2::dot2(C, cx, S, sx, -1.0f);
 }
 
-// 2^v as m * 2^n per lane, m in [2^-0.5, 2^0.5]
+// 2^v as m * 2^n per lane, m in [2^-0.5, 2^0.5]: v = k/64 + s with
+// k = rint(64 v.hi) and s = (v.hi - k/64) + v.lo (the float difference exact,
+// as in sincos_turn_dd2), k = 64 n + i with |i| <= 32; e^{s ln 2} = 1 + t +
+// t^2/2 + t^3 (1/6 + t/24 + t^2/120) with t = s ln 2, |t| <= ln 2 / 128, so the
+// terms from t^3 on (below 2.7e-8) are summed in float; times the table entry
+// 2^{i/64}.
 __device__ __forceinline__ dd2 exp2_dd2(const dd2 &v, const float2 *tab, int n_out[2])
 {
-    const float2 nf = df2::p2(rintf(v.hi.x), rintf(v.hi.y));
-    const dd2 r = df2::add_f(v, df2::pneg(nf));
-    const float2 i_f = df2::p2(rintf(__fmul_rn(r.hi.x, 64.0f)), rintf(__fmul_rn(r.hi.y, 64.0f)));
-    const dd2 s = df2::add_f(r, df2::pneg(df2::pmul(i_f, df2::b2(1.0f / 64.0f))));
+    const float2 kf = df2::p2(rintf(__fmul_rn(v.hi.x, 64.0f)), rintf(__fmul_rn(v.hi.y, 64.0f)));
+    const dd2 s{df2::pfma(kf, df2::b2(-1.0f / 64.0f), v.hi), v.lo};
+    const float2 nf = df2::p2(rintf(__fmul_rn(kf.x, 1.0f / 64.0f)), rintf(__fmul_rn(kf.y, 1.0f / 64.0f)));
+    const float2 i_f = df2::pfma(nf, df2::b2(-64.0f), kf);
     const dd2 t = df2::mul(s, df2::bcast(dconst(0.69314718055994530941723212145818)));
     const dd2 t2 = df2::sqr(t);
-    const dd2 t3_6 = df2::mul(t2, df2::mul(t, df2::bcast(dconst(1.0 / 6.0))));
-    const float2 t4 = df2::pmul(t2.hi, t2.hi);
-    const float2 tail = df2::padd(df2::pmul(t4, df2::b2(1.0f / 24.0f)),
-                                  df2::pmul(df2::pmul(t4, t.hi), df2::b2(1.0f / 120.0f)));
-    dd2 p = df2::add(df2::make(1.0f), t);
-    p = df2::add(p, df2::scale2(t2, df2::b2(0.5f)));
-    p = df2::add(p, t3_6);
+    const float2 tail = df2::pmul(df2::pmul(t2.hi, t.hi),
+                                  df2::pfma(t.hi, df2::pfma(t.hi, df2::b2(1.0f / 120.0f), df2::b2(1.0f / 24.0f)),
+                                            df2::b2(1.0f / 6.0f)));
+    dd2 p = df2::add_u(df2::make(1.0f), t);
+    p = df2::add_u(p, df2::scale2(t2, df2::b2(0.5f)));
     p = df2::add_f(p, tail);
     const float2 ea = tab[(int)i_f.x + 32], eb = tab[(int)i_f.y + 32];
     n_out[0] = (int)nf.x;
@@ -383,20 +394,20 @@ __device__ __forceinline__ void eval_point_dd2(const DStage *__restrict__ st, co
         yi = df2::sel(dd_less_lane(yi_max, yi, 0), dd_less_lane(yi_max, yi, 1), yi_max, yi);
         Y = df2::add(Y, yi);
         dd2 sn, cs;
-        sincos_turn_dd2(df2::add_f(yr, df2::pneg(df2::p2(rintf(yr.hi.x), rintf(yr.hi.y)))), sc, &sn, &cs);
+        sincos_turn_dd2(yr, sc, &sn, &cs);
         int n2[2];
         const dd2 m2 = exp2_dd2(df2::mul(yi, kE), e2, n2);
         const dd2 E2 = df2::scale2(m2, df2::p2(ldexpf(1.0f, n2[0]), ldexpf(1.0f, n2[1])));
         const cdd2 emi{cs, df2::neg(sn)};
         const cdd2 epi{df2::mul(E2, cs), df2::mul(E2, sn)};
         if (POL & 1) {
-            df2::interface_pair(q, q_nx, s0, s1);
+            df2::interface_pair_u(q, q_nx, s0, s1);
             s0 = df2::cmul(emi, s0);
             s1 = df2::cmul(epi, s1);
         }
         if (POL & 2) {
             const cdd2 g = df2::cmul(q, bc_c(A.in2xh, A.in2xl, A.in2yh, A.in2yl));
-            df2::interface_pair(g, g_nx, p0, p1);
+            df2::interface_pair_u(g, g_nx, p0, p1);
             p0 = df2::cmul(emi, p0);
             p1 = df2::cmul(epi, p1);
             g_nx = g;
