@@ -196,25 +196,52 @@ __device__ __forceinline__ dd2 sub_u(const dd2 &a, const dd2 &b)
     return dd2{s, padd(e, psub(a.lo, b.lo))};
 }
 
-__device__ __forceinline__ dd2 dot2_u(const dd2 &a, const dd2 &b, const dd2 &c, const dd2 &d, float sgn)
+// ---------------------------------------------------------------- complex product, few negations
+// Paired instructions take no sign modifiers, so every negation is an
+// instruction of its own.  cmul_t forms a b (CONJ: conj(a) b) with the four
+// high products taken exactly from -a.x.hi, -a.y.hi and -a.y.lo only, each
+// used twice: a product term t = x y is rounded as q = fl(x y) and its exact
+// error carried negated, q - x y = fma(-x, y, q); a term t = -x y likewise as
+// q = fl((-x) y) with q + x y = fma(x, y, q).  Each part is then
+// two_sum(q1, q2) minus the two carried errors plus the cross terms with the
+// low parts, the same roundings as dot2.  NORM: close with fast_two_sum.
+template <bool NORM>
+__device__ __forceinline__ dd2 close_dd2(const dd2 &s, float2 e)
 {
-    const float2 sc = pmul(b2(sgn), c.hi), sl = pmul(b2(sgn), c.lo);
-    const float2 np1 = pmul(pneg(a.hi), b.hi);
-    const float2 e1 = pfma(a.hi, b.hi, np1);
-    const float2 np2 = pmul(pneg(sc), d.hi);
-    const float2 e2 = pfma(sc, d.hi, np2);
-    const dd2 t = two_sum(np1, np2);  // -(p1 + p2)
-    float2 e = padd(pneg(t.lo), padd(e1, e2));
-    e = pfma(a.hi, b.lo, e);
-    e = pfma(a.lo, b.hi, e);
-    e = pfma(sc, d.lo, e);
-    e = pfma(sl, d.hi, e);
-    return dd2{pneg(t.hi), e};
+    if constexpr (NORM) {
+        return fast_two_sum(s.hi, e);
+    } else {
+        return dd2{s.hi, e};
+    }
 }
 
-__device__ __forceinline__ cdd2 cmul_u(const cdd2 &a, const cdd2 &b)
+template <bool NORM, bool CONJ>
+__device__ __forceinline__ cdd2 cmul_t(const cdd2 &a, const cdd2 &b)
 {
-    return cdd2{dot2_u(a.x, b.x, a.y, b.y, -1.0f), dot2_u(a.x, b.y, a.y, b.x, 1.0f)};
+    const float2 nax = pneg(a.x.hi), nay = pneg(a.y.hi), nayl = pneg(a.y.lo);
+    // real part: a.x b.x -+ a.y b.y
+    const float2 q1 = pmul(a.x.hi, b.x.hi);
+    const float2 c1 = pfma(nax, b.x.hi, q1);  // q1 - a.x.hi b.x.hi
+    const float2 q2 = CONJ ? pmul(a.y.hi, b.y.hi) : pmul(nay, b.y.hi);
+    const float2 c2 = CONJ ? pfma(nay, b.y.hi, q2) : pfma(a.y.hi, b.y.hi, q2);
+    const dd2 sr = two_sum(q1, q2);
+    float2 er = psub(psub(sr.lo, c1), c2);
+    er = pfma(a.x.hi, b.x.lo, er);
+    er = pfma(a.x.lo, b.x.hi, er);
+    er = pfma(CONJ ? a.y.hi : nay, b.y.lo, er);
+    er = pfma(CONJ ? a.y.lo : nayl, b.y.hi, er);
+    // imaginary part: a.x b.y +- a.y b.x
+    const float2 q3 = pmul(a.x.hi, b.y.hi);
+    const float2 c3 = pfma(nax, b.y.hi, q3);
+    const float2 q4 = CONJ ? pmul(nay, b.x.hi) : pmul(a.y.hi, b.x.hi);
+    const float2 c4 = CONJ ? pfma(a.y.hi, b.x.hi, q4) : pfma(nay, b.x.hi, q4);
+    const dd2 si = two_sum(q3, q4);
+    float2 ei = psub(psub(si.lo, c3), c4);
+    ei = pfma(a.x.hi, b.y.lo, ei);
+    ei = pfma(a.x.lo, b.y.hi, ei);
+    ei = pfma(CONJ ? nay : a.y.hi, b.x.lo, ei);
+    ei = pfma(CONJ ? nayl : a.y.lo, b.x.hi, ei);
+    return cdd2{close_dd2<NORM>(sr, er), close_dd2<NORM>(si, ei)};
 }
 
 // interface_pair with unnormalised intermediates and outputs (see above)
@@ -222,8 +249,8 @@ __device__ __forceinline__ void interface_pair_u(const cdd2 &k, const cdd2 &kn, 
 {
     const cdd2 u{add_u(x0.x, x1.x), add_u(x0.y, x1.y)};
     const cdd2 v{sub_u(x0.x, x1.x), sub_u(x0.y, x1.y)};
-    const cdd2 X = cmul_u(k, u);
-    const cdd2 Z = cmul_u(kn, v);
+    const cdd2 X = cmul_t<false, false>(k, u);
+    const cdd2 Z = cmul_t<false, false>(kn, v);
     x0 = cdd2{add_u(X.x, Z.x), add_u(X.y, Z.y)};
     x1 = cdd2{sub_u(X.x, Z.x), sub_u(X.y, Z.y)};
 }

@@ -261,9 +261,10 @@ __device__ __forceinline__ void sincos_turn_dd2(const dd2 &y, const float4 *tab,
         else if (quad == 2) { sj[i] = df::neg(sk); cj[i] = df::neg(ck); }
         else { sj[i] = df::neg(ck); cj[i] = sk; }
     }
-    const dd2 S = df2::pack(sj[0], sj[1]), C = df2::pack(cj[0], cj[1]);
-    *s = df2::dot2(S, cx, C, sx, 1.0f);
-    *c = df2::dot2(C, cx, S, sx, -1.0f);
+    // cos + i sin of the sum: (C + i S)(cx + i sx)
+    const cdd2 w = df2::cmul_t<true, false>(cdd2{df2::pack(cj[0], cj[1]), df2::pack(sj[0], sj[1])}, cdd2{cx, sx});
+    *c = w.x;
+    *s = w.y;
 }
 
 // 2^v as m * 2^n per lane, m in [2^-0.5, 2^0.5]: v = k/64 + s with
@@ -398,18 +399,19 @@ __device__ __forceinline__ void eval_point_dd2(const DStage *__restrict__ st, co
         int n2[2];
         const dd2 m2 = exp2_dd2(df2::mul(yi, kE), e2, n2);
         const dd2 E2 = df2::scale2(m2, df2::p2(ldexpf(1.0f, n2[0]), ldexpf(1.0f, n2[1])));
-        const cdd2 emi{cs, df2::neg(sn)};
+        // phase factors e^{-i Re delta} = conj(w) and e^{i delta} / e^{Im delta} = E2 w
+        const cdd2 w{cs, sn};
         const cdd2 epi{df2::mul(E2, cs), df2::mul(E2, sn)};
         if (POL & 1) {
             df2::interface_pair_u(q, q_nx, s0, s1);
-            s0 = df2::cmul(emi, s0);
-            s1 = df2::cmul(epi, s1);
+            s0 = df2::cmul_t<true, true>(w, s0);
+            s1 = df2::cmul_t<true, false>(epi, s1);
         }
         if (POL & 2) {
-            const cdd2 g = df2::cmul(q, bc_c(A.in2xh, A.in2xl, A.in2yh, A.in2yl));
+            const cdd2 g = df2::cmul_t<true, false>(q, bc_c(A.in2xh, A.in2xl, A.in2yh, A.in2yl));
             df2::interface_pair_u(g, g_nx, p0, p1);
-            p0 = df2::cmul(emi, p0);
-            p1 = df2::cmul(epi, p1);
+            p0 = df2::cmul_t<true, true>(w, p0);
+            p1 = df2::cmul_t<true, false>(epi, p1);
             g_nx = g;
         }
         q_nx = q;
