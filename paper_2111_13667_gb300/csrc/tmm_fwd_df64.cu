@@ -35,9 +35,11 @@ namespace {
 constexpr int kDfMaxThreads = 512;
 constexpr int kDfPairThreads = 256;
 
+constexpr int kScEntries = 256;
+
 struct DfTables {
-    float4 sc[64];  // {sin hi, sin lo, cos hi, cos lo} of 2 pi k / 256
-    float2 e2[65];  // 2^{i/64}, i = -32 .. 32
+    float4 sc[kScEntries];  // {sin hi, sin lo, cos hi, cos lo} of 2 pi k / 256, the whole turn
+    float2 e2[65];          // 2^{i/64}, i = -32 .. 32
 };
 
 // per (medium, wavelength): n^2 - n0^2, Im n^2, 1/n^2, d/lambda, |1/n^2|^2
@@ -235,7 +237,7 @@ using df2::dd2;
 // factor of two of each other, or the subtrahend is 0), so the reduction takes
 // no error-free transformation; |r.hi| <= 1/512 and r is an unnormalised pair.
 // Taylor series of sin, cos (2 pi r) to x^5 / x^6 and the angle-addition
-// formulas with the table entry of m mod 256, as sincos_turn_dd.
+// formulas with the table entry of m mod 256 (a table of the whole turn).
 __device__ __forceinline__ void sincos_turn_dd2(const dd2 &y, const float4 *tab, dd2 *s, dd2 *c)
 {
     const float2 c0 = df2::psub(y.hi, df2::p2(rintf(y.hi.x), rintf(y.hi.y)));
@@ -250,19 +252,11 @@ __device__ __forceinline__ void sincos_turn_dd2(const dd2 &y, const float4 *tab,
     const float2 h4 = df2::psub(df2::pmul(x4, df2::b2(1.0f / 24.0f)),
                                 df2::pmul(df2::pmul(x4, x2.hi), df2::b2(1.0f / 720.0f)));
     const dd2 cx = df2::add_f(df2::sub(df2::make(1.0f), df2::scale2(x2, df2::b2(0.5f))), h4);
-    dd sj[2], cj[2];
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-        const int jj = (int)(i ? jf.y : jf.x) & 255, quad = jj >> 6, k = jj & 63;
-        const float4 e = tab[k];
-        const dd sk{e.x, e.y}, ck{e.z, e.w};
-        if (quad == 0) { sj[i] = sk; cj[i] = ck; }
-        else if (quad == 1) { sj[i] = ck; cj[i] = df::neg(sk); }
-        else if (quad == 2) { sj[i] = df::neg(sk); cj[i] = df::neg(ck); }
-        else { sj[i] = df::neg(ck); cj[i] = sk; }
-    }
+    // the table covers the whole turn: entry m mod 256 directly, no quadrant logic
+    const float4 ea = tab[(int)jf.x & 255], eb = tab[(int)jf.y & 255];
+    const dd2 S{df2::p2(ea.x, eb.x), df2::p2(ea.y, eb.y)}, C{df2::p2(ea.z, eb.z), df2::p2(ea.w, eb.w)};
     // cos + i sin of the sum: (C + i S)(cx + i sx)
-    const cdd2 w = df2::cmul_t<true, false>(cdd2{df2::pack(cj[0], cj[1]), df2::pack(sj[0], sj[1])}, cdd2{cx, sx});
+    const cdd2 w = df2::cmul_t<true, false>(cdd2{C, S}, cdd2{cx, sx});
     *c = w.x;
     *s = w.y;
 }
@@ -328,6 +322,48 @@ __device__ __forceinline__ cdd2 root_dd2(const cdd2 &z, dd2 *absz)
     return q;
 }
 
+// |x| and x with the sign of another value, on a float pair by its sign bits
+// (integer instructions, off the FMA pipe): both floats of a pair share the
+// sign of the high part's value.
+__device__ __forceinline__ unsigned sign_of(float h) { return __float_as_uint(h) & 0x80000000u; }
+__device__ __forceinline__ dd xor_sign(dd a, unsigned sb)
+{
+    return dd{__uint_as_float(__float_as_uint(a.hi) ^ sb), __uint_as_float(__float_as_uint(a.lo) ^ sb)};
+}
+
+// Root of z = n^2 - beta^2 inside the stack, per lane: R and T do not depend
+// on which of the two roots an interior layer takes (the oracle's pin of
+// reading C2), so Im q >= 0 is taken by the sign of Im z alone, without the
+// bounding media's tolerance band: q = sgn(Im z) sqrt(z) from the principal
+// root, i.e. (sgn(Im z) t, |o|) for Re z >= 0 and (sgn(Im z) |o|, t) otherwise,
+// with t = sqrt((|z| + |Re z|) / 2), o = Im z / (2 t).
+__device__ __forceinline__ cdd2 root_inner_dd2(const cdd2 &z, dd2 *absz)
+{
+    const dd2 hyp = df2::cabs2(z);
+    const bool v0 = !(hyp.hi.x <= 0.0f), v1 = !(hyp.hi.y <= 0.0f);
+    dd2 az, rh;
+    df2::sqrt_rsqrt(df2::sel(v0, v1, hyp, df2::make(1.0f)), &az, &rh);
+    const dd zx0 = df2::lane(z.x, 0), zx1 = df2::lane(z.x, 1);
+    const dd ax0 = xor_sign(zx0, sign_of(zx0.hi)), ax1 = xor_sign(zx1, sign_of(zx1.hi));
+    const dd2 u = df2::scale2(df2::add(az, df2::pack(ax0, ax1)), df2::b2(0.5f));
+    dd2 t, ru;
+    df2::sqrt_rsqrt(u, &t, &ru);
+    const dd2 o = df2::scale2(df2::mul(z.y, ru), df2::b2(0.5f));
+    dd qx[2], qy[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const dd zi = df2::lane(z.y, i), ti = df2::lane(t, i), oi = df2::lane(o, i);
+        const unsigned sy = sign_of(zi.hi);
+        const dd ao = xor_sign(oi, sign_of(oi.hi));
+        const bool rp = (i ? z.x.hi.y : z.x.hi.x) >= 0.0f;
+        qx[i] = xor_sign(rp ? ti : ao, sy);
+        qy[i] = rp ? ao : ti;
+    }
+    const dd2 zero = df2::make(0.0f);
+    *absz = df2::sel(v0, v1, az, zero);
+    return cdd2{df2::sel(v0, v1, df2::pack(qx[0], qx[1]), zero), df2::sel(v0, v1, df2::pack(qy[0], qy[1]), zero)};
+}
+
 __device__ __forceinline__ void renorm_dd_pair2(cdd2 &a, cdd2 &b, int e[2])
 {
     int k[2];
@@ -386,8 +422,8 @@ __device__ __forceinline__ void eval_point_dd2(const DStage *__restrict__ st, co
 
     for (int j = L; j >= 1; --j) {
         A = st[j * TL + tl];
-        const cdd2 q = root_dd2(cdd2{df2::add(df2::bcast(dd{A.d2h, A.d2l}), Q0SQ), df2::bcast(dd{A.n2yh, A.n2yl})},
-                                &absz);
+        const cdd2 q = root_inner_dd2(
+            cdd2{df2::add(df2::bcast(dd{A.d2h, A.d2l}), Q0SQ), df2::bcast(dd{A.n2yh, A.n2yl})}, &absz);
         Ps = df2::mul(Ps, absz);
         const dd2 dl = df2::bcast(dd{A.dlh, A.dll});
         const dd2 yr = df2::mul(dl, q.x);
@@ -442,7 +478,7 @@ __global__ void __launch_bounds__(PAIR ? kDfPairThreads : kDfMaxThreads, PAIR ? 
     extern __shared__ __align__(16) unsigned char smem[];
     DStage *st = reinterpret_cast<DStage *>(smem);
     float4 *sc = reinterpret_cast<float4 *>(st + (size_t)(p.L_max + 2) * TL);
-    float2 *e2 = reinterpret_cast<float2 *>(sc + 64);
+    float2 *e2 = reinterpret_cast<float2 *>(sc + kScEntries);
     float2 *n0s = e2 + 65;         // [TL] dd n_0 (NaN if complex)
     float2 *ppm = n0s + TL;        // [TL] dd prod |1/n^2|^2
     int *ppe = reinterpret_cast<int *>(ppm + TL);
@@ -458,7 +494,7 @@ __global__ void __launch_bounds__(PAIR ? kDfPairThreads : kDfMaxThreads, PAIR ? 
     const double *lam = (const double *)p.lambda;
     const double *d = (const double *)p.d;
 
-    for (int i = tid; i < 64; i += nthr) sc[i] = tabs.sc[i];
+    for (int i = tid; i < kScEntries; i += nthr) sc[i] = tabs.sc[i];
     for (int i = tid; i < 65; i += nthr) e2[i] = tabs.e2[i];
     if (L >= 0) {
         const int total = (L + 2) * TL;
@@ -549,8 +585,13 @@ const DfTables &host_tables()
     static DfTables t;
     static std::once_flag once;
     std::call_once(once, [] {
-        const SinCosTable &sc = sincos_table();
-        for (int k = 0; k < 64; ++k) t.sc[k] = sc.sc[k];
+        // entries 0..63 are those of the quadrant table the scalar sincos_turn_dd reads
+        for (int k = 0; k < kScEntries; ++k) {
+            const double a = 2.0 * kPi * k / 256.0;
+            const double sv = std::sin(a), cv = std::cos(a);
+            const float sh = (float)sv, ch = (float)cv;
+            t.sc[k] = make_float4(sh, (float)(sv - sh), ch, (float)(cv - ch));
+        }
         for (int i = -32; i <= 32; ++i) {
             const double v = std::exp2(i / 64.0);
             const float h = (float)v;
@@ -562,7 +603,7 @@ const DfTables &host_tables()
 
 size_t df_stage_bytes(const tmm_problem *p, int TL)
 {
-    return (size_t)(p->L_max + 2) * TL * sizeof(DStage) + 64 * sizeof(float4) + 65 * sizeof(float2) +
+    return (size_t)(p->L_max + 2) * TL * sizeof(DStage) + kScEntries * sizeof(float4) + 65 * sizeof(float2) +
            (size_t)TL * (2 * sizeof(float2) + sizeof(int));
 }
 
