@@ -166,6 +166,26 @@ def test_single_interface_and_opaque_layers(prec):
         assert_close(T, To, TOL[prec], f"T {media[:3]}")
 
 
+@pytest.mark.parametrize("prec", ALL)
+def test_interior_gain_and_evanescent_layers(prec):
+    # interior roots on both sides of the branch rule: a gain layer (Im n < 0,
+    # so Im(n^2 - beta^2) < 0), absorbing layers, and lossless layers that turn
+    # evanescent (Re(n^2 - beta^2) < 0) past their critical angle for light
+    # injected from index 1.8.  R and T do not depend on which root an interior
+    # layer takes (reading C2), so every path matches the oracle at its tolerance.
+    lam = np.linspace(400, 800, 41)
+    th = np.deg2rad(np.linspace(0, 80, 10))
+    for media, d in (([1.8, 1.35, 2.1 - 0.02j, 1.45, 1.9 + 0.01j, 1.3, 1.9], [120.0, 80.0, 60.0, 150.0, 40.0]),
+                     ([1.8, 1.6 - 0.005j, 1.2, 2.4 + 0.1j, 1.2, 1.52 + 0.001j], [200.0, 30.0, 90.0, 25.0])):
+        L = len(d)
+        nd = np.asarray(media, dtype=np.complex128)[None, :]
+        w = W.Workload("case", theta=th, lam=lam, d=np.asarray(d, dtype=np.float64).reshape(1, L), n_direct=nd)
+        Ro, To = oracle_RT(w)
+        R, T = gpu_RT(w, prec)
+        assert_close(R, Ro, TOL[prec], f"R {media}")
+        assert_close(T, To, TOL[prec], f"T {media}")
+
+
 @pytest.mark.parametrize("prec,persistent", [("f64", 0), ("f64", 1), ("f32", 0), ("f32", 1), ("f64x", 0),
                                              ("f32d", 0), ("f32d", 1)])
 def test_ragged_layer_counts(prec, persistent):
