@@ -15,8 +15,8 @@ The amplitudes come from the boundary conditions written as 2x2 matrices
 for p), multiplied in full (complex128), the incident amplitude set to 1.
 The integral of |a e^{i kappa z} + b e^{-i kappa z}|^2 (and of the difference)
 is taken in closed form, the backward term with its amplitude at the layer's
-right boundary (no growing exponential).  Layers past L_s give 0; the clamp of Im delta
-(reading C6) applies to the propagation matrices as in the other oracles.
+right boundary (no growing exponential).  Layers past L_s give 0; the clamp Im delta <= 35
+applies to the propagation matrices as in the other oracles.
 """
 from __future__ import annotations
 
@@ -26,7 +26,7 @@ IM_DELTA_MAX = 35.0
 
 
 def _root(z):
-    """Forward branch of sqrt(z) (reading C2)."""
+    """Forward branch of sqrt(z): Im >= 0, the principal root where Im is zero to rounding."""
     q = np.sqrt(z + 0j)
     flip = (q.imag < 0) & (np.abs(q.imag) > 100 * np.finfo(float).eps * np.abs(q))
     q = np.where(flip, -q, q)

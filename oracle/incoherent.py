@@ -18,7 +18,7 @@ Readings (the paper gives none):
   coefficients of Eq. 1 and the layer phases of Eq. 3 with these roots, the
   product of Eq. 4, and R = |r|^2, T = Re(n_b conj-or-not cos theta_b) /
   Re(n_a ... cos theta_a) |t|^2 (the Poynting form of Eq. 2 with complex
-  bounding media, reading C4); each block is evaluated once from each side,
+  bounding media); each block is evaluated once from each side,
   no reciprocity is assumed;
 * an incoherent layer with a complex index attenuates every single pass of
   light by P_j = |exp(i delta_j)|^2 = exp(-4 pi Im(q_j) d_j / lambda);
@@ -39,12 +39,12 @@ import math
 
 import numpy as np
 
-IM_DELTA_MAX = 35.0  # the opaque-layer clamp of the coherent method (reading C6)
+IM_DELTA_MAX = 35.0  # the coherent method's opaque-layer clamp Im(delta) <= 35 (not in the paper)
 
 
 def forward_root(z):
     """Root of z with Im >= 0; the principal root (Re >= 0) where the imaginary
-    part is zero to rounding (|Im| <= 100 eps |q|), reading C2."""
+    part is zero to rounding (|Im| <= 100 eps |q|); the paper leaves the branch open."""
     q = cmath.sqrt(complex(z))  # principal: Re q >= 0
     if q.imag < -100 * 2.220446049250313e-16 * abs(q):
         q = -q

@@ -332,8 +332,8 @@ __device__ __forceinline__ dd xor_sign(dd a, unsigned sb)
 }
 
 // Root of z = n^2 - beta^2 inside the stack, per lane: R and T do not depend
-// on which of the two roots an interior layer takes (the oracle's pin of
-// reading C2), so Im q >= 0 is taken by the sign of Im z alone, without the
+// on which of the two roots an interior layer takes (the sign flips cancel;
+// an oracle test pins it), so Im q >= 0 is taken by the sign of Im z alone, without the
 // bounding media's tolerance band: q = sgn(Im z) sqrt(z) from the principal
 // root, i.e. (sgn(Im z) t, |o|) for Re z >= 0 and (sgn(Im z) |o|, t) otherwise,
 // with t = sqrt((|z| + |Re z|) / 2), o = Im z / (2 t).

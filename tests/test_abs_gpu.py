@@ -118,7 +118,7 @@ def test_field_profile_ragged_opaque_and_unpolarised():
     Eu = gpu_field(w, "f64", 3, pols="u")
     assert np.max(np.abs(Eu[0] - 0.5 * (Eo[0] + Eo[1]))) <= 1e-10
     # an opaque metal layer: the profile stays finite and vanishes past the skin
-    # depth (beyond it the Im(delta) clamp of reading C6 sets the field's
+    # depth (beyond it the Im(delta) <= 35 clamp sets the field's
     # floor: far below any physical scale, identical in the oracle)
     nd = np.array([[1.0, 1.7, 0.2 + 3.5j, 1.52]], dtype=np.complex128)
     wo = W.Workload("opaque", theta=np.deg2rad([0.0, 40.0]), lam=np.array([550.0]), d=np.array([[90.0, 2e4]]),

@@ -172,7 +172,7 @@ def test_interior_gain_and_evanescent_layers(prec):
     # so Im(n^2 - beta^2) < 0), absorbing layers, and lossless layers that turn
     # evanescent (Re(n^2 - beta^2) < 0) past their critical angle for light
     # injected from index 1.8.  R and T do not depend on which root an interior
-    # layer takes (reading C2), so every path matches the oracle at its tolerance.
+    # layer takes (the sign flips cancel), so every path matches the oracle at its tolerance.
     lam = np.linspace(400, 800, 41)
     th = np.deg2rad(np.linspace(0, 80, 10))
     for media, d in (([1.8, 1.35, 2.1 - 0.02j, 1.45, 1.9 + 0.01j, 1.3, 1.9], [120.0, 80.0, 60.0, 150.0, 40.0]),
