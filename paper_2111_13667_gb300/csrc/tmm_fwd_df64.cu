@@ -8,7 +8,8 @@
 // applied divided by e^{Im delta}, power-of-two rescaling every two layers).  Transcendentals:
 //   sin, cos of 2 pi f: f = j/256 + r, |r| <= 1/512; Taylor series of
 //     sin, cos (2 pi r) to x^5 / x^6, recombined with a table of
-//     sin, cos(2 pi k / 256) by the angle-addition formulas;
+//     sin, cos(2 pi k / 256) by the angle-addition formulas (the paired
+//     sweep: j/1024, a whole-turn table, shorter series);
 //   2^v: v = n + i/64 + s, |s| <= 1/128; Taylor series of e^{s ln 2} to s^5,
 //     times a table of 2^{i/64}, times 2^n;
 //   square roots: Karp-Markstein correction of the float reciprocal root.
@@ -35,11 +36,12 @@ namespace {
 constexpr int kDfMaxThreads = 512;
 constexpr int kDfPairThreads = 256;
 
-constexpr int kScEntries = 256;
+constexpr int kFine = 1024;  // entries of the whole-turn table of the paired sweep
 
 struct DfTables {
-    float4 sc[kScEntries];  // {sin hi, sin lo, cos hi, cos lo} of 2 pi k / 256, the whole turn
-    float2 e2[65];          // 2^{i/64}, i = -32 .. 32
+    float4 sc[64];     // {sin hi, sin lo, cos hi, cos lo} of 2 pi k / 256, k < 64 (sincos_turn_dd)
+    float4 sf[kFine];  // the same of 2 pi k / 1024 over the whole turn (sincos_turn_dd2)
+    float2 e2[65];     // 2^{i/64}, i = -32 .. 32
 };
 
 // per (medium, wavelength): n^2 - n0^2, Im n^2, 1/n^2, d/lambda, |1/n^2|^2
@@ -231,29 +233,29 @@ __device__ __forceinline__ void eval_point_dd(const DStage *__restrict__ st, con
 using df2::cdd2;
 using df2::dd2;
 
-// sin and cos of 2 pi y per lane for a phase y in turns: y = n + m/256 + r
-// with n = rint(y.hi), m = rint(256 (y.hi - n)) and r = ((y.hi - n) - m/256) +
-// y.lo.  Both float differences are exact (Sterbenz: the operands lie within a
-// factor of two of each other, or the subtrahend is 0), so the reduction takes
-// no error-free transformation; |r.hi| <= 1/512 and r is an unnormalised pair.
-// Taylor series of sin, cos (2 pi r) to x^5 / x^6 and the angle-addition
-// formulas with the table entry of m mod 256 (a table of the whole turn).
+// sin and cos of 2 pi y per lane for a phase y in turns: y = n + m/1024 + r
+// with n = rint(y.hi), m = rint(1024 (y.hi - n)) and r = ((y.hi - n) - m/1024)
+// + y.lo.  Both float differences are exact (Sterbenz: the operands lie within
+// a factor of two of each other, or the subtrahend is 0), so the reduction
+// takes no error-free transformation; |r.hi| <= 1/2048 and r is an
+// unnormalised pair.  With x = 2 pi r, |x| <= pi/1024:
+//   sin x = x - x e, e = x^2/6 - x^4/120 < 1.6e-6, so e and x e are formed in
+//     float (their roundings move sin x by less than 2^-50);
+//   cos x = 1 - x^2/2 + x^4/24 with x^2 as a float pair and x^4/24 < 3.7e-12
+//     in float (the next term, x^6/720, is below 2^-60);
+// then the angle-addition formulas with the table entry of m mod 1024.
 __device__ __forceinline__ void sincos_turn_dd2(const dd2 &y, const float4 *tab, dd2 *s, dd2 *c)
 {
     const float2 c0 = df2::psub(y.hi, df2::p2(rintf(y.hi.x), rintf(y.hi.y)));
-    const float2 jf = df2::p2(rintf(__fmul_rn(c0.x, 256.0f)), rintf(__fmul_rn(c0.y, 256.0f)));
-    const dd2 r{df2::pfma(jf, df2::b2(-1.0f / 256.0f), c0), y.lo};
+    const float2 jf = df2::p2(rintf(__fmul_rn(c0.x, (float)kFine)), rintf(__fmul_rn(c0.y, (float)kFine)));
+    const dd2 r{df2::pfma(jf, df2::b2(-1.0f / kFine), c0), y.lo};
     const dd2 x = df2::mul(r, df2::bcast(dconst(2.0 * kPi)));
     const dd2 x2 = df2::sqr(x);
-    const dd2 t = df2::mul(x2, df2::bcast(dconst(1.0 / 6.0)));
-    const float2 x4 = df2::pmul(x2.hi, x2.hi);
-    const dd2 p = df2::add_f(df2::sub(df2::make(1.0f), t), df2::pmul(x4, df2::b2(1.0f / 120.0f)));
-    const dd2 sx = df2::mul(x, p);
-    const float2 h4 = df2::psub(df2::pmul(x4, df2::b2(1.0f / 24.0f)),
-                                df2::pmul(df2::pmul(x4, x2.hi), df2::b2(1.0f / 720.0f)));
-    const dd2 cx = df2::add_f(df2::sub(df2::make(1.0f), df2::scale2(x2, df2::b2(0.5f))), h4);
-    // the table covers the whole turn: entry m mod 256 directly, no quadrant logic
-    const float4 ea = tab[(int)jf.x & 255], eb = tab[(int)jf.y & 255];
+    const float2 e = df2::pmul(x2.hi, df2::pfma(x2.hi, df2::b2(-1.0f / 120.0f), df2::b2(1.0f / 6.0f)));
+    const dd2 sx = df2::add_u(x, dd2{df2::pneg(df2::pmul(x.hi, e)), df2::b2(0.0f)});
+    dd2 cx = df2::sub_u(df2::make(1.0f), df2::scale2(x2, df2::b2(0.5f)));
+    cx.lo = df2::pfma(df2::pmul(x2.hi, x2.hi), df2::b2(1.0f / 24.0f), cx.lo);
+    const float4 ea = tab[(int)jf.x & (kFine - 1)], eb = tab[(int)jf.y & (kFine - 1)];
     const dd2 S{df2::p2(ea.x, eb.x), df2::p2(ea.y, eb.y)}, C{df2::p2(ea.z, eb.z), df2::p2(ea.w, eb.w)};
     // cos + i sin of the sum: (C + i S)(cx + i sx)
     const cdd2 w = df2::cmul_t<true, false>(cdd2{C, S}, cdd2{cx, sx});
@@ -478,7 +480,8 @@ __global__ void __launch_bounds__(PAIR ? kDfPairThreads : kDfMaxThreads, PAIR ? 
     extern __shared__ __align__(16) unsigned char smem[];
     DStage *st = reinterpret_cast<DStage *>(smem);
     float4 *sc = reinterpret_cast<float4 *>(st + (size_t)(p.L_max + 2) * TL);
-    float2 *e2 = reinterpret_cast<float2 *>(sc + kScEntries);
+    float4 *sf = sc + 64;
+    float2 *e2 = reinterpret_cast<float2 *>(sf + kFine);
     float2 *n0s = e2 + 65;         // [TL] dd n_0 (NaN if complex)
     float2 *ppm = n0s + TL;        // [TL] dd prod |1/n^2|^2
     int *ppe = reinterpret_cast<int *>(ppm + TL);
@@ -494,7 +497,9 @@ __global__ void __launch_bounds__(PAIR ? kDfPairThreads : kDfMaxThreads, PAIR ? 
     const double *lam = (const double *)p.lambda;
     const double *d = (const double *)p.d;
 
-    for (int i = tid; i < kScEntries; i += nthr) sc[i] = tabs.sc[i];
+    for (int i = tid; i < 64; i += nthr) sc[i] = tabs.sc[i];
+    if (PAIR)
+        for (int i = tid; i < kFine; i += nthr) sf[i] = tabs.sf[i];
     for (int i = tid; i < 65; i += nthr) e2[i] = tabs.e2[i];
     if (L >= 0) {
         const int total = (L + 2) * TL;
@@ -553,7 +558,7 @@ __global__ void __launch_bounds__(PAIR ? kDfPairThreads : kDfMaxThreads, PAIR ? 
             const dd Ppd = (POL & 2) ? dd{ppm[tl].x, ppm[tl].y} : df::make(1.0f);
             const int Ppe = (POL & 2) ? ppe[tl] : 0;
             if constexpr (PAIR)
-                eval_point_dd2<POL>(st, sc, e2, TL, tl, L, dd{n0.x, n0.y}, sth, cth, Ppd, Ppe, out);
+                eval_point_dd2<POL>(st, sf, e2, TL, tl, L, dd{n0.x, n0.y}, sth, cth, Ppd, Ppe, out);
             else
                 eval_point_dd<POL>(st, sc, e2, TL, tl, L, dd{n0.x, n0.y}, sth[0], cth[0], Ppd, Ppe, out[0]);
         } else {
@@ -585,12 +590,13 @@ const DfTables &host_tables()
     static DfTables t;
     static std::once_flag once;
     std::call_once(once, [] {
-        // entries 0..63 are those of the quadrant table the scalar sincos_turn_dd reads
-        for (int k = 0; k < kScEntries; ++k) {
-            const double a = 2.0 * kPi * k / 256.0;
+        const SinCosTable &q = sincos_table();
+        for (int k = 0; k < 64; ++k) t.sc[k] = q.sc[k];
+        for (int k = 0; k < kFine; ++k) {
+            const double a = 2.0 * kPi * k / kFine;
             const double sv = std::sin(a), cv = std::cos(a);
             const float sh = (float)sv, ch = (float)cv;
-            t.sc[k] = make_float4(sh, (float)(sv - sh), ch, (float)(cv - ch));
+            t.sf[k] = make_float4(sh, (float)(sv - sh), ch, (float)(cv - ch));
         }
         for (int i = -32; i <= 32; ++i) {
             const double v = std::exp2(i / 64.0);
@@ -603,7 +609,7 @@ const DfTables &host_tables()
 
 size_t df_stage_bytes(const tmm_problem *p, int TL)
 {
-    return (size_t)(p->L_max + 2) * TL * sizeof(DStage) + kScEntries * sizeof(float4) + 65 * sizeof(float2) +
+    return (size_t)(p->L_max + 2) * TL * sizeof(DStage) + (64 + kFine) * sizeof(float4) + 65 * sizeof(float2) +
            (size_t)TL * (2 * sizeof(float2) + sizeof(int));
 }
 
